@@ -1,0 +1,55 @@
+"""Input generators: determinism, sizes and the structural properties the
+workloads ask for (unique non-loop pairs, degree skew, block structure)."""
+import numpy as np
+
+import synth
+
+
+def _pairs(s, d):
+    return set(zip(np.minimum(s, d).tolist(), np.maximum(s, d).tolist()))
+
+
+def test_t_grid():
+    t = synth.t_grid()
+    assert t.size == 256 and t[0] == 1e-2 and t[-1] == 1e2
+    assert np.all(np.diff(np.log10(t)) > 0)
+
+
+def test_barabasi_albert():
+    s, d, n = synth.barabasi_albert(500, 4, seed=0)
+    assert n == 500 and s.size == 4 + 4 * (500 - 5)
+    assert len(_pairs(s, d)) == s.size and not np.any(s == d)
+    s2, d2, _ = synth.barabasi_albert(500, 4, seed=0)
+    assert np.array_equal(s, s2) and np.array_equal(d, d2)
+    deg = np.bincount(np.concatenate([s, d]))
+    assert deg.max() > 5 * np.median(deg)            # preferential attachment skew
+
+
+def test_rmat_unique_and_skewed():
+    s, d, n = synth.rmat(12, 16 << 12, seed=1)
+    assert n == 4096 and s.size == 16 << 12
+    assert not np.any(s == d)
+    assert len(_pairs(s, d)) == s.size
+    s2, d2, _ = synth.rmat(12, 16 << 12, seed=1)
+    assert np.array_equal(s, s2) and np.array_equal(d, d2)
+    deg = np.bincount(np.concatenate([s, d]), minlength=n)
+    assert deg[0] == deg.max()                        # a=0.57: node 0 is the hub
+    assert np.count_nonzero(deg == 0) > 0
+
+
+def test_sbm_batch_shapes():
+    gs = synth.sbm_batch(6, seed=3)
+    for s, d, n in gs:
+        assert 10 <= n <= 5000
+        assert len(_pairs(s, d)) == s.size and not np.any(s == d)
+        assert s.max(initial=0) < n and d.max(initial=0) < n
+
+
+def test_rewire_keeps_edge_count():
+    s, d, n = synth.barabasi_albert(300, 3, seed=2)
+    s2, d2, n2 = synth.rewire(s, d, n, frac=0.01, seed=5)
+    a, b = _pairs(s, d), _pairs(s2, d2)
+    assert n2 == n and len(b) == len(a)
+    k = int(np.ceil(0.01 * len(a)))
+    assert len(a - b) == k and len(b - a) == k
+    assert not np.any(s2 == d2)
