@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the SLQ hot path on the R-MAT 2^20 workload.
+
+Workload: R-MAT scale 20 (a, b, c, d = .57, .19, .19, .05), 16 Mi unique
+undirected edges, seed 1, isolated nodes dropped, normalized Laplacian;
+nv = 100 Rademacher probes, s = 20 Lanczos steps with full reorthogonalization;
+heat and wave traces on 256 log-spaced t in [1e-2, 1e2] and the VNGE.
+
+One step = the whole path on device-resident edges: Laplacian build, Lanczos
+(SpMM, Gram-Schmidt dots and update, reductions), Gauss rules, quadrature and
+the distance of the heat trace to a stored signature.  The metric is
+probe-edges per second: nnz * nv * s per step.  The headline form computes
+the Lanczos iteration in FP32 (alpha/beta reductions, eigensolve and
+quadrature in FP64); the FP64 form is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs the same graph with its own probe
+seed (weak scaling over probes); the per-rank estimates are averaged with
+one all-reduce of the descriptor vector.  `--impl reference` times the CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+if "--impl" in sys.argv and "reference" in sys.argv or "--cpu-baseline-worker" in sys.argv:
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "probe-edges/s in Lanczos SpMM (% HBM peak); graphs/s batched; rel err vs FP64"
+UNIT = "probe-edges/s"
+SCALE, EDGES, GRAPH_SEED = 20, 16 << 20, 1
+NV, S, NT, PROBE_SEED = 100, 20, 256, 1
+WORKLOAD = ("R-MAT scale 20 (2^20 nodes, 16Mi unique undirected edges, a,b,c,d=.57,.19,.19,.05, "
+            "seed 1), isolated nodes dropped, normalized Laplacian; nv=100 Rademacher probes, "
+            "s=20 Lanczos steps, full CGS reorthogonalization; heat + wave traces on 256 "
+            "log-spaced t in [1e-2,1e2] + VNGE")
+CPU_PROBES = 4        # probes of the CPU-oracle sample
+REF_PROBES = 1        # probes per step of the reference (oracle) arm
+
+
+def make_graph():
+    return synth.rmat(SCALE, EDGES, seed=GRAPH_SEED)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(src, dst, n, probes: int, s: int):
+    """Oracle on a bounded sample: CSR build + `probes` probes of Lanczos +
+    heat/wave/VNGE quadrature.  Returns (seconds, nnz)."""
+    from oracle import descriptors as od
+    from oracle.laplacian import build_laplacian
+    t = synth.t_grid(NT)
+    t0 = time.perf_counter()
+    lap = build_laplacian(src, dst, n, drop_isolated=True)
+    runs = od.slq_runs(lap, s, probes, PROBE_SEED, probes=range(probes))
+    od.heat_trace(runs, lap.n, t)
+    od.wave_trace(runs, lap.n, t)
+    od.vnge(runs, lap.n, lap.trace)
+    return time.perf_counter() - t0, lap.nnz
+
+
+def cpu_baseline_worker(path: str):
+    d = np.load(path)
+    sec, nnz = oracle_sample(d["src"], d["dst"], int(d["n"]), CPU_PROBES, S)
+    print(json.dumps({"seconds": sec, "nnz": nnz}))
+
+
+def cpu_baseline(src, dst, n):
+    """Run the oracle sample in a child process limited to one thread."""
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "g.npz")
+        np.savez(path, src=src, dst=dst, n=n)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", path],
+                           capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    pe = out["nnz"] * CPU_PROBES * S
+    return {"value": pe / out["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"CSR build of the full graph + {CPU_PROBES} of {NV} probes x {S} Lanczos "
+                      f"steps + heat/wave/VNGE quadrature ({out['seconds']:.1f} s, one thread)"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample
+    (REF_PROBES probes of the workload), timed on one host thread."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import descriptors as od
+    from oracle.laplacian import build_laplacian
+    src, dst, n = make_graph()
+    lap = build_laplacian(src, dst, n, drop_isolated=True)
+    t = synth.t_grid(NT)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        runs = od.slq_runs(lap, S, REF_PROBES, PROBE_SEED + i, probes=range(REF_PROBES))
+        od.heat_trace(runs, lap.n, t)
+        od.wave_trace(runs, lap.n, t)
+        od.vnge(runs, lap.n, lap.trace)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    sec = float(np.mean(times))
+    value = lap.nnz * REF_PROBES * S / sec
+    sample = f"{REF_PROBES} of {NV} probes x {S} Lanczos steps + quadrature per step, one thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nnz": lap.nnz, "n_prime": lap.n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.rows, self.proc, self.thread = [], None, None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [r for ts, r in self.rows if t0 <= ts <= t1 and len(r) >= 9] or \
+               [r for _, r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ our arm
+def algorithmic_bytes(n, nnz, prec, nv=NV, s=S):
+    """Algorithmic bytes of one run, per kernel class (useful nv columns)."""
+    bq = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+    bw = 8 if prec == "fp64" else 4
+    vec = n * nv
+    spmm = s * (8 * (n + 1) + 4 * nnz + vec * (bq + bw) + n * 2 * bw)
+    dots = sum(((k + 1 if k < s - 1 else 1) * bq + bw) * vec for k in range(s))
+    update = sum(((k + 1) * bq + bw + bq) * vec for k in range(s - 1))
+    return {"spmm": spmm, "dots": dots, "update": update}
+
+
+def run_ours(args):
+    import torch
+    from paper_2003_01282_gb300 import slaq
+    from paper_2003_01282_gb300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build()
+    slaq.lib()
+    if slaq.device_check() != 0:
+        raise SystemExit(f"libslaq: {slaq.last_error()[1]}")
+    dev = torch.device("cuda", local if dist else torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+
+    src_np, dst_np, n_nodes = make_graph()
+    src_h = torch.from_numpy(src_np).pin_memory()
+    dst_h = torch.from_numpy(dst_np).pin_memory()
+    src = src_h.to(dev)
+    dst = dst_h.to(dev)
+    t_np = synth.t_grid(NT)
+    t = torch.as_tensor(t_np, device=dev)
+    seed = PROBE_SEED + 1000 * rank
+    prec = args.precision
+    P = slaq.PRECISIONS[prec]
+
+    state = {"K": None, "ref": None}
+
+    def step(precision=P, key="K"):
+        g = slaq.build_laplacian(src, dst, n_nodes, kind=slaq.NORMALIZED, flags=slaq.DROP_ISOLATED)
+        state[key] = slaq.lanczos(g, NV, S, seed, precision=precision, reuse=state.get(key))
+        K = state[key]
+        heat, _ = slaq.trace_heat(K, t)
+        (wr, _), (wi, _) = slaq.trace_wave(K, t)
+        vn, _ = slaq.trace_vnge(K)
+        desc = torch.cat([heat, wr, wi, vn])
+        if dist:
+            tdist.all_reduce(desc)
+            desc /= world
+        if state["ref"] is None:
+            state["ref"] = desc[:NT].clone()
+        d = slaq.distance(desc[:NT], state["ref"], slaq.DIST_HEAT)
+        info = g.info
+        g.close()
+        return desc, d, info
+
+    for _ in range(args.warmup):
+        desc, _, info = step()
+    torch.cuda.synchronize(dev)
+    n_prime, nnz = info["n"], info["nnz"]
+
+    gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if \
+        os.environ.get("CUDA_VISIBLE_DEVICES") else str(dev.index)
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.5)
+    slaq.profile_enable(True)
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tw0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        desc, dval, _ = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    tw1 = time.perf_counter()
+    if dist:
+        tdist.barrier()
+    prof = slaq.profile_read()
+    slaq.profile_enable(False)
+    clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        mt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(mt, op=tdist.ReduceOp.MAX)
+        ms = float(mt.item())
+    pe_step = nnz * NV * S
+    value = world * pe_step / (ms * 1e-3)
+
+    # roofline of the dominant Lanczos kernel class
+    hbm, peak_src = peaks()
+    alg = algorithmic_bytes(n_prime, nnz, prec)
+    kernels = {}
+    for name in ("spmm", "dots", "update", "reduce", "build", "ritz", "trace", "probes", "dist"):
+        kms, kl = prof[name]
+        entry = {"ms_per_step": kms / args.steps, "launches_per_step": kl / args.steps}
+        if name in alg and kms > 0:
+            gbs = alg[name] * args.steps / (kms * 1e-3) / 1e9
+            entry.update({"GBps": gbs, "frac": gbs / hbm})
+        kernels[name] = entry
+    dom = max(("spmm", "dots", "update"), key=lambda k: prof[k][0])
+    dom_ms, dom_launch = prof[dom]
+    achieved = alg[dom] * args.steps / (dom_ms * 1e-3) / 1e9
+    launches = sum(v[1] for v in prof.values())
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else ("bf16" if prec == "bf16" else "f64"),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_prime": n_prime, "nnz": nnz, "nv": NV, "s": S, "nt": NT,
+                   "precision": prec, "parallelism": f"probes x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (basis %.1f GB, edge list %.0f MB)" % (
+                       S * n_prime * NV * {"fp64": 8, "fp32": 4, "bf16": 2}[prec] / 1e9,
+                       src.numel() * 8 / 1e6)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None,
+                     "algorithmic_bytes_per_launch": alg[dom] / max(1, dom_launch / args.steps)},
+        "kernels": kernels,
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(tw0, tw1),
+    }
+
+    # FP64 form beside it: time and error of the headline form against it
+    if prec != "fp64" and not args.quick:
+        for _ in range(1):
+            d64, _, _ = step(slaq.FP64, "K64")
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            d64, _, _ = step(slaq.FP64, "K64")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1) / 2
+        a, b = desc.double().cpu().numpy(), d64.cpu().numpy()
+        h, h64 = a[:NT], b[:NT]
+        result["fp64_form"] = {"ms_per_step": ms64, "value": world * pe_step / (ms64 * 1e-3),
+                               "speedup_of_headline": ms64 / ms}
+        result["rel_err_vs_fp64"] = {
+            "heat_max": float(np.max(np.abs(h - h64) / np.abs(h64))),
+            "wave_re_max": float(np.max(np.abs(a[NT:2 * NT] - b[NT:2 * NT])) / np.max(np.abs(b[NT:2 * NT]))),
+            "wave_im_max": float(np.max(np.abs(a[2 * NT:3 * NT] - b[2 * NT:3 * NT])) / np.max(np.abs(b[2 * NT:3 * NT]))),
+            "vnge": float(abs(a[-1] - b[-1]) / abs(b[-1])),
+        }
+
+    # end to end through the host-memory entry point (pinned buffers)
+    if not args.quick:
+        src_np_p, dst_np_p = src_h.numpy(), dst_h.numpy()
+        e2e_times = []
+        for i in range(1 + min(args.steps, 3)):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            out = slaq.descriptors_host(src_np_p, dst_np_p, n_nodes, t_np, kind=slaq.NORMALIZED,
+                                        flags=slaq.DROP_ISOLATED, nv=NV, s=S, seed=seed, precision=P)
+            t1 = time.perf_counter()
+            if i > 0:
+                e2e_times.append(t1 - t0)
+        e2e_s = float(np.mean(e2e_times))
+        result["e2e"] = {"value": world * pe_step / e2e_s, "unit": UNIT,
+                         "h2d_bytes_per_step": int(2 * 4 * src.numel() + 8 * NT),
+                         "d2h_bytes_per_step": int(8 * (3 * NT + 1)),
+                         "ms_per_step": e2e_s * 1e3}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(src_np, dst_np, n_nodes)
+    if rank == 0:
+        print(json.dumps(result))
+    if dist:
+        tdist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "bf16"], default="fp32")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64-form and end-to-end legs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-worker", default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_baseline_worker:
+        cpu_baseline_worker(args.cpu_baseline_worker)
+        return
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * slaq.h -- C ABI of libslaq: stochastic Lanczos quadrature (SLQ) estimates
+ * of spectral trace functions tr f(L) of graph Laplacians on one GPU
+ * (NVIDIA GB300, sm_103a).
+ *
+ * Method: Tsitsulin, Munkhoeva, Perozzi, "Just SLaQ When You Approximate:
+ * Accurate Spectral Distances for Web-Scale Graphs", WWW'20 (arXiv
+ * 2003.01282), Sec. 3 and Algorithm 1.
+ *
+ * Conventions (all entry points)
+ *   - Every function returns an int status (enum slaq_status); 0 is success.
+ *     slaq_last_error() gives a message for the calling thread's last failure.
+ *     No C++ exception crosses this boundary.
+ *   - Array arguments are DEVICE pointers of the current CUDA device unless
+ *     their name ends in _host.  The caller owns every array it passes.
+ *   - Handles (slaq_graph, slaq_krylov) own device memory allocated by the
+ *     library and are released by their *_destroy function, which waits for
+ *     the device to be idle first.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; unless a function says that it
+ *     synchronizes, it returns before the GPU work completes.
+ *   - There is no CPU fallback: without a compute-capability 10.3 GPU every
+ *     compute entry point returns SLAQ_ENODEVICE.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef SLAQ_H
+#define SLAQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum slaq_status {
+    SLAQ_OK = 0,
+    SLAQ_EINVAL = 1,        /* bad argument or malformed input */
+    SLAQ_ENOMEM = 2,        /* device allocation failed */
+    SLAQ_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SLAQ_ENODEVICE = 4,     /* no sm_103 device current (no CPU fallback) */
+    SLAQ_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    SLAQ_EUNSUPPORTED = 6,  /* valid request beyond what this build handles */
+    SLAQ_ENUMERIC = 7       /* the tridiagonal eigensolver did not converge */
+};
+
+/* Laplacian kinds (Sec. 2): L = D - A, or I - D^{-1/2} A D^{-1/2}. */
+enum { SLAQ_NORMALIZED = 0, SLAQ_COMBINATORIAL = 1 };
+/* Build flags. */
+enum { SLAQ_DROP_ISOLATED = 1 };
+/* Arithmetic forms of the Lanczos iteration (the alpha/beta reductions, the
+ * tridiagonal eigensolve and the quadrature are FP64 in every form):
+ *   SLAQ_FP64           basis, SpMM and reorthogonalization in FP64;
+ *   SLAQ_FP32           basis, SpMM and reorthogonalization in FP32;
+ *   SLAQ_FP32_BF16BASIS basis stored in BF16, SpMM and updates in FP32.   */
+enum { SLAQ_FP64 = 0, SLAQ_FP32 = 1, SLAQ_FP32_BF16BASIS = 2 };
+/* Distance kinds. */
+enum { SLAQ_DIST_HEAT = 0, SLAQ_DIST_WAVE = 1, SLAQ_DIST_VNGE = 2 };
+
+typedef struct slaq_graph_s *slaq_graph;    /* CSR Laplacian on the device */
+typedef struct slaq_krylov_s *slaq_krylov;  /* Lanczos result + workspace  */
+
+/* Library version as major*10000 + minor*100 + patch. */
+int slaq_version(void);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to len) into buf_host; returns the status of that error. */
+int slaq_last_error(char *buf_host, size_t len);
+
+/* SLAQ_OK if the current CUDA device is compute capability 10.3 (GB300),
+ * SLAQ_ENODEVICE otherwise.  Touches no memory. */
+int slaq_device_check(void);
+
+/* ---------------------------------------------------------------- graphs */
+
+/* Build the Laplacian of an undirected graph (Sec. 2) as CSR on the device.
+ *   src, dst   int32[n_edges] endpoint ids in [0, n_nodes); each pair is an
+ *              undirected edge.  Self-loops are dropped; duplicate pairs (in
+ *              either orientation) are merged, keeping the largest weight.
+ *   weights    float64[n_edges] positive edge weights, or NULL (all 1).
+ *   kind       SLAQ_NORMALIZED: diag 1 and off-diagonal -(a_ij s_i) s_j with
+ *              s_i = 1/sqrt(d_i); an isolated node gets s_i = 0 and a zero
+ *              row.  SLAQ_COMBINATORIAL: diag d_i, off-diagonal -a_ij.
+ *   flags      SLAQ_DROP_ISOLATED removes degree-0 nodes and renumbers the
+ *              rest in increasing order of their original ids.
+ * Degrees of weighted graphs are summed in increasing column order.  The CSR
+ * (rows, ascending column ids, values) is canonical, so it is bit-identical
+ * to any correct builder's.  Ids outside [0, n_nodes) give SLAQ_EINVAL.
+ * Synchronizes `stream` (array sizes are needed on the host).
+ * *out receives a new handle. */
+int slaq_build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges,
+                         int64_t n_nodes, const double *weights, int kind, int flags,
+                         void *stream, slaq_graph *out);
+
+/* Host copies of: kept node count n', stored off-diagonal count nnz, tr(L),
+ * and the n_nodes given at build time (any pointer may be NULL). */
+int slaq_graph_info(slaq_graph g, int64_t *n_host, int64_t *nnz_host,
+                    double *trace_host, int64_t *n_input_host);
+
+/* Device copies of the CSR: rowptr int64[n'+1], colidx int32[nnz],
+ * vals float64[nnz] (off-diagonal values), diag float64[n'], scale float64[n']
+ * (s_i; 1 for combinatorial), old_id int64[n'] (original id of each kept
+ * node).  Any pointer may be NULL.  For bit-exact checks. */
+int slaq_graph_export(slaq_graph g, int64_t *rowptr, int32_t *colidx, double *vals,
+                      double *diag, double *scale, int64_t *old_id, void *stream);
+
+void slaq_graph_destroy(slaq_graph g);
+
+/* ---------------------------------------------------------------- Lanczos */
+
+/* Run s-step Lanczos (Sec. 3.1, Algorithm 1 `lanczos`) of the graph's
+ * Laplacian from nv Rademacher probes at once, then the Gauss rule of every
+ * probe's tridiagonal T (Eq. quadratic: nodes = eigenvalues of T, weights =
+ * squared first eigenvector components).
+ *   Probe p's entry at node i is the sign of SplitMix64 applied to
+ *   seed + 0x9E3779B97F4A7C15 * (c + 1), c = graph_id<<48 | p<<32 | orig_id(i)
+ *   (-1 where bit 63 is set); the starting vector is that sign vector / sqrt(n').
+ *   Every step orthogonalizes the new vector against all previous Lanczos
+ *   vectors of its probe by classical Gram-Schmidt (reorth_passes = 1) or
+ *   twice (2).  A probe whose beta_k falls to tol * bound (tol 1e-10 FP64,
+ *   1e-4 FP32, 3e-2 BF16 basis; bound 2 or 2 max d) stops with m = k+1.
+ *   1 <= nv <= 1024, 1 <= s <= 64, precision one of SLAQ_FP64/FP32/
+ *   FP32_BF16BASIS, graph_id < 65536.
+ * inout: if *inout is NULL a new handle is created; otherwise *inout must
+ * come from an earlier call with the same nv, s and precision, and its
+ * device workspace is reused (grown if the graph is larger).
+ * The graph handle must stay alive until the work on `stream` completes. */
+int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id,
+                 int precision, int reorth_passes, void *stream, slaq_krylov *inout);
+
+/* The probe block the Lanczos run starts from, as float64[n'][nv] (+-1),
+ * generated on the device exactly as slaq_lanczos does (Eq. trace needs
+ * zero-mean, unit-variance probes; the text allows Rademacher signs).
+ * For bit-exact checks of the generator. */
+int slaq_probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, void *stream);
+
+/* Device copies of alpha float64[nv*s] (row p holds alpha_0..alpha_{m_p-1}),
+ * beta float64[nv*s] (beta_0..beta_{m_p-2}) and m int32[nv].  NULL skips. */
+int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, void *stream);
+
+/* Device copies of the Gauss nodes theta float64[nv*s] (ascending within a
+ * probe's first m_p entries) and weights tau2 float64[nv*s]. */
+int slaq_ritz_export(slaq_krylov k, double *theta, double *tau2, void *stream);
+
+/* Host copies of nv, s, precision, n'. */
+int slaq_krylov_info(slaq_krylov k, int *nv_host, int *s_host, int *precision_host,
+                     int64_t *n_host);
+
+/* Heat trace h_t = tr exp(-t L) (Eq. heat-trace) at nt times t (float64[nt],
+ * device) by Eq. slq: out[i] = (n'/nv) sum_p sum_k tau2 exp(-t_i theta);
+ * stderr_[i] = sample std over probes / sqrt(nv) (NaN when nv = 1);
+ * per_probe float64[nv*nt] (row p = n' sum_k tau2 exp(-t theta)) or NULL. */
+int slaq_trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *stderr_,
+                    double *per_probe, void *stream);
+
+/* Wave trace tr exp(-i t L): re[i] = sum cos(t lambda), im[i] = -sum sin(t lambda),
+ * estimated as above; stderr arrays may be NULL. */
+int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im,
+                    double *stderr_re, double *stderr_im, void *stream);
+
+/* Von Neumann graph entropy (Definition 1, Sec. 2.1) of P = L / tr(L) for
+ * the Laplacian the graph was built with: -sum mu ln mu over mu = theta/tr(L)
+ * > 0 (natural log, 0 ln 0 = 0).  out, stderr_: float64[1]; per_probe
+ * float64[nv] or NULL. */
+int slaq_trace_vnge(slaq_krylov k, double *out, double *stderr_, double *per_probe,
+                    void *stream);
+
+void slaq_krylov_destroy(slaq_krylov k);
+
+/* --------------------------------------------------------------- distances */
+
+/* Spectral distance between two descriptors (Sec. 4.2):
+ *   SLAQ_DIST_HEAT: a, b float64[nt]; out = ||a - b||_2;
+ *   SLAQ_DIST_WAVE: a, b float64[2*nt] (re then im); out = ||a - b||_2;
+ *   SLAQ_DIST_VNGE: a, b float64[1]; out = |a - b|.
+ * out: float64[1] on the device. */
+int slaq_distance(const double *a, const double *b, int nt, int kind, double *out,
+                  void *stream);
+
+/* ------------------------------------------------------------- host calls */
+
+/* The whole path in one call, from host memory to host memory: copies the
+ * edge list and t grid to the device, builds the Laplacian, runs Lanczos and
+ * the quadrature, and copies heat[nt], wave_re[nt], wave_im[nt] and vnge[1]
+ * back (any output may be NULL).  Synchronizes `stream` before returning. */
+int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int64_t n_edges,
+                          int64_t n_nodes, int kind, int flags, int nv, int s, uint64_t seed,
+                          int precision, const double *t_host, int nt, double *heat_host,
+                          double *wave_re_host, double *wave_im_host, double *vnge_host,
+                          void *stream);
+
+/* ------------------------------------------------------------- profiling */
+
+/* Kernel classes timed by the profiler. */
+enum {
+    SLAQ_PROF_BUILD = 0,   /* every kernel of slaq_build_laplacian            */
+    SLAQ_PROF_PROBES = 1,  /* probe generation                                */
+    SLAQ_PROF_SPMM = 2,    /* L u_k for the probe block (split rows included)  */
+    SLAQ_PROF_DOTS = 3,    /* u_j^T z (or u_j^T u_{k+1}) block partial sums    */
+    SLAQ_PROF_UPDATE = 4,  /* u_{k+1} = z - sum_j c_j u_j and its norm partials*/
+    SLAQ_PROF_REDUCE = 5,  /* partial-sum reductions, alpha, beta, breakdown   */
+    SLAQ_PROF_RITZ = 6,    /* tridiagonal Gauss rules                          */
+    SLAQ_PROF_TRACE = 7,   /* quadrature: heat, wave, VNGE                     */
+    SLAQ_PROF_DIST = 8,    /* distances                                        */
+    SLAQ_PROF_NCAT = 9
+};
+
+/* on != 0: from now on, bracket every kernel class above with CUDA events
+ * recorded on the stream it is launched on; clears all totals (times and
+ * launch counts).  on == 0: stop recording (totals are kept). */
+int slaq_profile_enable(int on);
+
+/* Host copies of the accumulated device time (ms) and number of kernel
+ * launches of one class since the last slaq_profile_enable(1).  Launches
+ * are counted whether or not timing is on.  Waits for the recorded events. */
+int slaq_profile_read(int category, double *ms_host, int64_t *launches_host);
+
+/* Gauss rule of one symmetric tridiagonal matrix on the host, with the same
+ * implicit-shift QR code the GPU kernel runs (Golub & Van Loan, Sec. 8.3):
+ * alpha_host[m] diagonal, beta_host[m-1] off-diagonal; theta_host[m]
+ * ascending eigenvalues, tau2_host[m] squared first eigenvector components.
+ * Needs no GPU; for testing the solver on its own.  SLAQ_ENUMERIC if it did
+ * not converge. */
+int slaq_tridiag_gauss_host(const double *alpha_host, const double *beta_host, int m,
+                            double *theta_host, double *tau2_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLAQ_H */

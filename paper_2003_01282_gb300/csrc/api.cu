@@ -1,0 +1,413 @@
+// extern "C" entry points of libslaq (declared in include/slaq.h): argument
+// checks, device check, error reporting; the work is in build.cu,
+// lanczos.cu and quad.cu.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "tridiag.cuh"
+
+namespace slaq {
+namespace {
+thread_local char g_msg[512] = "no error";
+thread_local int g_status = SLAQ_OK;
+
+struct DeviceInfo {
+  int checked = 0;  // 0 unknown, 1 ok, 2 wrong device
+  int sms = 0;
+};
+std::mutex g_dev_mutex;
+DeviceInfo g_dev[64];
+}  // namespace
+
+int set_error(int status, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  g_status = status;
+  return status;
+}
+
+int cuda_status(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(SLAQ_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return set_error(SLAQ_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int device_check() {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return set_error(SLAQ_ENODEVICE, "no CUDA device available (%s); libslaq has no CPU path",
+                     cudaGetErrorString(e));
+  }
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  DeviceInfo &d = g_dev[dev];
+  if (d.checked == 0) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SLAQ_ENODEVICE, "cannot query CUDA device %d", dev);
+    }
+    d.checked = (prop.major == 10 && prop.minor == 3) ? 1 : 2;
+    d.sms = prop.multiProcessorCount;
+    if (d.checked == 1) {
+      // keep freed stream-ordered allocations cached in the pool
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      cudaGetLastError();
+    }
+  }
+  if (d.checked != 1)
+    return set_error(SLAQ_ENODEVICE,
+                     "CUDA device %d is not compute capability 10.3 (GB300); libslaq is built "
+                     "for sm_103a only",
+                     dev);
+  return SLAQ_OK;
+}
+
+int num_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return std::max(1, g_dev[dev].sms);
+}
+
+int dalloc(void **p, size_t bytes, cudaStream_t st) {
+  cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_error(SLAQ_ENOMEM, "cudaMallocAsync of %zu bytes failed: %s", bytes,
+                     cudaGetErrorString(e));
+  }
+  return SLAQ_OK;
+}
+
+void dfree(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+// ---------------------------------------------------------------- profiler
+thread_local int64_t tl_launches = 0;
+namespace {
+struct ProfPair {
+  int cat;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mutex;
+bool g_prof_on = false;
+std::vector<ProfPair> g_prof_pairs;
+std::vector<cudaEvent_t> g_prof_pool;
+std::vector<std::pair<int, cudaEvent_t>> g_prof_open;  // (cat, start) per open scope
+double g_prof_ms[SLAQ_PROF_NCAT] = {0};
+int64_t g_prof_launch[SLAQ_PROF_NCAT] = {0};
+
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void prof_collect_locked() {
+  for (auto &p : g_prof_pairs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+      g_prof_ms[p.cat] += ms;
+    cudaGetLastError();
+    g_prof_pool.push_back(p.a);
+    g_prof_pool.push_back(p.b);
+  }
+  g_prof_pairs.clear();
+}
+}  // namespace
+
+void prof_begin(int cat, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  cudaEvent_t e = nullptr;
+  if (g_prof_on) {
+    e = prof_event();
+    if (e && cudaEventRecord(e, st) != cudaSuccess) {
+      cudaGetLastError();
+      g_prof_pool.push_back(e);
+      e = nullptr;
+    }
+  }
+  g_prof_open.push_back({cat, e});
+}
+
+void prof_end(int cat, cudaStream_t st, int64_t launches) {
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  cudaEvent_t a = nullptr;
+  for (size_t i = g_prof_open.size(); i-- > 0;) {
+    if (g_prof_open[i].first == cat) {
+      a = g_prof_open[i].second;
+      g_prof_open.erase(g_prof_open.begin() + i);
+      break;
+    }
+  }
+  if (cat >= 0 && cat < SLAQ_PROF_NCAT) g_prof_launch[cat] += launches;
+  if (!a) return;
+  cudaEvent_t b = prof_event();
+  if (!b || cudaEventRecord(b, st) != cudaSuccess) {
+    cudaGetLastError();
+    g_prof_pool.push_back(a);
+    if (b) g_prof_pool.push_back(b);
+    return;
+  }
+  g_prof_pairs.push_back({cat, a, b});
+  if (g_prof_pairs.size() > 4096) prof_collect_locked();
+}
+
+}  // namespace slaq
+
+using namespace slaq;
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+int slaq_version(void) { return 100; }
+
+int slaq_last_error(char *buf, size_t len) {
+  if (buf && len) {
+    strncpy(buf, g_msg, len - 1);
+    buf[len - 1] = '\0';
+  }
+  return g_status;
+}
+
+int slaq_device_check(void) { return device_check(); }
+
+int slaq_build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges, int64_t n_nodes,
+                         const double *weights, int kind, int flags, void *stream,
+                         slaq_graph *out) {
+  SLAQ_TRY(device_check());
+  return build_laplacian(src, dst, n_edges, n_nodes, weights, kind, flags, as_stream(stream), out);
+}
+
+int slaq_graph_info(slaq_graph g, int64_t *n, int64_t *nnz, double *trace, int64_t *n_input) {
+  if (!g) return set_error(SLAQ_EINVAL, "NULL graph");
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (trace) *trace = g->trace;
+  if (n_input) *n_input = g->n_input;
+  return SLAQ_OK;
+}
+
+int slaq_graph_export(slaq_graph g, int64_t *rowptr, int32_t *colidx, double *vals, double *diag,
+                      double *scale, int64_t *old_id, void *stream) {
+  if (!g) return set_error(SLAQ_EINVAL, "NULL graph");
+  SLAQ_TRY(device_check());
+  cudaStream_t st = as_stream(stream);
+  auto cp = [&](void *dst, const void *src, size_t bytes) -> int {
+    if (dst && bytes) SLAQ_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+    return SLAQ_OK;
+  };
+  SLAQ_TRY(cp(rowptr, g->rowptr, (g->n + 1) * sizeof(int64_t)));
+  SLAQ_TRY(cp(colidx, g->colidx, g->nnz * sizeof(int32_t)));
+  SLAQ_TRY(cp(vals, g->vals, g->nnz * sizeof(double)));
+  SLAQ_TRY(cp(diag, g->diag, g->n * sizeof(double)));
+  SLAQ_TRY(cp(scale, g->scale, g->n * sizeof(double)));
+  SLAQ_TRY(cp(old_id, g->old_id, g->n * sizeof(int64_t)));
+  return SLAQ_OK;
+}
+
+void slaq_graph_destroy(slaq_graph g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  graph_free(g);
+}
+
+int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
+                 int reorth_passes, void *stream, slaq_krylov *inout) {
+  SLAQ_TRY(device_check());
+  cudaStream_t st = as_stream(stream);
+  SLAQ_TRY(run_lanczos(g, nv, s, seed, graph_id, precision, reorth_passes, st, inout));
+  int32_t status = 0;
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, (*inout)->status, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
+  return SLAQ_OK;
+}
+
+int slaq_probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, void *stream) {
+  SLAQ_TRY(device_check());
+  return probes(g, nv, seed, graph_id, out, as_stream(stream));
+}
+
+int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  cudaStream_t st = as_stream(stream);
+  const size_t ns = (size_t)k->nv * k->s;
+  if (alpha) SLAQ_CHECK_CUDA(cudaMemcpyAsync(alpha, k->alpha, ns * 8, cudaMemcpyDeviceToDevice, st));
+  if (beta) SLAQ_CHECK_CUDA(cudaMemcpyAsync(beta, k->beta, ns * 8, cudaMemcpyDeviceToDevice, st));
+  if (m) SLAQ_CHECK_CUDA(cudaMemcpyAsync(m, k->m, k->nv * 4, cudaMemcpyDeviceToDevice, st));
+  return SLAQ_OK;
+}
+
+int slaq_ritz_export(slaq_krylov k, double *theta, double *tau2, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  cudaStream_t st = as_stream(stream);
+  const size_t ns = (size_t)k->nv * k->s;
+  if (theta) SLAQ_CHECK_CUDA(cudaMemcpyAsync(theta, k->theta, ns * 8, cudaMemcpyDeviceToDevice, st));
+  if (tau2) SLAQ_CHECK_CUDA(cudaMemcpyAsync(tau2, k->tau2, ns * 8, cudaMemcpyDeviceToDevice, st));
+  return SLAQ_OK;
+}
+
+int slaq_krylov_info(slaq_krylov k, int *nv, int *s, int *precision, int64_t *n) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  if (nv) *nv = k->nv;
+  if (s) *s = k->s;
+  if (precision) *precision = k->precision;
+  if (n) *n = k->n;
+  return SLAQ_OK;
+}
+
+int slaq_trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *stderr_,
+                    double *per_probe, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  return trace_heat(k, t, nt, out, stderr_, per_probe, as_stream(stream));
+}
+
+int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im,
+                    double *stderr_re, double *stderr_im, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  return trace_wave(k, t, nt, re, im, stderr_re, stderr_im, as_stream(stream));
+}
+
+int slaq_trace_vnge(slaq_krylov k, double *out, double *stderr_, double *per_probe, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  return trace_vnge(k, out, stderr_, per_probe, as_stream(stream));
+}
+
+void slaq_krylov_destroy(slaq_krylov k) {
+  if (!k) return;
+  cudaDeviceSynchronize();
+  krylov_free(k);
+}
+
+int slaq_distance(const double *a, const double *b, int nt, int kind, double *out, void *stream) {
+  SLAQ_TRY(device_check());
+  return distance(a, b, nt, kind, out, as_stream(stream));
+}
+
+int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int64_t n_edges,
+                          int64_t n_nodes, int kind, int flags, int nv, int s, uint64_t seed,
+                          int precision, const double *t_host, int nt, double *heat_host,
+                          double *wave_re_host, double *wave_im_host, double *vnge_host,
+                          void *stream) {
+  SLAQ_TRY(device_check());
+  if (n_edges < 0 || (n_edges > 0 && (!src_host || !dst_host)))
+    return set_error(SLAQ_EINVAL, "bad edge arrays");
+  if ((heat_host || wave_re_host || wave_im_host) && (!t_host || nt < 1))
+    return set_error(SLAQ_EINVAL, "traces need t_host and nt >= 1");
+  cudaStream_t st = as_stream(stream);
+  struct Bufs {
+    cudaStream_t st;
+    std::vector<void *> p;
+    slaq_graph g = nullptr;
+    slaq_krylov k = nullptr;
+    ~Bufs() {
+      cudaStreamSynchronize(st);
+      for (void *x : p) cudaFreeAsync(x, st);
+      if (k) krylov_free(k);
+      if (g) graph_free(g);
+      cudaStreamSynchronize(st);
+    }
+  } b{st, {}};
+  auto get = [&](void **x, size_t bytes) -> int {
+    SLAQ_TRY(dalloc(x, bytes, st));
+    b.p.push_back(*x);
+    return SLAQ_OK;
+  };
+  int32_t *src = nullptr, *dst = nullptr;
+  double *t = nullptr, *out = nullptr;
+  const int ntt = std::max(nt, 1);
+  SLAQ_TRY(get((void **)&src, n_edges * sizeof(int32_t)));
+  SLAQ_TRY(get((void **)&dst, n_edges * sizeof(int32_t)));
+  SLAQ_TRY(get((void **)&t, ntt * sizeof(double)));
+  SLAQ_TRY(get((void **)&out, (3 * (size_t)ntt + 1) * sizeof(double)));
+  if (n_edges > 0) {
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(src, src_host, n_edges * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(dst, dst_host, n_edges * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  }
+  if (t_host && nt > 0)
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(t, t_host, nt * sizeof(double), cudaMemcpyHostToDevice, st));
+  SLAQ_TRY(build_laplacian(src, dst, n_edges, n_nodes, nullptr, kind, flags, st, &b.g));
+  SLAQ_TRY(run_lanczos(b.g, nv, s, seed, 0, precision, 1, st, &b.k));
+  if (heat_host) SLAQ_TRY(trace_heat(b.k, t, nt, out, nullptr, nullptr, st));
+  if (wave_re_host || wave_im_host)
+    SLAQ_TRY(trace_wave(b.k, t, nt, out + ntt, out + 2 * ntt, nullptr, nullptr, st));
+  if (vnge_host) SLAQ_TRY(trace_vnge(b.k, out + 3 * ntt, nullptr, nullptr, st));
+  std::vector<double> h(3 * (size_t)ntt + 1);
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(h.data(), out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  int32_t status = 0;
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, b.k->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
+  if (heat_host) std::memcpy(heat_host, h.data(), nt * sizeof(double));
+  if (wave_re_host) std::memcpy(wave_re_host, h.data() + ntt, nt * sizeof(double));
+  if (wave_im_host) std::memcpy(wave_im_host, h.data() + 2 * ntt, nt * sizeof(double));
+  if (vnge_host) *vnge_host = h[3 * ntt];
+  return SLAQ_OK;
+}
+
+int slaq_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  if (on) {
+    prof_collect_locked();
+    for (int i = 0; i < SLAQ_PROF_NCAT; ++i) {
+      g_prof_ms[i] = 0.0;
+      g_prof_launch[i] = 0;
+    }
+  }
+  g_prof_on = on != 0;
+  return SLAQ_OK;
+}
+
+int slaq_profile_read(int category, double *ms, int64_t *launches) {
+  if (category < 0 || category >= SLAQ_PROF_NCAT)
+    return set_error(SLAQ_EINVAL, "unknown profile category %d", category);
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  prof_collect_locked();
+  if (ms) *ms = g_prof_ms[category];
+  if (launches) *launches = g_prof_launch[category];
+  return SLAQ_OK;
+}
+
+int slaq_tridiag_gauss_host(const double *alpha, const double *beta, int m, double *theta,
+                            double *tau2) {
+  if (m < 1 || m > 4096 || !alpha || !theta || !tau2 || (m > 1 && !beta))
+    return set_error(SLAQ_EINVAL, "bad arguments to slaq_tridiag_gauss_host");
+  std::vector<double> e(std::max(m, 1), 0.0);
+  for (int i = 0; i < m; ++i) theta[i] = alpha[i];
+  for (int i = 0; i + 1 < m; ++i) e[i] = beta[i];
+  if (tridiag_gauss(theta, e.data(), tau2, m) != 0)
+    return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
+  return SLAQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,700 @@
+// CSR / degree-normalization builder (Sec. 2: L = D - A and
+// I - D^{-1/2} A D^{-1/2}).
+//
+// Pipeline, all on the device:
+//   1. validate ids; emit both orientations of every non-loop edge as 64-bit
+//      keys (row << cb | col), with the weight as payload;
+//   2. stable LSD radix sort of the keys (8-bit digits, reduce-then-scan);
+//   3. merge duplicates (largest weight kept), rowptr from the sorted rows;
+//   4. degrees, optional removal of isolated nodes with order-preserving
+//      renumbering, scales s_i = 1/sqrt(d_i) and off-diagonal values;
+//   5. the SpMM schedule that splits rows of more than `heavy_degree`
+//      entries into chunks.
+// The result is canonical (sorted columns, merged duplicates), so it equals
+// any correct builder's bit for bit.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace slaq {
+namespace {
+
+// ------------------------------------------------------------- block scan
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t warp_inclusive_scan(int64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread across the block; returns the
+// thread's prefix and writes the block total to *total.
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
+  __shared__ int64_t warp_tot[33];   // [0, 32): warp prefixes, [32]: total
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  int64_t inc = warp_inclusive_scan(v);
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < nwarps ? warp_tot[lane] : 0;
+    int64_t wi = warp_inclusive_scan(w);
+    if (lane < nwarps) warp_tot[lane] = wi - w;
+    if (lane == 31) warp_tot[32] = wi;  // lanes past nwarps add zeros
+  }
+  __syncthreads();
+  int64_t res = warp_tot[warp] + inc - v;
+  if (total) *total = warp_tot[32];
+  __syncthreads();
+  return res;
+}
+
+template <typename TI>
+__global__ void k_scan_tile_sums(const TI *in, int64_t n, int64_t *bsum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t acc = 0;
+#pragma unroll
+  for (int it = 0; it < kScanItems; ++it) {
+    int64_t i = base + (int64_t)it * kScanThreads + threadIdx.x;
+    if (i < n) acc += (int64_t)in[i];
+  }
+  int64_t tot;
+  block_exclusive_scan(acc, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// One block scans the tile sums in place (exclusive) and stores the grand
+// total in *total.
+__global__ void k_scan_tile_prefix(int64_t *bsum, int64_t nb, int64_t *total) {
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    int64_t i = b0 + threadIdx.x;
+    int64_t v = i < nb ? bsum[i] : 0;
+    int64_t tot;
+    int64_t ex = block_exclusive_scan(v, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+template <typename TI>
+__global__ void k_scan_apply(const TI *in, int64_t n, const int64_t *bsum, int64_t *out) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t vals[kScanItems];
+  int64_t acc = 0;
+#pragma unroll
+  for (int it = 0; it < kScanItems; ++it) {
+    int64_t i = base + it;
+    vals[it] = i < n ? (int64_t)in[i] : 0;
+    acc += vals[it];
+  }
+  int64_t ex = block_exclusive_scan(acc, nullptr) + bsum[blockIdx.x];
+#pragma unroll
+  for (int it = 0; it < kScanItems; ++it) {
+    int64_t i = base + it;
+    if (i < n) out[i] = ex;
+    ex += vals[it];
+  }
+}
+
+// out[0..n) = exclusive prefix sums of in; *total_dev = sum (device int64).
+template <typename TI>
+int exclusive_scan(const TI *in, int64_t n, int64_t *out, int64_t *total_dev, cudaStream_t st) {
+  int64_t nb = std::max<int64_t>(1, ceil_div(n, kScanTile));
+  int64_t *bsum = nullptr;
+  SLAQ_TRY(dalloc_t(&bsum, nb, st));
+  if (n > 0) {
+    ++tl_launches;
+    k_scan_tile_sums<TI><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum);
+  } else {
+    SLAQ_CHECK_CUDA(cudaMemsetAsync(bsum, 0, sizeof(int64_t), st));
+  }
+  ++tl_launches;
+  k_scan_tile_prefix<<<1, 1024, 0, st>>>(bsum, nb, total_dev);
+  if (n > 0) {
+    // the apply kernel walks kScanItems consecutive items per thread
+    ++tl_launches;
+    k_scan_apply<TI><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum, out);
+  }
+  SLAQ_CHECK_LAUNCH("exclusive_scan");
+  dfree(bsum, st);
+  return SLAQ_OK;
+}
+
+// ------------------------------------------------------------- radix sort
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsRounds = 16;                       // 32-key rounds per warp
+constexpr int kRsTile = kRsThreads * kRsRounds;     // 4096 keys per block
+
+__global__ void k_radix_hist(const uint64_t *keys, int64_t n, int shift, uint32_t *counts,
+                             int64_t ntiles) {
+  __shared__ uint32_t hist[256];
+  hist[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+  for (int it = 0; it < kRsRounds; ++it) {
+    int64_t i = base + (int64_t)it * kRsThreads + threadIdx.x;
+    if (i < n) atomicAdd(&hist[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
+}
+
+// Stable scatter: warp w of a block owns keys [tile + 512 w, tile + 512 (w+1))
+// and ranks them round by round (32 keys per round, lane order), so equal
+// digits keep their input order inside the warp; warps are ordered by a
+// per-digit prefix over warps, tiles by the digit-major global scan.
+template <bool PAYLOAD>
+__global__ void __launch_bounds__(kRsThreads)
+    k_radix_scatter(const uint64_t *__restrict__ kin, const double *__restrict__ pin,
+                    uint64_t *__restrict__ kout, double *__restrict__ pout, int64_t n, int shift,
+                    const int64_t *__restrict__ offsets, int64_t ntiles) {
+  __shared__ uint32_t whist[kRsWarps][256];
+  __shared__ int64_t gbase[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&whist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t seg = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * (32 * kRsRounds);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  uint64_t key[kRsRounds];
+  uint32_t local[kRsRounds];
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    const int64_t i = seg + r * 32 + lane;
+    const bool valid = i < n;
+    key[r] = valid ? kin[i] : 0ull;
+    const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt_mask);
+    uint32_t before = d < 256u ? whist[warp][d] : 0u;
+    __syncwarp();
+    if (d < 256u && rank == 0) whist[warp][d] = before + __popc(peers);
+    __syncwarp();
+    local[r] = before + rank;
+  }
+  __syncthreads();
+  {
+    const int d = threadIdx.x;  // 256 threads, one digit each
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) {
+      uint32_t c = whist[w][d];
+      whist[w][d] = run;
+      run += c;
+    }
+    gbase[d] = offsets[(int64_t)d * ntiles + blockIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    const int64_t i = seg + r * 32 + lane;
+    if (i < n) {
+      const uint32_t d = (uint32_t)((key[r] >> shift) & 255u);
+      const int64_t pos = gbase[d] + whist[warp][d] + local[r];
+      kout[pos] = key[r];
+      if (PAYLOAD) pout[pos] = pin[i];
+    }
+  }
+}
+
+// Sorts n keys on their low `bits` bits.  Result in *keys (buffers swapped
+// as needed; both buffers hold n entries).
+int radix_sort(uint64_t **keys, uint64_t **keys_alt, double **pay, double **pay_alt, int64_t n,
+               int bits, cudaStream_t st) {
+  if (n <= 1) return SLAQ_OK;
+  const int64_t ntiles = ceil_div(n, kRsTile);
+  uint32_t *counts = nullptr;
+  int64_t *offsets = nullptr, *total = nullptr;
+  SLAQ_TRY(dalloc_t(&counts, 256 * ntiles, st));
+  SLAQ_TRY(dalloc_t(&offsets, 256 * ntiles, st));
+  SLAQ_TRY(dalloc_t(&total, 1, st));
+  const bool with_pay = pay && *pay;
+  for (int shift = 0; shift < bits; shift += 8) {
+    ++tl_launches;
+    k_radix_hist<<<(unsigned)ntiles, kRsThreads, 0, st>>>(*keys, n, shift, counts, ntiles);
+    SLAQ_CHECK_LAUNCH("radix_hist");
+    SLAQ_TRY(exclusive_scan(counts, 256 * ntiles, offsets, total, st));
+    if (with_pay) {
+      ++tl_launches;
+      k_radix_scatter<true><<<(unsigned)ntiles, kRsThreads, 0, st>>>(
+          *keys, *pay, *keys_alt, *pay_alt, n, shift, offsets, ntiles);
+      std::swap(*pay, *pay_alt);
+    } else {
+      ++tl_launches;
+      k_radix_scatter<false><<<(unsigned)ntiles, kRsThreads, 0, st>>>(
+          *keys, nullptr, *keys_alt, nullptr, n, shift, offsets, ntiles);
+    }
+    SLAQ_CHECK_LAUNCH("radix_scatter");
+    std::swap(*keys, *keys_alt);
+  }
+  dfree(counts, st);
+  dfree(offsets, st);
+  dfree(total, st);
+  return SLAQ_OK;
+}
+
+// ---------------------------------------------------------- CSR kernels
+__global__ void k_validate(const int32_t *src, const int32_t *dst, const double *w, int64_t m,
+                           int64_t n, int32_t *bad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t a = src[e], b = dst[e];
+    if (a < 0 || b < 0 || a >= n || b >= n) atomicOr(bad, 1);
+    if (w && !(w[e] > 0.0)) atomicOr(bad, 2);
+  }
+}
+
+// Both orientations of every non-loop edge; slots taken with one atomic per
+// warp, so the emission order is arbitrary (the sort removes it).
+__global__ void k_emit(const int32_t *src, const int32_t *dst, const double *w, int64_t m, int cb,
+                       uint64_t *keys, double *pay, unsigned long long *counter) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x; e0 < m; e0 += stride) {
+    const int64_t e = e0 + threadIdx.x;
+    bool emit = false;
+    uint64_t a = 0, b = 0;
+    if (e < m) {
+      a = (uint32_t)src[e];
+      b = (uint32_t)dst[e];
+      emit = a != b;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, emit);
+    if (mask == 0) continue;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, 2ull * __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (emit) {
+      const unsigned long long pos = base + 2ull * __popc(mask & ((1u << lane) - 1u));
+      keys[pos] = (a << cb) | b;
+      keys[pos + 1] = (b << cb) | a;
+      if (pay) {
+        pay[pos] = w[e];
+        pay[pos + 1] = w[e];
+      }
+    }
+  }
+}
+
+__global__ void k_first_flags(const uint64_t *k, int64_t m, uint8_t *flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = (i == 0 || k[i] != k[i - 1]) ? 1 : 0;
+}
+
+// Unique keys; the weight of a merged run is the largest of the run.
+__global__ void k_unique(const uint64_t *k, const double *pay, int64_t m, const uint8_t *flag,
+                         const int64_t *pos, uint64_t *ukey, double *uw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    ukey[pos[i]] = k[i];
+    if (pay) {
+      double mx = pay[i];
+      for (int64_t j = i + 1; j < m && k[j] == k[i]; ++j) mx = fmax(mx, pay[j]);
+      uw[pos[i]] = mx;
+    }
+  }
+}
+
+// rowptr[r] = index of the first key with row >= r (rows = key >> cb).
+__global__ void k_rowptr(const uint64_t *ukey, int64_t nnz, int cb, int64_t n, int64_t *rowptr) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r_prev = i == 0 ? -1 : (int64_t)(ukey[i - 1] >> cb);
+    const int64_t r_cur = i == nnz ? n : (int64_t)(ukey[i] >> cb);
+    for (int64_t r = r_prev + 1; r <= r_cur; ++r) rowptr[r] = i;
+  }
+}
+
+// Degrees: entry counts, or weights summed left to right in column order.
+__global__ void k_degree(const int64_t *rowptr, const double *uw, int64_t n, double *deg,
+                         uint8_t *keep) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    double d;
+    if (uw) {
+      d = 0.0;
+      for (int64_t j = b; j < e; ++j) d += uw[j];
+    } else {
+      d = (double)(e - b);
+    }
+    deg[i] = d;
+    keep[i] = e > b ? 1 : 0;
+  }
+}
+
+// Compacted node arrays (old ids, degrees, row starts).  With drop == 0
+// newid is the identity and every node is kept.
+__global__ void k_compact_nodes(const int64_t *rowptr, const double *deg, const uint8_t *keep,
+                                const int64_t *newid, int64_t n, int drop, int64_t nnz,
+                                int64_t n_out, int64_t *rowptr_out, double *deg_out,
+                                int64_t *old_id) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (drop && !keep[i]) continue;
+    const int64_t j = drop ? newid[i] : i;
+    rowptr_out[j] = rowptr[i];
+    deg_out[j] = deg[i];
+    old_id[j] = i;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rowptr_out[n_out] = nnz;
+}
+
+__global__ void k_scale(const double *deg, int64_t n, int kind, double *scale, double *diag,
+                        float *scale32, float *diag32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = deg[i];
+    double s, g;
+    if (kind == SLAQ_NORMALIZED) {
+      s = d > 0.0 ? 1.0 / sqrt(d) : 0.0;   // IEEE round-to-nearest sqrt and divide
+      g = d > 0.0 ? 1.0 : 0.0;
+    } else {
+      s = 1.0;
+      g = d;
+    }
+    scale[i] = s;
+    diag[i] = g;
+    scale32[i] = (float)s;
+    diag32[i] = (float)g;
+  }
+}
+
+// Row of every stored entry is needed for the values; the kernel walks rows.
+__global__ void k_values(const int64_t *rowptr, const uint64_t *ukey, const double *uw,
+                         const int64_t *newid, int drop, int cb, int64_t n, int kind,
+                         const double *scale, int32_t *colidx, double *vals, float *vals32) {
+  const uint64_t cmask = (cb >= 64) ? ~0ull : ((1ull << cb) - 1ull);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); i < n;
+       i += (int64_t)gridDim.x * (blockDim.x / 32)) {
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    const double si = scale[i];
+    for (int64_t j = b + (threadIdx.x & 31); j < e; j += 32) {
+      const int64_t c_old = (int64_t)(ukey[j] & cmask);
+      const int64_t c = drop ? newid[c_old] : c_old;
+      const double a = uw ? uw[j] : 1.0;
+      double v;
+      if (kind == SLAQ_NORMALIZED) v = -((a * si) * scale[c]);
+      else v = -a;
+      colidx[j] = (int32_t)c;
+      vals[j] = v;
+      if (vals32) vals32[j] = (float)v;
+    }
+  }
+}
+
+__global__ void k_heavy_flags(const int64_t *rowptr, int64_t n, int64_t heavy_degree,
+                              int32_t *is_heavy, int64_t *nchunk) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = rowptr[i + 1] - rowptr[i];
+    const bool h = d > heavy_degree;
+    is_heavy[i] = h ? 1 : 0;
+    nchunk[i] = h ? (d + kHeavyChunk - 1) / kHeavyChunk : 0;
+  }
+}
+
+__global__ void k_heavy_table(const int32_t *is_heavy, const int64_t *slot_of,
+                              const int64_t *chunk_of, const int64_t *nchunk, int64_t n,
+                              int64_t n_heavy, int64_t n_chunks, int32_t *heavy_row,
+                              int64_t *heavy_first, int32_t *chunk_slot) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!is_heavy[i]) continue;
+    const int64_t slot = slot_of[i];
+    heavy_row[slot] = (int32_t)i;
+    heavy_first[slot] = chunk_of[i];
+    for (int64_t c = 0; c < nchunk[i]; ++c) chunk_slot[chunk_of[i] + c] = (int32_t)slot;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) heavy_first[n_heavy] = n_chunks;
+}
+
+__global__ void k_max_degree(const double *deg, int64_t n, unsigned long long *mx) {
+  double local = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    local = fmax(local, deg[i]);
+  // non-negative doubles order like their bit patterns
+  atomicMax(mx, (unsigned long long)__double_as_longlong(local));
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+  int64_t b = ceil_div(std::max<int64_t>(n, 1), threads);
+  return (unsigned)std::min<int64_t>(b, 65535LL * 8);
+}
+
+template <typename T>
+int to_host(T *host, const T *dev, size_t count, cudaStream_t st) {
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(host, dev, count * sizeof(T), cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  return SLAQ_OK;
+}
+
+int bits_for(int64_t n) {
+  int b = 1;
+  while (b < 62 && (1ll << b) < n) ++b;
+  return b;
+}
+
+}  // namespace
+
+void graph_free(slaq_graph g) {
+  if (!g) return;
+  void *ptrs[] = {g->rowptr, g->colidx, g->vals, g->vals32, g->diag, g->scale, g->diag32,
+                  g->scale32, g->old_id, g->heavy_row, g->heavy_first, g->chunk_slot,
+                  g->heavy_count};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete g;
+}
+
+namespace {
+// Temporaries released on every exit path (stream-ordered frees).
+struct Temps {
+  cudaStream_t st;
+  std::vector<void *> ptrs;
+  explicit Temps(cudaStream_t s) : st(s) {}
+  template <typename T>
+  int get(T **p, size_t count) {
+    int r = dalloc_t(p, std::max<size_t>(count, 1), st);
+    if (r == SLAQ_OK) ptrs.push_back(*p);
+    return r;
+  }
+  ~Temps() {
+    for (void *p : ptrs) dfree(p, st);
+  }
+};
+
+template <typename T>
+int persistent(T **p, size_t count) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_error(SLAQ_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                     cudaGetErrorString(e));
+  }
+  return SLAQ_OK;
+}
+}  // namespace
+
+int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                    const double *weights, int kind, int flags, cudaStream_t st,
+                    slaq_graph *out) {
+  if (!out) return set_error(SLAQ_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 0 || m < 0) return set_error(SLAQ_EINVAL, "negative n_nodes or n_edges");
+  if (kind != SLAQ_NORMALIZED && kind != SLAQ_COMBINATORIAL)
+    return set_error(SLAQ_EINVAL, "unknown Laplacian kind %d", kind);
+  if (flags & ~SLAQ_DROP_ISOLATED) return set_error(SLAQ_EINVAL, "unknown flags 0x%x", flags);
+  if (n > 0x7fffffffLL) return set_error(SLAQ_EUNSUPPORTED, "n_nodes must be < 2^31");
+  if (m > 0 && (!src || !dst)) return set_error(SLAQ_EINVAL, "src/dst is NULL");
+  if (m > (1ll << 34)) return set_error(SLAQ_EUNSUPPORTED, "too many edges");
+  const bool drop = (flags & SLAQ_DROP_ISOLATED) != 0;
+  const bool weighted = weights != nullptr;
+  ProfScope prof(SLAQ_PROF_BUILD, st);
+  Temps tmp(st);
+
+  // 1. validate
+  if (m > 0) {
+    int32_t *bad = nullptr;
+    SLAQ_TRY(tmp.get(&bad, 1));
+    SLAQ_CHECK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+    ++tl_launches;
+    k_validate<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, n, bad);
+    SLAQ_CHECK_LAUNCH("validate");
+    int32_t hbad = 0;
+    SLAQ_TRY(to_host(&hbad, bad, 1, st));
+    if (hbad & 1) return set_error(SLAQ_EINVAL, "edge endpoint outside [0, n_nodes)");
+    if (hbad & 2) return set_error(SLAQ_EINVAL, "edge weights must be positive");
+  }
+
+  // 2. emit and sort
+  const int cb = bits_for(n);
+  uint64_t *k0 = nullptr, *k1 = nullptr;
+  double *p0 = nullptr, *p1 = nullptr;
+  unsigned long long *counter = nullptr;
+  SLAQ_TRY(tmp.get(&k0, 2 * m));
+  SLAQ_TRY(tmp.get(&k1, 2 * m));
+  if (weighted) {
+    SLAQ_TRY(tmp.get(&p0, 2 * m));
+    SLAQ_TRY(tmp.get(&p1, 2 * m));
+  }
+  SLAQ_TRY(tmp.get(&counter, 1));
+  SLAQ_CHECK_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+  if (m > 0) {
+    ++tl_launches;
+    k_emit<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, cb, k0, p0, counter);
+    SLAQ_CHECK_LAUNCH("emit");
+  }
+  unsigned long long hm2 = 0;
+  SLAQ_TRY(to_host(&hm2, counter, 1, st));
+  const int64_t m2 = (int64_t)hm2;
+  {
+    uint64_t *ka = k0, *kb = k1;
+    double *pa = p0, *pb = p1;
+    SLAQ_TRY(radix_sort(&ka, &kb, weighted ? &pa : nullptr, &pb, m2, 2 * cb, st));
+    k0 = ka;
+    k1 = kb;
+    p0 = pa;
+    p1 = pb;
+  }
+
+  // 3. merge duplicates, rows
+  uint8_t *first = nullptr;
+  int64_t *upos = nullptr, *d_total = nullptr;
+  SLAQ_TRY(tmp.get(&first, m2));
+  SLAQ_TRY(tmp.get(&upos, m2));
+  SLAQ_TRY(tmp.get(&d_total, 1));
+  if (m2 > 0) {
+    ++tl_launches;
+    k_first_flags<<<grid_for(m2, 256), 256, 0, st>>>(k0, m2, first);
+    SLAQ_CHECK_LAUNCH("first_flags");
+  }
+  SLAQ_TRY(exclusive_scan(first, m2, upos, d_total, st));
+  int64_t nnz = 0;
+  SLAQ_TRY(to_host(&nnz, d_total, 1, st));
+  uint64_t *ukey = k1;  // the sort's spare buffer
+  double *uw = weighted ? p1 : nullptr;
+  if (m2 > 0) {
+    ++tl_launches;
+    k_unique<<<grid_for(m2, 256), 256, 0, st>>>(k0, weighted ? p0 : nullptr, m2, first, upos,
+                                                ukey, uw);
+    SLAQ_CHECK_LAUNCH("unique");
+  }
+  int64_t *rowptr_full = nullptr;
+  double *deg_full = nullptr;
+  uint8_t *keep = nullptr;
+  SLAQ_TRY(tmp.get(&rowptr_full, n + 1));
+  SLAQ_TRY(tmp.get(&deg_full, n));
+  SLAQ_TRY(tmp.get(&keep, n));
+  ++tl_launches;
+  k_rowptr<<<grid_for(nnz + 1, 256), 256, 0, st>>>(ukey, nnz, cb, n, rowptr_full);
+  SLAQ_CHECK_LAUNCH("rowptr");
+  if (n > 0) {
+    ++tl_launches;
+    k_degree<<<grid_for(n, 256), 256, 0, st>>>(rowptr_full, uw, n, deg_full, keep);
+    SLAQ_CHECK_LAUNCH("degree");
+  }
+
+  // 4. isolated nodes, renumbering
+  int64_t *newid = nullptr;
+  SLAQ_TRY(tmp.get(&newid, n));
+  SLAQ_TRY(exclusive_scan(keep, n, newid, d_total, st));
+  int64_t n_nonisolated = 0;
+  SLAQ_TRY(to_host(&n_nonisolated, d_total, 1, st));
+  const int64_t n_out = drop ? n_nonisolated : n;
+
+  slaq_graph g = new slaq_graph_s();
+  struct Guard {
+    slaq_graph *g;
+    ~Guard() {
+      if (*g) graph_free(*g);
+    }
+  } guard{&g};
+  SLAQ_CHECK_CUDA(cudaGetDevice(&g->device));
+  g->n_input = n;
+  g->n = n_out;
+  g->nnz = nnz;
+  g->kind = kind;
+  g->flags = flags;
+  g->weighted = weighted;
+  SLAQ_TRY(persistent(&g->rowptr, n_out + 1));
+  SLAQ_TRY(persistent(&g->colidx, nnz));
+  SLAQ_TRY(persistent(&g->vals, nnz));
+  if (weighted) SLAQ_TRY(persistent(&g->vals32, nnz));
+  SLAQ_TRY(persistent(&g->diag, n_out));
+  SLAQ_TRY(persistent(&g->scale, n_out));
+  SLAQ_TRY(persistent(&g->diag32, n_out));
+  SLAQ_TRY(persistent(&g->scale32, n_out));
+  SLAQ_TRY(persistent(&g->old_id, n_out));
+  double *deg = nullptr;
+  SLAQ_TRY(tmp.get(&deg, n_out));
+  ++tl_launches;
+  k_compact_nodes<<<grid_for(n, 256), 256, 0, st>>>(rowptr_full, deg_full, keep, newid, n,
+                                                    drop ? 1 : 0, nnz, n_out, g->rowptr, deg,
+                                                    g->old_id);
+  SLAQ_CHECK_LAUNCH("compact_nodes");
+  if (n_out > 0) {
+    ++tl_launches;
+    k_scale<<<grid_for(n_out, 256), 256, 0, st>>>(deg, n_out, kind, g->scale, g->diag,
+                                                  g->scale32, g->diag32);
+    SLAQ_CHECK_LAUNCH("scale");
+    ++tl_launches;
+    k_values<<<grid_for(n_out * 32, 256), 256, 0, st>>>(g->rowptr, ukey, uw, newid,
+                                                        drop ? 1 : 0, cb, n_out, kind, g->scale,
+                                                        g->colidx, g->vals, g->vals32);
+    SLAQ_CHECK_LAUNCH("values");
+  }
+
+  // trace and spectral bound
+  if (kind == SLAQ_NORMALIZED) {
+    g->trace = (double)n_nonisolated;
+    g->bound = 2.0;
+  } else {
+    std::vector<double> hdeg(n_out);
+    if (n_out > 0) SLAQ_TRY(to_host(hdeg.data(), deg, n_out, st));
+    double s = 0.0, c = 0.0, mx = 0.0;   // Neumaier-compensated sum of degrees
+    for (double d : hdeg) {
+      double t = s + d;
+      c += std::fabs(s) >= std::fabs(d) ? (s - t) + d : (d - t) + s;
+      s = t;
+      mx = std::max(mx, d);
+    }
+    g->trace = s + c;
+    g->bound = 2.0 * mx;
+  }
+
+  // 5. SpMM schedule for heavy rows
+  g->heavy_degree = 4 * kHeavyChunk;
+  if (n_out > 0) {
+    int32_t *is_heavy = nullptr;
+    int64_t *nchunk = nullptr, *slot_of = nullptr, *chunk_of = nullptr;
+    SLAQ_TRY(tmp.get(&is_heavy, n_out));
+    SLAQ_TRY(tmp.get(&nchunk, n_out));
+    SLAQ_TRY(tmp.get(&slot_of, n_out));
+    SLAQ_TRY(tmp.get(&chunk_of, n_out));
+    ++tl_launches;
+    k_heavy_flags<<<grid_for(n_out, 256), 256, 0, st>>>(g->rowptr, n_out, g->heavy_degree,
+                                                        is_heavy, nchunk);
+    SLAQ_CHECK_LAUNCH("heavy_flags");
+    SLAQ_TRY(exclusive_scan(is_heavy, n_out, slot_of, d_total, st));
+    SLAQ_TRY(to_host(&g->n_heavy, d_total, 1, st));
+    SLAQ_TRY(exclusive_scan(nchunk, n_out, chunk_of, d_total, st));
+    SLAQ_TRY(to_host(&g->n_chunks, d_total, 1, st));
+    if (g->n_heavy > 0) {
+      SLAQ_TRY(persistent(&g->heavy_row, g->n_heavy));
+      SLAQ_TRY(persistent(&g->heavy_first, g->n_heavy + 1));
+      SLAQ_TRY(persistent(&g->chunk_slot, g->n_chunks));
+      SLAQ_TRY(persistent(&g->heavy_count, g->n_heavy));
+      SLAQ_CHECK_CUDA(cudaMemsetAsync(g->heavy_count, 0, g->n_heavy * sizeof(uint32_t), st));
+      ++tl_launches;
+      k_heavy_table<<<grid_for(n_out, 256), 256, 0, st>>>(is_heavy, slot_of, chunk_of, nchunk,
+                                                          n_out, g->n_heavy, g->n_chunks,
+                                                          g->heavy_row, g->heavy_first,
+                                                          g->chunk_slot);
+      SLAQ_CHECK_LAUNCH("heavy_table");
+    }
+  }
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  *out = g;
+  g = nullptr;  // ownership passed to the caller
+  return SLAQ_OK;
+}
+
+}  // namespace slaq

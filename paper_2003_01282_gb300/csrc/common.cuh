@@ -1,0 +1,158 @@
+// Internal declarations shared by the libslaq translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+
+#include "slaq.h"
+
+namespace slaq {
+
+// ------------------------------------------------------------------ errors
+int set_error(int status, const char *fmt, ...);
+int cuda_status(cudaError_t e, const char *what);
+
+#define SLAQ_CHECK_CUDA(call)                                             \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) return ::slaq::cuda_status(e_, #call);         \
+  } while (0)
+
+#define SLAQ_CHECK_LAUNCH(name)                                           \
+  do {                                                                    \
+    cudaError_t e_ = cudaPeekAtLastError();                               \
+    if (e_ != cudaSuccess) return ::slaq::cuda_status(e_, name);          \
+  } while (0)
+
+#define SLAQ_TRY(call)                                                    \
+  do {                                                                    \
+    int st_ = (call);                                                     \
+    if (st_ != SLAQ_OK) return st_;                                       \
+  } while (0)
+
+int device_check();        // SLAQ_OK on a compute-capability 10.3 device
+
+// Profiler (api.cu): CUDA events around a kernel class on its launch
+// stream, and kernel launch counts (every launch site bumps tl_launches).
+extern thread_local int64_t tl_launches;
+void prof_begin(int cat, cudaStream_t st);
+void prof_end(int cat, cudaStream_t st, int64_t launches);
+struct ProfScope {
+  int cat;
+  cudaStream_t st;
+  int64_t start;
+  ProfScope(int c, cudaStream_t s) : cat(c), st(s), start(tl_launches) { prof_begin(c, s); }
+  ~ProfScope() { prof_end(cat, st, tl_launches - start); }
+};
+int num_sms();             // streaming multiprocessors of the current device
+
+// stream-ordered device allocation (the device's default memory pool)
+int dalloc(void **p, size_t bytes, cudaStream_t st);
+void dfree(void *p, cudaStream_t st);
+
+template <typename T>
+inline int dalloc_t(T **p, size_t count, cudaStream_t st) {
+  return dalloc(reinterpret_cast<void **>(p), count * sizeof(T), st);
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// --------------------------------------------------------- precision forms
+// Basis element type TB and work type TW of each form.
+//   FP64: TB = double, TW = double
+//   FP32: TB = float,  TW = float
+//   BF16: TB = bf16,   TW = float
+// Every thread owns one 16-byte vector of a basis row: VE = 16/sizeof(TB)
+// probe columns.  The row stride `ld` (elements) makes a basis row a whole
+// number of 32-byte sectors.
+inline int basis_bytes(int precision) { return precision == SLAQ_FP64 ? 8 : (precision == SLAQ_FP32 ? 4 : 2); }
+inline int work_bytes(int precision) { return precision == SLAQ_FP64 ? 8 : 4; }
+inline int row_ld(int nv, int precision) {
+  int per_sector = 32 / basis_bytes(precision);
+  return (int)ceil_div(nv, per_sector) * per_sector;
+}
+inline int vec_elems(int precision) { return 16 / basis_bytes(precision); }
+
+// ------------------------------------------------------------ graph handle
+constexpr int kHeavyChunk = 512;   // nnz per work item of a split (heavy) row
+
+}  // namespace slaq
+
+struct slaq_graph_s {
+  int device = -1;
+  int64_t n_input = 0;   // n_nodes given at build time
+  int64_t n = 0;         // kept nodes n'
+  int64_t nnz = 0;       // stored off-diagonal entries
+  int kind = 0;
+  int flags = 0;
+  bool weighted = false;
+  double trace = 0.0;    // tr(L)
+  double bound = 0.0;    // Gershgorin bound of the spectrum
+  int64_t *rowptr = nullptr;   // [n+1]
+  int32_t *colidx = nullptr;   // [nnz]
+  double *vals = nullptr;      // [nnz] off-diagonal values (FP64)
+  float *vals32 = nullptr;     // [nnz] FP32 copy (weighted graphs only)
+  double *diag = nullptr;      // [n]
+  double *scale = nullptr;     // [n]
+  float *diag32 = nullptr;     // [n]
+  float *scale32 = nullptr;    // [n]
+  int64_t *old_id = nullptr;   // [n]
+  // SpMM schedule for rows with more than kHeavyDegree entries: each such
+  // row is split into chunks of kHeavyChunk entries.
+  int64_t heavy_degree = 0;
+  int64_t n_heavy = 0;               // heavy rows
+  int64_t n_chunks = 0;              // chunks over all heavy rows
+  int32_t *heavy_row = nullptr;      // [n_heavy] row id
+  int64_t *heavy_first = nullptr;    // [n_heavy+1] first chunk of each heavy row
+  int32_t *chunk_slot = nullptr;     // [n_chunks] heavy slot of each chunk
+  uint32_t *heavy_count = nullptr;   // [n_heavy] arrival counters (kept zero between launches)
+};
+
+struct slaq_krylov_s {
+  int device = -1;
+  int nv = 0, s = 0, ld = 0, precision = 0, reorth = 1;
+  int graph_id = 0;
+  uint64_t seed = 0;
+  int64_t n = 0;          // n' of the last run
+  int64_t n_cap = 0;      // rows the workspace holds
+  int64_t chunk_cap = 0;  // heavy-row partial rows the workspace holds
+  int kind = 0;
+  double trace = 0.0, bound = 0.0, tol = 0.0;
+  int G = 0;              // row blocks of the reduction kernels
+  void *U = nullptr;      // [s][n_cap][ld] basis (TB)
+  void *Z = nullptr;      // [n_cap][ld] L u_k (TW)
+  void *P = nullptr;      // [chunk_cap][ld] partial sums of split rows (TW)
+  double *part = nullptr; // [G][s][ld] per-block partial sums
+  double *dsum = nullptr; // [s][ld] reduced dot products
+  double *coef = nullptr; // [s][ld] Gram-Schmidt coefficients
+  double *nu2 = nullptr;  // [s][ld] squared norms of the stored basis vectors
+  double *alpha = nullptr;  // [nv][s]
+  double *beta = nullptr;   // [nv][s]
+  int32_t *m = nullptr;     // [nv]
+  double *theta = nullptr;  // [nv][s]
+  double *tau2 = nullptr;   // [nv][s]
+  int32_t *status = nullptr;  // [1] device-side error flags
+};
+
+namespace slaq {
+// internal entry points (definitions in build.cu, lanczos.cu, quad.cu)
+int build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges, int64_t n_nodes,
+                    const double *weights, int kind, int flags, cudaStream_t st,
+                    slaq_graph *out);
+void graph_free(slaq_graph g);
+int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
+                int reorth, cudaStream_t st, slaq_krylov *inout);
+void krylov_free(slaq_krylov k);
+int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st);
+int run_ritz(slaq_krylov k, cudaStream_t st);
+int trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *se,
+               double *per_probe, cudaStream_t st);
+int trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im, double *se_re,
+               double *se_im, cudaStream_t st);
+int trace_vnge(slaq_krylov k, double *out, double *se, double *per_probe, cudaStream_t st);
+int distance(const double *a, const double *b, int nt, int kind, double *out, cudaStream_t st);
+}  // namespace slaq

@@ -1,0 +1,197 @@
+// Gauss rule per probe and the Hutchinson estimate of Eq. slq for the heat
+// trace (Eq. heat-trace), the wave trace and the VNGE (Definition 1,
+// Sec. 2.1); spectral distances between descriptors (Sec. 4.2).
+// All FP64.  Probe sums run in probe order, so results are deterministic.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "tridiag.cuh"
+
+namespace slaq {
+namespace {
+
+constexpr int kMaxS = 64;
+constexpr int kMaxNv = 512;
+
+__global__ void k_ritz(const double *__restrict__ alpha, const double *__restrict__ beta,
+                       const int32_t *__restrict__ mm, int nv, int s, double *__restrict__ theta,
+                       double *__restrict__ tau2, int32_t *status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nv) return;
+  double d[kMaxS], e[kMaxS], w[kMaxS];
+  const int m = mm[p];
+  for (int i = 0; i < m; ++i) d[i] = alpha[p * s + i];
+  for (int i = 0; i + 1 < m; ++i) e[i] = beta[p * s + i];
+  if (tridiag_gauss(d, e, w, m) != 0) atomicOr(status, 1);
+  for (int i = 0; i < s; ++i) {
+    theta[p * s + i] = i < m ? d[i] : 0.0;
+    tau2[p * s + i] = i < m ? w[i] : 0.0;
+  }
+}
+
+struct NeumaierD {
+  double s = 0.0, c = 0.0;
+  __device__ void add(double x) {
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ double value() const { return s + c; }
+};
+
+// mean and standard error over nv values held in shared memory (thread 0)
+__device__ void mean_se(const double *g, int nv, double *mean_out, double *se_out) {
+  NeumaierD acc;
+  for (int p = 0; p < nv; ++p) acc.add(g[p]);
+  const double mean = acc.value() / nv;
+  double se = nan("");
+  if (nv > 1) {
+    NeumaierD sq;
+    for (int p = 0; p < nv; ++p) {
+      const double dv = g[p] - mean;
+      sq.add(dv * dv);
+    }
+    se = sqrt(sq.value() / (nv - 1) / nv);
+  }
+  *mean_out = mean;
+  if (se_out) *se_out = se;
+}
+
+// FUN 0: exp(-t theta); FUN 1: cos(t theta); FUN 2: -sin(t theta)
+template <int FUN>
+__device__ __forceinline__ double fval(double t, double th) {
+  if (FUN == 0) return exp(-t * th);
+  if (FUN == 1) return cos(t * th);
+  return -sin(t * th);
+}
+
+// One block per time value: g_p = n' sum_k tau2 f(t theta_k) for every probe.
+template <int FUN>
+__global__ void k_trace_t(const double *__restrict__ theta, const double *__restrict__ tau2,
+                          const int32_t *__restrict__ mm, int nv, int s, double n,
+                          const double *__restrict__ t, int nt, double *out, double *se,
+                          double *per_probe) {
+  __shared__ double g[kMaxNv];
+  const int ti = blockIdx.x;
+  const double tv = t[ti];
+  for (int p = threadIdx.x; p < nv; p += blockDim.x) {
+    double acc = 0.0;
+    const int m = mm[p];
+    for (int k = 0; k < m; ++k) acc += tau2[p * s + k] * fval<FUN>(tv, theta[p * s + k]);
+    g[p] = n * acc;
+    if (per_probe) per_probe[(int64_t)p * nt + ti] = n * acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mean_se(g, nv, out + ti, se ? se + ti : nullptr);
+}
+
+// VNGE: f(theta) = -(theta/c) ln(theta/c) for theta > 0, else 0.
+__global__ void k_vnge(const double *__restrict__ theta, const double *__restrict__ tau2,
+                       const int32_t *__restrict__ mm, int nv, int s, double n, double c,
+                       double *out, double *se, double *per_probe) {
+  __shared__ double g[kMaxNv];
+  for (int p = threadIdx.x; p < nv; p += blockDim.x) {
+    double acc = 0.0;
+    const int m = mm[p];
+    for (int k = 0; k < m; ++k) {
+      const double th = theta[p * s + k];
+      if (th > 0.0 && c > 0.0) {
+        const double x = th / c;
+        acc += tau2[p * s + k] * (-x * log(x));
+      }
+    }
+    g[p] = n * acc;
+    if (per_probe) per_probe[p] = n * acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mean_se(g, nv, out, se);
+}
+
+__global__ void k_distance(const double *a, const double *b, int len, int absdiff, double *out) {
+  __shared__ double ps[256], pc[256];
+  NeumaierD acc;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const double d = a[i] - b[i];
+    acc.add(d * d);
+  }
+  ps[threadIdx.x] = acc.s;
+  pc[threadIdx.x] = acc.c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (absdiff) {
+      out[0] = fabs(a[0] - b[0]);
+    } else {
+      NeumaierD tot;
+      for (int i = 0; i < (int)blockDim.x; ++i) {
+        tot.add(ps[i]);
+        tot.add(pc[i]);
+      }
+      out[0] = sqrt(tot.value());
+    }
+  }
+}
+
+}  // namespace
+
+int run_ritz(slaq_krylov K, cudaStream_t st) {
+  ProfScope prof(SLAQ_PROF_RITZ, st);
+  SLAQ_CHECK_CUDA(cudaMemsetAsync(K->status, 0, sizeof(int32_t), st));
+  ++tl_launches;
+  k_ritz<<<(unsigned)ceil_div(K->nv, 64), 64, 0, st>>>(K->alpha, K->beta, K->m, K->nv, K->s,
+                                                       K->theta, K->tau2, K->status);
+  SLAQ_CHECK_LAUNCH("ritz");
+  return SLAQ_OK;
+}
+
+int trace_heat(slaq_krylov K, const double *t, int nt, double *out, double *se, double *per_probe,
+               cudaStream_t st) {
+  if (nt < 1 || !t || !out) return set_error(SLAQ_EINVAL, "heat trace needs t, nt >= 1 and out");
+  ProfScope prof(SLAQ_PROF_TRACE, st);
+  ++tl_launches;
+  k_trace_t<0><<<nt, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, (double)K->n, t, nt,
+                                   out, se, per_probe);
+  SLAQ_CHECK_LAUNCH("trace_heat");
+  return SLAQ_OK;
+}
+
+int trace_wave(slaq_krylov K, const double *t, int nt, double *re, double *im, double *se_re,
+               double *se_im, cudaStream_t st) {
+  if (nt < 1 || !t || !re || !im) return set_error(SLAQ_EINVAL, "wave trace needs t, nt, re, im");
+  ProfScope prof(SLAQ_PROF_TRACE, st);
+  ++tl_launches;
+  k_trace_t<1><<<nt, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, (double)K->n, t, nt, re,
+                                   se_re, nullptr);
+  ++tl_launches;
+  k_trace_t<2><<<nt, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, (double)K->n, t, nt, im,
+                                   se_im, nullptr);
+  SLAQ_CHECK_LAUNCH("trace_wave");
+  return SLAQ_OK;
+}
+
+int trace_vnge(slaq_krylov K, double *out, double *se, double *per_probe, cudaStream_t st) {
+  if (!out) return set_error(SLAQ_EINVAL, "vnge needs out");
+  ProfScope prof(SLAQ_PROF_TRACE, st);
+  ++tl_launches;
+  k_vnge<<<1, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, (double)K->n, K->trace, out, se,
+                            per_probe);
+  SLAQ_CHECK_LAUNCH("trace_vnge");
+  return SLAQ_OK;
+}
+
+int distance(const double *a, const double *b, int nt, int kind, double *out, cudaStream_t st) {
+  if (!a || !b || !out) return set_error(SLAQ_EINVAL, "distance needs a, b and out");
+  int len;
+  if (kind == SLAQ_DIST_HEAT) len = nt;
+  else if (kind == SLAQ_DIST_WAVE) len = 2 * nt;
+  else if (kind == SLAQ_DIST_VNGE) len = 1;
+  else return set_error(SLAQ_EINVAL, "unknown distance kind %d", kind);
+  if (len < 1) return set_error(SLAQ_EINVAL, "nt must be >= 1");
+  ProfScope prof(SLAQ_PROF_DIST, st);
+  ++tl_launches;
+  k_distance<<<1, 256, 0, st>>>(a, b, len, kind == SLAQ_DIST_VNGE ? 1 : 0, out);
+  SLAQ_CHECK_LAUNCH("distance");
+  return SLAQ_OK;
+}
+
+}  // namespace slaq

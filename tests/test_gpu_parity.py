@@ -1,0 +1,294 @@
+"""GPU path against the CPU oracle, through the C ABI.
+
+Bars: CSR, renumbering and probes bit-exact; FP64 Lanczos coefficients,
+Gauss rules and descriptors within relative 1e-10 per entry of the oracle run
+with the same probes; FP32 / BF16-basis forms within relative 1e-4 (heat,
+wave real part) and 1e-3 (VNGE) of the FP64 GPU run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import descriptors as odesc
+from oracle import distance as odist
+from oracle import probes as oprobes
+from oracle.laplacian import COMBINATORIAL, NORMALIZED, build_laplacian
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2003_01282_gb300 import slaq  # noqa: E402
+from paper_2003_01282_gb300.build import build  # noqa: E402
+
+RTOL64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build()
+    slaq.lib()
+    assert slaq.device_check() == 0, slaq.last_error()
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def gpu_graph(src, dst, n, kind=NORMALIZED, drop=False, weights=None):
+    k = slaq.NORMALIZED if kind == NORMALIZED else slaq.COMBINATORIAL
+    w = None if weights is None else dev(weights, torch.float64)
+    return slaq.build_laplacian(dev(src, torch.int32), dev(dst, torch.int32), n, weights=w, kind=k,
+                                flags=slaq.DROP_ISOLATED if drop else 0)
+
+
+def check_csr(g, lap):
+    info = g.info
+    assert info["n"] == lap.n and info["nnz"] == lap.nnz
+    assert info["trace"] == lap.trace
+    ex = {k: v.cpu().numpy() for k, v in slaq.graph_export(g).items()}
+    assert np.array_equal(ex["rowptr"], lap.rowptr)
+    assert np.array_equal(ex["colidx"], lap.colidx)
+    assert np.array_equal(ex["vals"].view(np.uint64), lap.vals.view(np.uint64))
+    assert np.array_equal(ex["diag"].view(np.uint64), lap.diag.view(np.uint64))
+    assert np.array_equal(ex["scale"].view(np.uint64), lap.scale.view(np.uint64))
+    assert np.array_equal(ex["old_id"], lap.old_id)
+
+
+GRAPHS = {
+    "ba2000": lambda: synth.barabasi_albert(2000, 4, seed=0),
+    "rmat13": lambda: synth.rmat(13, 16 << 13, seed=3),
+    "islands": lambda: synth.disjoint_union(synth.erdos_renyi(300, 0.03, 1), synth.cycle(17),
+                                            synth.star(40), extra_isolated=9),
+    "k9": lambda: synth.complete(9),
+    "star30": lambda: synth.star(30),
+    "k35": lambda: synth.complete_bipartite(3, 5),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("kind", [NORMALIZED, COMBINATORIAL])
+@pytest.mark.parametrize("drop", [False, True])
+def test_csr_bit_exact(name, kind, drop):
+    s, d, n = GRAPHS[name]()
+    lap = build_laplacian(s, d, n, kind=kind, drop_isolated=drop)
+    g = gpu_graph(s, d, n, kind, drop)
+    check_csr(g, lap)
+
+
+def test_csr_dirty_input_and_weights():
+    s, d, n = synth.barabasi_albert(700, 3, seed=4)
+    rng = np.random.default_rng(0)
+    # self-loops, reversed and repeated pairs, random order
+    s2 = np.concatenate([s, d[:300], s[:50], np.arange(20)]).astype(np.int32)
+    d2 = np.concatenate([d, s[:300], d[:50], np.arange(20)]).astype(np.int32)
+    perm = rng.permutation(s2.size)
+    s2, d2 = s2[perm], d2[perm]
+    w = rng.uniform(0.1, 3.0, s2.size)
+    for kind in (NORMALIZED, COMBINATORIAL):
+        check_csr(gpu_graph(s2, d2, n, kind), build_laplacian(s2, d2, n, kind=kind))
+        check_csr(gpu_graph(s2, d2, n + 5, kind, drop=True, weights=w),
+                  build_laplacian(s2, d2, n + 5, weights=w, kind=kind, drop_isolated=True))
+
+
+def test_csr_empty_and_invalid():
+    e = np.zeros(0, np.int32)
+    g = gpu_graph(e, e, 5)
+    assert g.info["n"] == 5 and g.info["nnz"] == 0
+    g = gpu_graph(e, e, 5, drop=True)
+    assert g.info["n"] == 0
+    with pytest.raises(slaq.SlaqError) as ei:
+        slaq.lanczos(g, 4, 5, 0)
+    assert ei.value.status == 1
+    with pytest.raises(slaq.SlaqError) as ei:
+        gpu_graph(np.array([0, 7], np.int32), np.array([1, 2], np.int32), 5)
+    assert ei.value.status == 1
+    with pytest.raises(slaq.SlaqError):
+        gpu_graph(np.array([-1], np.int32), np.array([1], np.int32), 5)
+
+
+def test_csr_rmat_scale20_bit_exact():
+    """The R-MAT 2^20 / 16M-edge workload's CSR (isolated nodes dropped)."""
+    s, d, n = synth.rmat(20, 16 << 20, seed=1)
+    lap = build_laplacian(s, d, n, drop_isolated=True)
+    check_csr(gpu_graph(s, d, n, drop=True), lap)
+
+
+@pytest.mark.parametrize("nv,seed,gid", [(1, 0, 0), (10, 5, 0), (100, 2**64 - 1, 7), (37, 123, 65535)])
+def test_probes_bit_exact(nv, seed, gid):
+    s, d, n = GRAPHS["islands"]()
+    g = gpu_graph(s, d, n, drop=True)
+    lap = build_laplacian(s, d, n, drop_isolated=True)
+    got = slaq.probes(g, nv, seed, gid).cpu().numpy()
+    want = oprobes.probe_block(seed, gid, nv, lap.old_id)
+    assert np.array_equal(got, want)
+
+
+def _compare_runs(g, lap, nv, s, seed, precision=slaq.FP64, reorth=1, rtol=RTOL64, probes=None):
+    K = slaq.lanczos(g, nv, s, seed, precision=precision, reorth_passes=reorth)
+    alpha, beta, m = (x.cpu().numpy() for x in slaq.krylov_export(K))
+    theta, tau2 = (x.cpu().numpy() for x in slaq.ritz_export(K))
+    runs = odesc.slq_runs(lap, s, nv, seed, reorth_passes=reorth, probes=probes)
+    idx = list(range(nv)) if probes is None else list(probes)
+    for p, r in zip(idx, runs):
+        assert m[p] == r.m, (p, m[p], r.m)
+        np.testing.assert_allclose(alpha[p, :r.m], r.alpha, rtol=rtol, atol=rtol * lap.norm_bound())
+        np.testing.assert_allclose(beta[p, :r.m - 1], r.beta, rtol=rtol, atol=rtol * lap.norm_bound())
+        np.testing.assert_allclose(theta[p, :r.m], r.theta, rtol=rtol, atol=rtol * lap.norm_bound())
+        np.testing.assert_allclose(tau2[p, :r.m], r.tau2, rtol=1e3 * rtol, atol=rtol)
+    return K, runs
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
+
+
+@pytest.mark.parametrize("name,kind,drop,nv,s", [
+    ("ba2000", NORMALIZED, False, 10, 15),        # the small single-graph workload
+    ("ba2000", COMBINATORIAL, False, 7, 12),
+    ("rmat13", NORMALIZED, True, 17, 12),          # split (heavy) rows, ragged probe block
+    ("rmat13", COMBINATORIAL, True, 3, 10),
+    ("islands", NORMALIZED, False, 33, 10),        # isolated nodes kept: zero rows
+    ("k9", NORMALIZED, False, 6, 8),               # breakdown at m = 2
+    ("star30", COMBINATORIAL, False, 5, 8),        # breakdown at m = 3
+    ("k35", NORMALIZED, False, 4, 6),
+])
+def test_fp64_lanczos_and_descriptors(name, kind, drop, nv, s):
+    src, dst, n = GRAPHS[name]()
+    lap = build_laplacian(src, dst, n, kind=kind, drop_isolated=drop)
+    g = gpu_graph(src, dst, n, kind, drop)
+    K, runs = _compare_runs(g, lap, nv, s, seed=11)
+    t = synth.t_grid()
+    td = dev(t, torch.float64)
+    h, hse = (x.cpu().numpy() for x in slaq.trace_heat(K, td))
+    oh, ohse = odesc.heat_trace(runs, lap.n, t)
+    assert _rel(h, oh) < RTOL64
+    (wr, _), (wi, _) = slaq.trace_wave(K, td)
+    (owr, _), (owi, _) = odesc.wave_trace(runs, lap.n, t)
+    scale = lap.n
+    assert np.max(np.abs(wr.cpu().numpy() - owr)) < RTOL64 * scale
+    assert np.max(np.abs(wi.cpu().numpy() - owi)) < RTOL64 * scale
+    v, vse = slaq.trace_vnge(K)
+    ov, ovse = odesc.vnge(runs, lap.n, lap.trace)
+    assert abs(v.item() - ov) <= RTOL64 * abs(ov) + 1e-300
+    if nv > 1:
+        assert _rel(hse.cpu().numpy()[:64], ohse[:64]) < 1e-6
+    # h_0 = n' exactly up to rounding
+    h0, _ = slaq.trace_heat(K, dev([0.0], torch.float64))
+    assert abs(h0.item() - lap.n) < 1e-12 * lap.n
+
+
+def test_weighted_graph_values_form():
+    s, d, n = synth.barabasi_albert(600, 3, seed=8)
+    w = np.random.default_rng(3).uniform(0.5, 2.0, s.size)
+    for kind in (NORMALIZED, COMBINATORIAL):
+        lap = build_laplacian(s, d, n, weights=w, kind=kind)
+        g = gpu_graph(s, d, n, kind, weights=w)
+        _compare_runs(g, lap, 9, 10, seed=4)
+
+
+def test_cgs2_matches_oracle():
+    s, d, n = GRAPHS["ba2000"]()
+    lap = build_laplacian(s, d, n)
+    _compare_runs(gpu_graph(s, d, n), lap, 8, 15, seed=2, reorth=2)
+
+
+def test_heat_per_probe_and_stderr():
+    s, d, n = GRAPHS["ba2000"]()
+    lap = build_laplacian(s, d, n)
+    g = gpu_graph(s, d, n)
+    K = slaq.lanczos(g, 12, 10, 3)
+    t = np.array([0.01, 0.3, 5.0, 100.0])
+    out, se, pp = slaq.trace_heat(K, dev(t, torch.float64), per_probe=True)
+    pp = pp.cpu().numpy()
+    assert pp.shape == (12, 4)
+    assert np.allclose(pp.mean(0), out.cpu().numpy(), rtol=1e-13)
+    assert np.allclose(pp.std(0, ddof=1) / math.sqrt(12), se.cpu().numpy(), rtol=1e-10)
+    runs = odesc.slq_runs(lap, 10, 12, 3)
+    opp = odesc.per_probe(runs, odesc.heat_f(t)) * lap.n
+    assert _rel(pp, opp) < RTOL64
+
+
+def test_distance_matches_oracle():
+    rng = np.random.default_rng(0)
+    a, b = rng.normal(size=(2, 256))
+    out = slaq.distance(dev(a, torch.float64), dev(b, torch.float64), slaq.DIST_HEAT)
+    assert math.isclose(out.item(), odist.heat_distance(a, b), rel_tol=1e-14)
+    aw, bw = rng.normal(size=(2, 512))
+    out = slaq.distance(dev(aw, torch.float64), dev(bw, torch.float64), slaq.DIST_WAVE)
+    assert math.isclose(out.item(), odist.wave_distance(aw[:256], aw[256:], bw[:256], bw[256:]), rel_tol=1e-14)
+    out = slaq.distance(dev([3.846], torch.float64), dev([3.154], torch.float64), slaq.DIST_VNGE)
+    assert math.isclose(out.item(), 0.692, rel_tol=1e-12)
+
+
+def test_fig1_vnge_on_gpu(golden_dir):
+    """Fig. 1's printed VNGE from the GPU path (combinatorial Laplacian; the
+    Gauss rule is exact once s reaches the number of distinct eigenvalues)."""
+    import os
+    for fname, printed in (("karate_fig1.txt", 3.154), ("dolphins_fig1.txt", 3.846)):
+        s, d, n = synth.read_edge_file(os.path.join(golden_dir, fname))
+        lap = build_laplacian(s, d, n, kind=COMBINATORIAL)
+        g = gpu_graph(s, d, n, COMBINATORIAL)
+        K = slaq.lanczos(g, 200, 12, 7)
+        v, se = slaq.trace_vnge(K)
+        runs = odesc.slq_runs(lap, 12, 200, 7)
+        ov, _ = odesc.vnge(runs, lap.n, lap.trace)
+        assert abs(v.item() - ov) <= RTOL64 * ov
+        assert abs(v.item() - printed) < 3 * se.item() + 5e-4
+
+
+@pytest.mark.parametrize("precision,h_tol,v_tol", [(slaq.FP32, 1e-4, 1e-3),
+                                                   (slaq.FP32_BF16BASIS, 1e-2, 1e-2)])
+def test_reduced_precision_forms_vs_fp64(precision, h_tol, v_tol):
+    s, d, n = GRAPHS["rmat13"]()
+    g = gpu_graph(s, d, n, drop=True)
+    t = dev(synth.t_grid(), torch.float64)
+    K64 = slaq.lanczos(g, 32, 15, 9, precision=slaq.FP64)
+    K = slaq.lanczos(g, 32, 15, 9, precision=precision)
+    h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
+    h = slaq.trace_heat(K, t)[0].cpu().numpy()
+    assert _rel(h, h64) < h_tol
+    v64 = slaq.trace_vnge(K64)[0].item()
+    v = slaq.trace_vnge(K)[0].item()
+    assert abs(v - v64) / abs(v64) < v_tol
+
+
+def test_workspace_reuse_and_host_call():
+    s, d, n = GRAPHS["ba2000"]()
+    g = gpu_graph(s, d, n)
+    t = synth.t_grid(32)
+    td = dev(t, torch.float64)
+    K = slaq.lanczos(g, 10, 15, 0)
+    h1 = slaq.trace_heat(K, td)[0].cpu().numpy()
+    s2, d2, n2 = synth.barabasi_albert(3000, 4, seed=5)
+    g2 = gpu_graph(s2, d2, n2)
+    slaq.lanczos(g2, 10, 15, 0, reuse=K)            # grows the workspace
+    slaq.lanczos(g, 10, 15, 0, reuse=K)             # back to the first graph
+    h2 = slaq.trace_heat(K, td)[0].cpu().numpy()
+    assert np.array_equal(h1, h2)
+    host = slaq.descriptors_host(s, d, n, t, nv=10, s=15, seed=0)
+    assert np.array_equal(host["heat"], h1)
+    with pytest.raises(slaq.SlaqError):
+        slaq.lanczos(g, 11, 15, 0, reuse=K)
+
+
+def test_config2_full_size_sampled_probes():
+    """R-MAT 2^20, 16M edges, isolated dropped, nv = 100, s = 20 in FP64 and
+    FP32, in the launch configuration the bench times; the oracle recomputes
+    two sampled probes one by one."""
+    s, d, n = synth.rmat(20, 16 << 20, seed=1)
+    lap = build_laplacian(s, d, n, drop_isolated=True)
+    g = gpu_graph(s, d, n, drop=True)
+    _compare_runs(g, lap, 100, 20, seed=1, probes=[0, 61])
+    t = dev(synth.t_grid(), torch.float64)
+    K64 = slaq.lanczos(g, 100, 20, 1, precision=slaq.FP64)
+    K32 = slaq.lanczos(g, 100, 20, 1, precision=slaq.FP32)
+    h64, h32 = (slaq.trace_heat(K, t)[0].cpu().numpy() for K in (K64, K32))
+    assert _rel(h32, h64) < 1e-4
+    v64, v32 = (slaq.trace_vnge(K)[0].item() for K in (K64, K32))
+    assert abs(v32 - v64) / v64 < 1e-3
