@@ -8,7 +8,8 @@
 //   3. merge duplicates (largest weight kept), rowptr from the sorted rows;
 //   4. degrees, optional removal of isolated nodes with order-preserving
 //      renumbering, scales s_i = 1/sqrt(d_i) and off-diagonal values;
-//   5. the SpMM schedule that splits rows of more than `heavy_degree`
+//   5. an execution copy with nodes renumbered by descending degree;
+//   6. the SpMM schedule that splits rows of more than `heavy_degree`
 //      entries into chunks.
 // The result is canonical (sorted columns, merged duplicates), so it equals
 // any correct builder's bit for bit.
@@ -424,13 +425,52 @@ __global__ void k_heavy_table(const int32_t *is_heavy, const int64_t *slot_of,
   if (blockIdx.x == 0 && threadIdx.x == 0) heavy_first[n_heavy] = n_chunks;
 }
 
-__global__ void k_max_degree(const double *deg, int64_t n, unsigned long long *mx) {
-  double local = 0.0;
+// Sort key of the execution order: descending entry count, then id.
+__global__ void k_perm_keys(const int64_t *rowptr, int64_t n, int cb, uint64_t *key) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    local = fmax(local, deg[i]);
-  // non-negative doubles order like their bit patterns
-  atomicMax(mx, (unsigned long long)__double_as_longlong(local));
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t cnt = (uint64_t)(rowptr[i + 1] - rowptr[i]);
+    key[i] = (((uint64_t)n - cnt) << cb) | (uint64_t)i;
+  }
+}
+
+__global__ void k_perm_index(const uint64_t *key, const int64_t *rowptr, int64_t n, int cb,
+                             int64_t *perm, int64_t *inv, int64_t *xcnt) {
+  const uint64_t mask = (1ull << cb) - 1ull;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (int64_t)(key[r] & mask);
+    perm[r] = i;
+    inv[i] = r;
+    xcnt[r] = rowptr[i + 1] - rowptr[i];
+  }
+}
+
+// Execution row r is canonical row perm[r]; columns renamed through inv.
+__global__ void k_perm_rows(const int64_t *rowptr, const int32_t *colidx, const double *vals,
+                            const float *vals32, const double *diag, const double *scale,
+                            const int64_t *old_id, const int64_t *perm, const int64_t *inv,
+                            int64_t n, const int64_t *xrowptr, int32_t *xcol, double *xvals,
+                            float *xvals32, double *xdiag, double *xscale, float *xdiag32,
+                            float *xscale32, int64_t *xold) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); r < n;
+       r += (int64_t)gridDim.x * (blockDim.x / 32)) {
+    const int64_t i = perm[r];
+    const int64_t b = rowptr[i], e = rowptr[i + 1], xb = xrowptr[r];
+    for (int64_t t = lane; t < e - b; t += 32) {
+      xcol[xb + t] = (int32_t)inv[colidx[b + t]];
+      xvals[xb + t] = vals[b + t];
+      if (xvals32) xvals32[xb + t] = vals32[b + t];
+    }
+    if (lane == 0) {
+      xdiag[r] = diag[i];
+      xscale[r] = scale[i];
+      xdiag32[r] = (float)diag[i];
+      xscale32[r] = (float)scale[i];
+      xold[r] = old_id[i];
+    }
+  }
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -457,7 +497,8 @@ void graph_free(slaq_graph g) {
   if (!g) return;
   void *ptrs[] = {g->rowptr, g->colidx, g->vals, g->vals32, g->diag, g->scale, g->diag32,
                   g->scale32, g->old_id, g->heavy_row, g->heavy_first, g->chunk_slot,
-                  g->heavy_count};
+                  g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32, g->x_diag, g->x_scale,
+                  g->x_diag32, g->x_scale32, g->x_old_id};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -660,7 +701,46 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
     g->bound = 2.0 * mx;
   }
 
-  // 5. SpMM schedule for heavy rows
+  // 5. execution copy in descending-degree order
+  SLAQ_TRY(persistent(&g->x_rowptr, n_out + 1));
+  SLAQ_TRY(persistent(&g->x_colidx, nnz));
+  SLAQ_TRY(persistent(&g->x_vals, nnz));
+  if (weighted) SLAQ_TRY(persistent(&g->x_vals32, nnz));
+  SLAQ_TRY(persistent(&g->x_diag, n_out));
+  SLAQ_TRY(persistent(&g->x_scale, n_out));
+  SLAQ_TRY(persistent(&g->x_diag32, n_out));
+  SLAQ_TRY(persistent(&g->x_scale32, n_out));
+  SLAQ_TRY(persistent(&g->x_old_id, n_out));
+  if (n_out > 0) {
+    const int pcb = bits_for(n_out);
+    uint64_t *pk0 = nullptr, *pk1 = nullptr;
+    int64_t *perm = nullptr, *inv = nullptr, *xcnt = nullptr;
+    SLAQ_TRY(tmp.get(&pk0, n_out));
+    SLAQ_TRY(tmp.get(&pk1, n_out));
+    SLAQ_TRY(tmp.get(&perm, n_out));
+    SLAQ_TRY(tmp.get(&inv, n_out));
+    SLAQ_TRY(tmp.get(&xcnt, n_out));
+    ++tl_launches;
+    k_perm_keys<<<grid_for(n_out, 256), 256, 0, st>>>(g->rowptr, n_out, pcb, pk0);
+    SLAQ_CHECK_LAUNCH("perm_keys");
+    SLAQ_TRY(radix_sort(&pk0, &pk1, nullptr, nullptr, n_out, pcb + bits_for(n_out + 1), st));
+    ++tl_launches;
+    k_perm_index<<<grid_for(n_out, 256), 256, 0, st>>>(pk0, g->rowptr, n_out, pcb, perm, inv, xcnt);
+    SLAQ_CHECK_LAUNCH("perm_index");
+    SLAQ_TRY(exclusive_scan(xcnt, n_out, g->x_rowptr, d_total, st));
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(g->x_rowptr + n_out, d_total, sizeof(int64_t),
+                                    cudaMemcpyDeviceToDevice, st));
+    ++tl_launches;
+    k_perm_rows<<<grid_for(n_out * 32, 256), 256, 0, st>>>(
+        g->rowptr, g->colidx, g->vals, g->vals32, g->diag, g->scale, g->old_id, perm, inv, n_out,
+        g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32, g->x_diag, g->x_scale, g->x_diag32,
+        g->x_scale32, g->x_old_id);
+    SLAQ_CHECK_LAUNCH("perm_rows");
+  } else {
+    SLAQ_CHECK_CUDA(cudaMemsetAsync(g->x_rowptr, 0, sizeof(int64_t), st));
+  }
+
+  // 6. SpMM schedule for heavy rows (execution order)
   g->heavy_degree = 4 * kHeavyChunk;
   if (n_out > 0) {
     int32_t *is_heavy = nullptr;
@@ -670,7 +750,7 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
     SLAQ_TRY(tmp.get(&slot_of, n_out));
     SLAQ_TRY(tmp.get(&chunk_of, n_out));
     ++tl_launches;
-    k_heavy_flags<<<grid_for(n_out, 256), 256, 0, st>>>(g->rowptr, n_out, g->heavy_degree,
+    k_heavy_flags<<<grid_for(n_out, 256), 256, 0, st>>>(g->x_rowptr, n_out, g->heavy_degree,
                                                         is_heavy, nchunk);
     SLAQ_CHECK_LAUNCH("heavy_flags");
     SLAQ_TRY(exclusive_scan(is_heavy, n_out, slot_of, d_total, st));
@@ -681,8 +761,6 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
       SLAQ_TRY(persistent(&g->heavy_row, g->n_heavy));
       SLAQ_TRY(persistent(&g->heavy_first, g->n_heavy + 1));
       SLAQ_TRY(persistent(&g->chunk_slot, g->n_chunks));
-      SLAQ_TRY(persistent(&g->heavy_count, g->n_heavy));
-      SLAQ_CHECK_CUDA(cudaMemsetAsync(g->heavy_count, 0, g->n_heavy * sizeof(uint32_t), st));
       ++tl_launches;
       k_heavy_table<<<grid_for(n_out, 256), 256, 0, st>>>(is_heavy, slot_of, chunk_of, nchunk,
                                                           n_out, g->n_heavy, g->n_chunks,

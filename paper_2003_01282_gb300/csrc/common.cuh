@@ -101,15 +101,26 @@ struct slaq_graph_s {
   float *diag32 = nullptr;     // [n]
   float *scale32 = nullptr;    // [n]
   int64_t *old_id = nullptr;   // [n]
-  // SpMM schedule for rows with more than kHeavyDegree entries: each such
-  // row is split into chunks of kHeavyChunk entries.
+  // Execution copy used by the Lanczos kernels: the same Laplacian with the
+  // nodes renumbered by descending entry count (ties by id), so that the
+  // most-gathered rows of the basis are contiguous and rows of similar cost
+  // run side by side.  The trace functions are permutation invariant; probe
+  // signs follow x_old_id, so they are those of the canonical order.
+  int64_t *x_rowptr = nullptr;  // [n+1]
+  int32_t *x_colidx = nullptr;  // [nnz]
+  double *x_vals = nullptr;     // [nnz]
+  float *x_vals32 = nullptr;    // [nnz] (weighted only)
+  double *x_diag = nullptr, *x_scale = nullptr;    // [n]
+  float *x_diag32 = nullptr, *x_scale32 = nullptr; // [n]
+  int64_t *x_old_id = nullptr;  // [n]
+  // SpMM schedule (execution order) for rows with more than heavy_degree
+  // entries: each such row is split into chunks of kHeavyChunk entries.
   int64_t heavy_degree = 0;
   int64_t n_heavy = 0;               // heavy rows
   int64_t n_chunks = 0;              // chunks over all heavy rows
   int32_t *heavy_row = nullptr;      // [n_heavy] row id
   int64_t *heavy_first = nullptr;    // [n_heavy+1] first chunk of each heavy row
   int32_t *chunk_slot = nullptr;     // [n_chunks] heavy slot of each chunk
-  uint32_t *heavy_count = nullptr;   // [n_heavy] arrival counters (kept zero between launches)
 };
 
 struct slaq_krylov_s {
@@ -122,20 +133,23 @@ struct slaq_krylov_s {
   int64_t chunk_cap = 0;  // heavy-row partial rows the workspace holds
   int kind = 0;
   double trace = 0.0, bound = 0.0, tol = 0.0;
-  int G = 0;              // row blocks of the reduction kernels
+  int G = 0;              // row blocks the partials buffer holds
+  int Gdots = 0;          // row blocks of the last dots launch
   void *U = nullptr;      // [s][n_cap][ld] basis (TB)
   void *Z = nullptr;      // [n_cap][ld] L u_k (TW)
   void *P = nullptr;      // [chunk_cap][ld] partial sums of split rows (TW)
-  double *part = nullptr; // [G][s][ld] per-block partial sums
-  double *dsum = nullptr; // [s][ld] reduced dot products
-  double *coef = nullptr; // [s][ld] Gram-Schmidt coefficients
-  double *nu2 = nullptr;  // [s][ld] squared norms of the stored basis vectors
+  double *part = nullptr; // [G][2][s][ld] per-block partial sums (dots, Gram column)
+  double *dsum = nullptr; // [s][ld] reduced dot products u_j^T z
+  double *coef = nullptr; // [s][ld] projection coefficients
+  double *gram = nullptr; // [s][s][ld] Gram matrix u_i^T u_j of the stored basis
   double *alpha = nullptr;  // [nv][s]
   double *beta = nullptr;   // [nv][s]
   int32_t *m = nullptr;     // [nv]
   double *theta = nullptr;  // [nv][s]
   double *tau2 = nullptr;   // [nv][s]
   int32_t *status = nullptr;  // [1] device-side error flags
+  uint32_t *hcount = nullptr; // [n_heavy * slices] arrival counters of split rows (kept zero)
+  int64_t hcount_cap = 0;
 };
 
 namespace slaq {

@@ -6,20 +6,24 @@
 // node i, probe p innermost, row stride ld), so the gather of neighbour j in
 // the SpMM reads one contiguous row of nv values.
 //
-// The basis is kept UNNORMALIZED (u_0 is the +-1 probe itself) with the
-// squared norms nu_j^2 = ||u_j||^2 tracked per probe; q_j = u_j / nu_j.
-// Step k, for every probe:
-//     z       = L u_k                                        (SpMM)
-//     d_j     = u_j^T z                    j = 0..k          (dots)
-//     alpha_k = d_k / nu_k^2  (= q_k^T L q_k)
-//     u_{k+1} = z - sum_j (d_j / nu_j^2) u_j                 (update)
-//     nu_{k+1}^2 = ||u_{k+1}||^2,  beta_k = nu_{k+1} / nu_k
-// u_{k+1} is nu_k times the vector the textbook order "three-term recurrence,
-// then one classical Gram-Schmidt pass over q_0..q_k" produces: both remove
-// the projection of L q_k on span{q_0..q_k}; they differ only by rounding.
-// Deferring the normalization saves one pass over the basis per step.
+// The basis is kept UNNORMALIZED (u_0 is the +-1 probe itself); q_j =
+// u_j / ||u_j||.  Step k, for every probe:
+//     z       = L u_k                                          (SpMM)
+//     d_j     = u_j^T z,  G_jk = u_j^T u_k      j = 0..k       (dots)
+//     x       = G^{-1} d  over the Gram matrix G of u_0..u_k    (solve)
+//     alpha_k = d_k / G_kk = q_k^T L q_k,  beta_{k-1} = sqrt(G_kk / G_{k-1,k-1})
+//     u_{k+1} = z - sum_j x_j u_j                              (update)
+// u_{k+1} is ||u_k|| times the vector that "three-term recurrence, then
+// Gram-Schmidt against q_0..q_k" produces: both remove the projection of
+// L q_k on span{q_0..q_k}.  Solving with the Gram matrix (accumulated in the
+// dots pass, which reads u_k anyway) makes that projection exact for the
+// stored, rounded basis, so orthogonality does not decay step by step (one
+// classical Gram-Schmidt pass would lose it by a factor (alpha+beta)/beta
+// per step).  Deferring the normalization saves one pass over the basis.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -33,22 +37,36 @@ template <>
 struct Form<SLAQ_FP64> {
   using TB = double;
   using TW = double;
-  static constexpr int VE = 2;
-  static constexpr int J = 8;  // basis vectors per dots block
+  static constexpr int VE = 2;  // probe columns per 16-byte basis vector
 };
 template <>
 struct Form<SLAQ_FP32> {
   using TB = float;
   using TW = float;
   static constexpr int VE = 4;
-  static constexpr int J = 8;
 };
 template <>
 struct Form<SLAQ_FP32_BF16BASIS> {
   using TB = __nv_bfloat16;
   using TW = float;
   static constexpr int VE = 8;
-  static constexpr int J = 4;
+};
+
+// Column slicing of a block of vectors [n][ld] (probe columns innermost):
+// stored as consecutive [n][width_s] blocks, slice s holding columns
+// [s*w, s*w + width_s), width_s = min(w, ld - s*w).  A slice of the basis is
+// then contiguous, so the SpMM's gathers of one slice stay within an
+// L2-sized footprint.  Offsets are in elements.
+struct Slc {
+  int64_t n;
+  int ld, w;
+  __host__ __device__ __forceinline__ int64_t base(int col, int &stride) const {
+    const int sl = col / w;
+    const int c0 = sl * w;
+    stride = min(w, ld - c0);
+    return (int64_t)sl * n * w + (col - c0);
+  }
+  __host__ __device__ __forceinline__ int nslices() const { return (ld + w - 1) / w; }
 };
 
 // 16-byte basis loads (read-only path) and stores, widened to TW.
@@ -143,6 +161,14 @@ __device__ __forceinline__ void stw(TW *p, const TW (&v)[VE]) {
   for (int i = 0; i < (int)(sizeof(TW) * VE / 16); ++i)
     reinterpret_cast<float4 *>(p)[i] = reinterpret_cast<const float4 *>(v)[i];
 }
+// streaming (evict-first) store: the SpMM output must not push the gathered
+// basis out of L2
+template <typename TW, int VE>
+__device__ __forceinline__ void stw_cs(TW *p, const TW (&v)[VE]) {
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(TW) * VE / 16); ++i)
+    __stcs(reinterpret_cast<float4 *>(p) + i, reinterpret_cast<const float4 *>(v)[i]);
+}
 
 // ------------------------------------------------------------ probe init
 __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
@@ -152,21 +178,26 @@ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
 }
 
 template <int P>
-__global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id, int64_t n, int ld,
-                             int nv, uint64_t seed, uint64_t graph_id) {
+__global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id, Slc S, int nv,
+                             uint64_t seed, uint64_t graph_id) {
   using TB = typename Form<P>::TB;
+  const int64_t n = S.n;
+  const int ld = S.ld;
   const int64_t total = n * ld;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx / ld;
     const int p = (int)(idx - i * ld);
+    int stride;
+    const int64_t cbase = S.base(p, stride);
+    const int64_t off = cbase + i * stride;
     float v = 0.0f;
     if (p < nv) {
       const uint64_t c = (graph_id << 48) | ((uint64_t)p << 32) | (uint64_t)old_id[i];
       const uint64_t z = splitmix64_mix(seed + 0x9E3779B97F4A7C15ull * (c + 1ull));
       v = (z >> 63) ? -1.0f : 1.0f;
     }
-    U0[idx] = (TB)v;
+    U0[off] = (TB)v;
   }
 }
 
@@ -183,9 +214,7 @@ __global__ void k_probe_export(double *out, const int64_t *old_id, int64_t n, in
   }
 }
 
-__global__ void k_init_scalars(double *nu2, double *alpha, double *beta, int32_t *m, int nv, int s,
-                               int ld, double n) {
-  for (int i = threadIdx.x; i < s * ld; i += blockDim.x) nu2[i] = (i < nv) ? n : 0.0;
+__global__ void k_init_scalars(double *alpha, double *beta, int32_t *m, int nv, int s) {
   for (int i = threadIdx.x; i < nv * s; i += blockDim.x) {
     alpha[i] = 0.0;
     beta[i] = 0.0;
@@ -201,7 +230,7 @@ template <int P, int MODE>
 __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
                                             const typename Form<P>::TW *__restrict__ vals,
                                             const typename Form<P>::TW *__restrict__ scale,
-                                            const typename Form<P>::TB *__restrict__ Ul, int ld,
+                                            const typename Form<P>::TB *__restrict__ Ul, int stride,
                                             int64_t b, int64_t e,
                                             typename Form<P>::TW (&acc)[Form<P>::VE]) {
   using TW = typename Form<P>::TW;
@@ -211,23 +240,23 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
     int c[4];
     TW w[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) c[q] = __ldg(col + j + q);
+    for (int q = 0; q < 4; ++q) c[q] = __ldcs(col + j + q);  // streamed: keep L2 for the basis
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      w[q] = MODE == 0 ? __ldg(scale + c[q]) : (MODE == 2 ? __ldg(vals + j + q) : TW(1));
+      w[q] = MODE == 0 ? __ldg(scale + c[q]) : (MODE == 2 ? __ldcs(vals + j + q) : TW(1));
     TW x[4][VE];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) ldb(Ul + (int64_t)c[q] * ld, x[q]);
+    for (int q = 0; q < 4; ++q) ldb(Ul + (int64_t)c[q] * stride, x[q]);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int v = 0; v < VE; ++v) acc[v] = fma(w[q], x[q][v], acc[v]);
   }
   for (; j < e; ++j) {
-    const int c = __ldg(col + j);
-    const TW w = MODE == 0 ? __ldg(scale + c) : (MODE == 2 ? __ldg(vals + j) : TW(1));
+    const int c = __ldcs(col + j);
+    const TW w = MODE == 0 ? __ldg(scale + c) : (MODE == 2 ? __ldcs(vals + j) : TW(1));
     TW x[VE];
-    ldb(Ul + (int64_t)c * ld, x);
+    ldb(Ul + (int64_t)c * stride, x);
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc[v] = fma(w, x[v], acc[v]);
   }
@@ -236,22 +265,25 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
 template <int P, int MODE>
 __device__ __forceinline__ void finish_row(int64_t row, const typename Form<P>::TW *diag,
                                            const typename Form<P>::TW *scale,
-                                           const typename Form<P>::TB *Ul, int ld,
+                                           const typename Form<P>::TB *Ul, int stride,
                                            typename Form<P>::TW (&acc)[Form<P>::VE],
                                            typename Form<P>::TW *zrow) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   TW y[VE];
-  ldb(Ul + row * ld, y);
+  ldb(Ul + row * stride, y);
   const TW g = diag[row];
   const TW sr = MODE == 0 ? scale[row] : TW(1);
   TW z[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v)
     z[v] = MODE == 2 ? fma(g, y[v], acc[v]) : fma(g, y[v], -sr * acc[v]);
-  stw<TW, VE>(zrow, z);
+  stw_cs<TW, VE>(zrow, z);
 }
 
+// Probe slice sl = blockIdx.x / bps, rows (blockIdx.x % bps) * R + team:
+// team of Vt = w / VE threads per row, each owning VE probe columns.  Blocks
+// run slice-major, so one slice of u_k is gathered at a time.
 template <int P, int MODE>
 __global__ void __launch_bounds__(256)
     k_spmm_light(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
@@ -259,25 +291,32 @@ __global__ void __launch_bounds__(256)
                  const typename Form<P>::TW *__restrict__ diag,
                  const typename Form<P>::TW *__restrict__ scale,
                  const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
-                 int64_t n, int V, int R, int ld, int64_t heavy_degree) {
+                 Slc S, int Vt, int R, int64_t bps, int64_t heavy_degree) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
-  const int team = threadIdx.x / V, lane = threadIdx.x - team * V;
+  const int sl = (int)(blockIdx.x / bps);
+  const int64_t rb = blockIdx.x - (int64_t)sl * bps;
+  const int team = threadIdx.x / Vt, lane = threadIdx.x - team * Vt;
   if (team >= R) return;
-  const int64_t row = (int64_t)blockIdx.x * R + team;
-  if (row >= n) return;
+  const int c = sl * S.w + lane * VE;
+  if (c >= S.ld) return;  // narrower last slice
+  const int64_t row = rb * R + team;
+  if (row >= S.n) return;
   const int64_t b = rowptr[row], e = rowptr[row + 1];
   if (e - b > heavy_degree) return;  // split rows: k_spmm_heavy
-  const auto *Ul = U + lane * VE;
+  int stride;
+  const int64_t off = S.base(c, stride);
+  const auto *Ul = U + off;
   TW acc[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v) acc[v] = TW(0);
-  gather_rows<P, MODE>(col, vals, scale, Ul, ld, b, e, acc);
-  finish_row<P, MODE>(row, diag, scale, Ul, ld, acc, Z + row * ld + lane * VE);
+  gather_rows<P, MODE>(col, vals, scale, Ul, stride, b, e, acc);
+  finish_row<P, MODE>(row, diag, scale, Ul, stride, acc, Z + off + row * stride);
 }
 
-// One chunk of a split row per block; the last block to finish a row sums
-// the chunk partials in chunk order (deterministic) and writes the row.
+// One (slice, chunk of a split row) per block, slice-major; the last block to
+// finish a row's slice sums the chunk partials in chunk order
+// (deterministic) and writes that slice of the row.
 template <int P, int MODE>
 __global__ void __launch_bounds__(256)
     k_spmm_heavy(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
@@ -287,11 +326,12 @@ __global__ void __launch_bounds__(256)
                  const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
                  typename Form<P>::TW *__restrict__ part, const int32_t *__restrict__ heavy_row,
                  const int64_t *__restrict__ heavy_first, const int32_t *__restrict__ chunk_slot,
-                 uint32_t *__restrict__ heavy_count, int V, int ld) {
+                 uint32_t *__restrict__ heavy_count, Slc S, int Vt, int64_t n_chunks) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   __shared__ int is_last;
-  const int64_t q = blockIdx.x;
+  const int sl = (int)(blockIdx.x / n_chunks);
+  const int64_t q = blockIdx.x - (int64_t)sl * n_chunks;
   const int slot = chunk_slot[q];
   const int64_t row = heavy_row[slot];
   const int64_t first = heavy_first[slot];
@@ -301,19 +341,23 @@ __global__ void __launch_bounds__(256)
   const int64_t b = rb + c * kHeavyChunk;
   const int64_t e = min(b + (int64_t)kHeavyChunk, re);
   const int lane = threadIdx.x;
-  const bool active = lane < V;
-  const auto *Ul = U + lane * VE;
+  const int cc0 = sl * S.w + lane * VE;
+  const bool active = lane < Vt && cc0 < S.ld;
+  int stride = 1;
+  const int64_t off = active ? S.base(cc0, stride) : 0;
+  const auto *Ul = U + off;
   if (active) {
     TW acc[VE];
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc[v] = TW(0);
-    gather_rows<P, MODE>(col, vals, scale, Ul, ld, b, e, acc);
-    stw<TW, VE>(part + q * ld + lane * VE, acc);
+    gather_rows<P, MODE>(col, vals, scale, Ul, stride, b, e, acc);
+    stw<TW, VE>(part + q * S.ld + cc0, acc);
   }
   __threadfence();
   __syncthreads();
+  uint32_t *counter = heavy_count + (int64_t)slot * S.nslices() + sl;
   if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(heavy_count + slot, 1u);
+    const unsigned prev = atomicAdd(counter, 1u);
     is_last = (prev == (unsigned)(nch - 1)) ? 1 : 0;
   }
   __syncthreads();
@@ -323,24 +367,24 @@ __global__ void __launch_bounds__(256)
     TW acc[VE];
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc[v] = TW(0);
-    for (int64_t cc = 0; cc < nch; ++cc) {
+    for (int64_t ch = 0; ch < nch; ++ch) {
       TW x[VE];
-      ldw_cg<TW, VE>(part + (first + cc) * ld + lane * VE, x);
+      ldw_cg<TW, VE>(part + (first + ch) * S.ld + cc0, x);
 #pragma unroll
       for (int v = 0; v < VE; ++v) acc[v] += x[v];
     }
-    finish_row<P, MODE>(row, diag, scale, Ul, ld, acc, Z + row * ld + lane * VE);
+    finish_row<P, MODE>(row, diag, scale, Ul, stride, acc, Z + off + row * stride);
   }
-  if (threadIdx.x == 0) heavy_count[slot] = 0u;  // ready for the next launch
+  if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch
 }
 
 // ------------------------------------------------------ compensated sums
-// FP64 form: plain FP64 accumulation per thread.  FP32 forms: Kahan
-// summation in FP32 per thread (sum, c); the true value is sum - c.
+// Per-thread running sums of chunk sums.  FP64 form: plain FP64.  FP32
+// forms: Kahan summation in FP32 (sum, c); the true value is sum - c.
 struct KahanF {
   float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add_prod(float a, float b) {
-    const float y = fmaf(a, b, -c);
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
     const float t = s + y;
     c = (t - s) - y;
     s = t;
@@ -349,7 +393,7 @@ struct KahanF {
 };
 struct PlainD {
   double s = 0.0;
-  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ double value() const { return s; }
 };
 template <typename TW>
@@ -374,150 +418,337 @@ struct Neumaier {
   __device__ __forceinline__ double value() const { return s + c; }
 };
 
-// Reduce one double per (team, column) over the block's teams, in team
-// order, and store it to out[col] for the block's VE columns of each lane.
-__device__ __forceinline__ void block_team_sum(double *sm, int V, int R, int VE, int team, int lane,
-                                               const double *mine, double *out) {
-  const int width = V * VE;
-  for (int v = 0; v < VE; ++v) sm[team * width + lane * VE + v] = mine[v];
-  __syncthreads();
-  if (team == 0) {
-    for (int v = 0; v < VE; ++v) {
-      Neumaier acc;
-      for (int t = 0; t < R; ++t) acc.add(sm[t * width + lane * VE + v]);
-      out[lane * VE + v] = acc.value();
-    }
+// ------------------------------------------------------------------ dots
+// Thread (x, y) of block (g, c) owns probe columns [x*VE, x*VE + VE) of basis
+// vector j = jfirst + c*Jb + y over the rows of row block g and accumulates
+//   d_j = u_j^T x          (x = z = L u_k, or u_{k+1} in the second pass)
+//   g_j = u_j^T u_k        (Gram column of the newest vector; WITH_G only)
+// Every (j, column) has a single owner, so no reduction inside the block.
+// The rows of x and u_k, which every y of a column needs, are staged tile by
+// tile in shared memory (cp.async, double buffered); only the u_j stream
+// comes from HBM per thread.  Sums are plain over a tile of kTile rows and
+// compensated across tiles.
+constexpr int kTile = 32;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// smem element loads of VE columns (16 or 32 bytes)
+__device__ __forceinline__ void lds(const double *p, double (&v)[2]) {
+  const double2 t = *reinterpret_cast<const double2 *>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+}
+__device__ __forceinline__ void lds(const float *p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4 *>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void lds(const float *p, float (&v)[8]) {
+  const float4 a = reinterpret_cast<const float4 *>(p)[0];
+  const float4 b = reinterpret_cast<const float4 *>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void lds(const __nv_bfloat16 *p, float (&v)[8]) {
+  const uint4 t = *reinterpret_cast<const uint4 *>(p);
+  const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = __uint_as_float(w[i] << 16);
+    v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
   }
-  __syncthreads();
 }
 
-// ------------------------------------------------------------------ dots
-// part[g][j][ld] = sum over the rows of block g of u_j[i][p] * x[i][p] for
-// j in [j0, j0 + J) with j <= jlast, where x is the work vector z (TW) or,
-// for the second Gram-Schmidt pass, the stored basis vector u_{k+1} (TB).
-template <int P, bool X_IS_BASIS>
-__global__ void __launch_bounds__(256)
-    k_dots(const typename Form<P>::TB *__restrict__ U, const void *__restrict__ Xv, int64_t n,
-           int64_t rows_per_block, int V, int R, int ld, int64_t ustride, int jfirst, int jlast,
-           int JC, double *__restrict__ part, int s) {
+// Copy rows [row0, row0 + nr) of a sliced [n][ld] block (element type T) to
+// shared memory as a dense [nr][ld] tile, 16 bytes per cp.async.
+template <typename T>
+__device__ __forceinline__ void stage_rows(T *dst, const T *src, const Slc &S, int64_t row0, int nr,
+                                           int tid, int nthr) {
+  constexpr int E = 16 / sizeof(T);
+  const int per_row = S.ld / E;
+  for (int q = tid; q < nr * per_row; q += nthr) {
+    const int r = q / per_row;
+    const int col = (q - r * per_row) * E;
+    int stride;
+    const int64_t cb = S.base(col, stride);
+    cp_async16(dst + r * S.ld + col, src + cb + (row0 + r) * stride);
+  }
+}
+
+template <int P, bool X_IS_BASIS, bool WITH_G>
+__global__ void __launch_bounds__(512)
+    k_dots(const typename Form<P>::TB *__restrict__ U, const void *__restrict__ Xv,
+           const typename Form<P>::TB *__restrict__ Uk, Slc S, int64_t rows_per_block,
+           int64_t ustride, int jfirst, int jlast, int Jb, double *__restrict__ part, int s) {
   using TB = typename Form<P>::TB;
   using TW = typename Form<P>::TW;
+  using TX = typename std::conditional<X_IS_BASIS, TB, TW>::type;
   constexpr int VE = Form<P>::VE;
-  constexpr int J = Form<P>::J;
   using A = typename Acc<TW>::type;
-  __shared__ double sm[256 * VE];
-  const int g = blockIdx.x / JC, jc = blockIdx.x - g * JC;
-  const int j0 = jfirst + jc * J;
-  const int team = threadIdx.x / V, lane = threadIdx.x - team * V;
-  const bool in_team = team < R;
-  A acc[J][VE];
-  if (in_team) {
-    const int64_t r0 = (int64_t)g * rows_per_block;
-    const int64_t r1 = min(n, r0 + rows_per_block);
-    for (int64_t row = r0 + team; row < r1; row += R) {
-      TW x[VE];
-      if (X_IS_BASIS) ldb(static_cast<const TB *>(Xv) + row * ld + lane * VE, x);
-      else ldw<TW, VE>(static_cast<const TW *>(Xv) + row * ld + lane * VE, x);
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int ld = S.ld;
+  TX *xs = reinterpret_cast<TX *>(dyn);                 // [2][kTile][ld]
+  TB *us = reinterpret_cast<TB *>(xs + 2 * kTile * ld);  // [2][kTile][ld]
+  const TX *X = static_cast<const TX *>(Xv);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const int g = blockIdx.x;
+  const int j = jfirst + (int)blockIdx.y * Jb + (int)threadIdx.y;
+  const bool active = j <= jlast;  // idle threads still stage and synchronize
+  const int col = threadIdx.x * VE;
+  const int64_t r0 = (int64_t)g * rows_per_block;
+  const int64_t r1 = min(S.n, r0 + rows_per_block);
+  const int ntile = (int)((r1 - r0 + kTile - 1) / kTile);
+  int stride;
+  const int64_t off = S.base(col, stride);
+  const TB *Uj = U + (int64_t)(active ? j : jfirst) * ustride + off;
+  A d[VE], gg[VE];
+  auto stage = [&](int t) {
+    const int64_t row0 = r0 + (int64_t)t * kTile;
+    const int nr = (int)min((int64_t)kTile, r1 - row0);
+    const int buf = t & 1;
+    stage_rows<TX>(xs + buf * kTile * ld, X, S, row0, nr, tid, nthr);
+    if (WITH_G) stage_rows<TB>(us + buf * kTile * ld, Uk, S, row0, nr, tid, nthr);
+  };
+  if (ntile > 0) stage(0);
+  cp_async_commit();
+  for (int t = 0; t < ntile; ++t) {
+    if (t + 1 < ntile) stage(t + 1);
+    cp_async_commit();
+    cp_async_wait1();  // tile t has landed
+    __syncthreads();
+    if (active) {
+      const int64_t row0 = r0 + (int64_t)t * kTile;
+      const int nr = (int)min((int64_t)kTile, r1 - row0);
+      const TX *xt = xs + (t & 1) * kTile * ld + col;
+      const TB *ut = us + (t & 1) * kTile * ld + col;
+      TW dc[VE], gc[VE];
 #pragma unroll
-      for (int jj = 0; jj < J; ++jj) {
-        if (j0 + jj <= jlast) {
-          TW u[VE];
-          ldb(U + (int64_t)(j0 + jj) * ustride + row * ld + lane * VE, u);
+      for (int v = 0; v < VE; ++v) {
+        dc[v] = TW(0);
+        gc[v] = TW(0);
+      }
+      int r = 0;
+      for (; r + 4 <= nr; r += 4) {
+        TW u[4][VE];
 #pragma unroll
-          for (int v = 0; v < VE; ++v) acc[jj][v].add_prod(u[v], x[v]);
+        for (int q = 0; q < 4; ++q) ldb(Uj + (row0 + r + q) * stride, u[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          TW x[VE];
+          lds(xt + (r + q) * ld, x);
+#pragma unroll
+          for (int v = 0; v < VE; ++v) dc[v] = fma(u[q][v], x[v], dc[v]);
+          if (WITH_G) {
+            TW w[VE];
+            lds(ut + (r + q) * ld, w);
+#pragma unroll
+            for (int v = 0; v < VE; ++v) gc[v] = fma(u[q][v], w[v], gc[v]);
+          }
         }
       }
+      for (; r < nr; ++r) {
+        TW u[VE], x[VE];
+        ldb(Uj + (row0 + r) * stride, u);
+        lds(xt + r * ld, x);
+#pragma unroll
+        for (int v = 0; v < VE; ++v) dc[v] = fma(u[v], x[v], dc[v]);
+        if (WITH_G) {
+          TW w[VE];
+          lds(ut + r * ld, w);
+#pragma unroll
+          for (int v = 0; v < VE; ++v) gc[v] = fma(u[v], w[v], gc[v]);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VE; ++v) {
+        d[v].add(dc[v]);
+        if (WITH_G) gg[v].add(gc[v]);
+      }
     }
+    __syncthreads();  // buffer t&1 is restaged at t+2
   }
-  const int t = in_team ? team : 0;
+  if (!active) return;
+  double *pd = part + (((int64_t)g * 2 + 0) * s + j) * ld + col;
 #pragma unroll
-  for (int jj = 0; jj < J; ++jj) {
-    if (j0 + jj > jlast) break;  // uniform over the block
-    double mine[VE];
+  for (int v = 0; v < VE; ++v) pd[v] = d[v].value();
+  if (WITH_G) {
+    double *pg = part + (((int64_t)g * 2 + 1) * s + j) * ld + col;
 #pragma unroll
-    for (int v = 0; v < VE; ++v) mine[v] = in_team ? acc[jj][v].value() : 0.0;
-    // threads outside the teams (blockDim = V*R exactly, so none) never write
-    block_team_sum(sm, V, R, VE, t, lane, mine,
-                   part + ((int64_t)g * s + (j0 + jj)) * ld);
+    for (int v = 0; v < VE; ++v) pg[v] = gg[v].value();
   }
 }
 
-// Sum the G block partials of rows [jfirst, jfirst + jcount) of the dot
-// products; turn them into Gram-Schmidt coefficients c_j = d_j / nu_j^2 for
-// probes still running at step k (0 for stopped probes and padding), and
-// alpha_k = c_k.  Block (32, 8): x = column, y strides over blocks.
+// dynamic shared memory of a dots block
+inline size_t dots_smem(int precision, int ld, bool x_is_basis) {
+  const int bx = x_is_basis ? basis_bytes(precision) : work_bytes(precision);
+  return (size_t)2 * kTile * ld * (bx + basis_bytes(precision));
+}
+
+// Sum the G block partials (Neumaier, fixed order) of d_j and, with_g, of
+// g_j for j in [jfirst, jfirst + jcount).  d goes to dsum[j][p]; g_j is the
+// Gram entry (j, k), stored symmetrically in gram[j][k][p] and gram[k][j][p].
+// Block (32, kRedY): x = column, y strides over the blocks' partials.
+constexpr int kRedY = 32;
 __global__ void k_dot_reduce(const double *__restrict__ part, int G, int s, int ld, int jfirst,
-                             int jcount, int k, const double *__restrict__ nu2,
-                             const int32_t *__restrict__ m, int nv, double *__restrict__ coef,
-                             double *__restrict__ alpha, int write_alpha) {
-  __shared__ double ss[8][33], sc[8][33];
+                             int jcount, int k, int with_g, double *__restrict__ dsum,
+                             double *__restrict__ gram) {
+  __shared__ double ss[kRedY][33], sc[kRedY][33];
+  const int ncol = jcount * ld;
   const int col = blockIdx.x * 32 + threadIdx.x;
-  const bool valid = col < jcount * ld;
+  const int which = blockIdx.y;  // 0: d, 1: g
+  const bool valid = col < ncol && (which == 0 || with_g);
   const int j = jfirst + (valid ? col / ld : 0);
   const int p = valid ? col % ld : 0;
   Neumaier acc;
   if (valid)
-    for (int g = threadIdx.y; g < G; g += 8) acc.add(part[((int64_t)g * s + j) * ld + p]);
+    for (int g = threadIdx.y; g < G; g += kRedY) acc.add(part[(((int64_t)g * 2 + which) * s + j) * ld + p]);
   ss[threadIdx.y][threadIdx.x] = acc.s;
   sc[threadIdx.y][threadIdx.x] = acc.c;
   __syncthreads();
   if (threadIdx.y == 0 && valid) {
     Neumaier tot;
-    for (int y = 0; y < 8; ++y) {
+    for (int y = 0; y < kRedY; ++y) {
       tot.add(ss[y][threadIdx.x]);
       tot.add(sc[y][threadIdx.x]);
     }
-    const double d = tot.value();
-    const bool running = p < nv && m[p] > k;
-    const double c = running ? d / nu2[j * ld + p] : 0.0;
-    coef[j * ld + p] = c;
-    if (write_alpha && j == k && running) alpha[p * s + k] = c;
+    const double v = tot.value();
+    if (which == 0) {
+      dsum[j * ld + p] = v;
+    } else {
+      gram[((int64_t)j * s + k) * ld + p] = v;
+      gram[((int64_t)k * s + j) * ld + p] = v;
+    }
   }
 }
 
+// ---------------------------------------------------------------- solve
+// One block per probe (lane 0 computes).  With G the Gram matrix of the
+// stored basis u_0..u_k and d_j = u_j^T z, the coefficients of the projection
+// of z on span(u_0..u_k) are x = G^{-1} d (Cholesky of the unit-diagonal
+// scaling of G).  With an exactly orthogonal basis x_j = d_j / ||u_j||^2,
+// which is classical Gram-Schmidt; solving with G keeps the new vector
+// orthogonal to the stored basis to working precision even when the stored
+// vectors are rounded (BF16), like a second Gram-Schmidt pass.
+// first_pass: also records nu_k^2 = G_kk, beta_{k-1} = nu_k / nu_{k-1}
+// (stopping the probe with m = k if beta_{k-1} <= tol_abs) and
+// alpha_k = d_k / nu_k^2.  need_coef == 0 on the last step.
+constexpr int kMaxS = 64;
+__global__ void k_solve(const double *__restrict__ dsum, const double *__restrict__ gram, int k,
+                        int s, int ld, int nv, int first_pass, int need_coef, double tol_abs,
+                        int32_t *__restrict__ m, double *__restrict__ alpha,
+                        double *__restrict__ beta, double *__restrict__ coef) {
+  __shared__ double A[kMaxS * kMaxS];  // Gram block, factored in place (lower)
+  __shared__ double y[kMaxS], sc[kMaxS];
+  __shared__ int run_flag;
+  const int p = blockIdx.x;
+  const int K1 = k + 1;
+  const int lane = threadIdx.x;
+  if (lane == 0) {
+    bool running = p < nv && m[p] > k;
+    if (running && first_pass) {
+      const double nk = gram[((int64_t)k * s + k) * ld + p];
+      if (k > 0) {
+        const double b = sqrt(nk) / sqrt(gram[((int64_t)(k - 1) * s + (k - 1)) * ld + p]);
+        if (b <= tol_abs) {
+          m[p] = k;
+          running = false;
+        } else {
+          beta[p * s + k - 1] = b;
+        }
+      }
+      if (running) alpha[p * s + k] = dsum[k * ld + p] / nk;
+    }
+    run_flag = running ? 1 : 0;
+  }
+  __syncthreads();
+  if (!need_coef) return;
+  if (!run_flag) {
+    for (int j = lane; j < K1; j += blockDim.x) coef[j * ld + p] = 0.0;
+    return;
+  }
+  for (int j = lane; j < K1; j += blockDim.x) {
+    sc[j] = 1.0 / sqrt(gram[((int64_t)j * s + j) * ld + p]);
+    y[j] = dsum[j * ld + p];
+  }
+  __syncthreads();
+  for (int e = lane; e < K1 * K1; e += blockDim.x) {
+    const int i = e / K1, j = e - i * K1;
+    if (j <= i) A[i * K1 + j] = gram[((int64_t)i * s + j) * ld + p] * sc[i] * sc[j];
+  }
+  __syncthreads();
+  if (lane == 0) {
+    // Cholesky of Ghat = D^-1/2 G D^-1/2 (unit diagonal), in place
+    for (int i = 0; i < K1; ++i) {
+      for (int j = 0; j <= i; ++j) {
+        double a = A[i * K1 + j];
+        for (int q = 0; q < j; ++q) a -= A[i * K1 + q] * A[j * K1 + q];
+        if (i == j) A[i * K1 + i] = sqrt(fmax(a, 1e-300));
+        else A[i * K1 + j] = a / A[j * K1 + j];
+      }
+    }
+    // Ghat xhat = D^-1/2 d, x = D^-1/2 xhat
+    for (int i = 0; i < K1; ++i) {
+      double a = y[i] * sc[i];
+      for (int q = 0; q < i; ++q) a -= A[i * K1 + q] * y[q];
+      y[i] = a / A[i * K1 + i];
+    }
+    for (int i = K1 - 1; i >= 0; --i) {
+      double a = y[i];
+      for (int q = i + 1; q < K1; ++q) a -= A[q * K1 + i] * y[q];
+      y[i] = a / A[i * K1 + i];
+    }
+  }
+  __syncthreads();
+  for (int j = lane; j < K1; j += blockDim.x) coef[j * ld + p] = y[j] * sc[j];
+}
+
 // ---------------------------------------------------------------- update
-// u_{k+1} = x - sum_{j<=k} coef_j * u_j, with x = z (first pass) or the
-// stored u_{k+1} (second pass, in place); stopped probes get 0.  Also the
-// per-block partial sums of u_{k+1}^2 of the rounded stored values.
+// u_{k+1} = x - sum_{j<=k} coef_j u_j with x = z (first pass) or the stored
+// u_{k+1} (second pass, in place), rounded to the basis type; stopped probes
+// and padding columns get 0.  A pure streaming pass over the basis.
 template <int P, bool SECOND>
 __global__ void __launch_bounds__(256)
     k_update(const typename Form<P>::TB *__restrict__ U, const typename Form<P>::TW *__restrict__ Z,
-             typename Form<P>::TB *Unext, int64_t n, int64_t rows_per_block, int V, int R, int ld,
+             typename Form<P>::TB *Unext, Slc S, int64_t rows_per_block, int V, int R,
              int64_t ustride, int k, const double *__restrict__ coef,
-             const int32_t *__restrict__ m, int nv, double *__restrict__ part, int s) {
-  using TB = typename Form<P>::TB;
+             const int32_t *__restrict__ m, int nv) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
-  using A = typename Acc<TW>::type;
   extern __shared__ __align__(16) unsigned char dyn[];
-  TW *cf = reinterpret_cast<TW *>(dyn);                         // [(k+1) * ld]
-  double *sm = reinterpret_cast<double *>(cf + (k + 1) * ld);   // [V*R*VE]
-  for (int i = threadIdx.x; i < (k + 1) * ld; i += blockDim.x) {
-    const int p = i % ld;
-    const bool running = p < nv && m[p] > k;
-    cf[i] = running ? (TW)coef[i] : TW(0);
-  }
+  const int ld = S.ld;
+  TW *cf = reinterpret_cast<TW *>(dyn);  // [(k+1) * ld]
+  for (int i = threadIdx.x; i < (k + 1) * ld; i += blockDim.x) cf[i] = (TW)coef[i];
   __syncthreads();
-  const int g = blockIdx.x;
   const int team = threadIdx.x / V, lane = threadIdx.x - team * V;
+  if (team >= R) return;
   bool keep[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v) {
     const int p = lane * VE + v;
     keep[v] = p < nv && m[p] > k;
   }
-  A acc[VE];
-  const int64_t r0 = (int64_t)g * rows_per_block;
-  const int64_t r1 = min(n, r0 + rows_per_block);
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min(S.n, r0 + rows_per_block);
+  int stride;
+  const int64_t off = S.base(lane * VE, stride);
   for (int64_t row = r0 + team; row < r1; row += R) {
+    const int64_t o = off + row * stride;
     TW x[VE];
-    if (SECOND) ldb_rw(Unext + row * ld + lane * VE, x);
-    else ldw<TW, VE>(Z + row * ld + lane * VE, x);
+    if (SECOND) ldb_rw(Unext + o, x);
+    else ldw<TW, VE>(Z + o, x);
     int j = 0;
     for (; j + 2 <= k + 1; j += 2) {
       TW u0[VE], u1[VE];
-      ldb(U + (int64_t)j * ustride + row * ld + lane * VE, u0);
-      ldb(U + (int64_t)(j + 1) * ustride + row * ld + lane * VE, u1);
+      ldb(U + (int64_t)j * ustride + o, u0);
+      ldb(U + (int64_t)(j + 1) * ustride + o, u1);
       const TW *c0 = cf + j * ld + lane * VE;
       const TW *c1 = c0 + ld;
 #pragma unroll
@@ -528,7 +759,7 @@ __global__ void __launch_bounds__(256)
     }
     for (; j <= k; ++j) {
       TW u0[VE];
-      ldb(U + (int64_t)j * ustride + row * ld + lane * VE, u0);
+      ldb(U + (int64_t)j * ustride + o, u0);
       const TW *c0 = cf + j * ld + lane * VE;
 #pragma unroll
       for (int v = 0; v < VE; ++v) x[v] = fma(-c0[v], u0[v], x[v]);
@@ -537,66 +768,76 @@ __global__ void __launch_bounds__(256)
     for (int v = 0; v < VE; ++v)
       if (!keep[v]) x[v] = TW(0);
     TW r[VE];
-    stb(Unext + row * ld + lane * VE, x, r);
-#pragma unroll
-    for (int v = 0; v < VE; ++v) acc[v].add_prod(r[v], r[v]);
-  }
-  double mine[VE];
-#pragma unroll
-  for (int v = 0; v < VE; ++v) mine[v] = acc[v].value();
-  block_team_sum(sm, V, R, VE, team, lane, mine, part + (int64_t)g * s * ld);
-}
-
-// nu_{k+1}^2 from the block partials; beta_k = nu_{k+1} / nu_k; a probe
-// whose beta_k <= tol * bound stops with m = k + 1.
-__global__ void k_norm_reduce(const double *__restrict__ part, int G, int s, int ld, int k,
-                              double *__restrict__ nu2, int32_t *__restrict__ m, int nv,
-                              double *__restrict__ beta, double tol_abs) {
-  __shared__ double ss[8][33], sc[8][33];
-  const int p = blockIdx.x * 32 + threadIdx.x;
-  const bool valid = p < ld;
-  Neumaier acc;
-  if (valid)
-    for (int g = threadIdx.y; g < G; g += 8) acc.add(part[(int64_t)g * s * ld + p]);
-  ss[threadIdx.y][threadIdx.x] = acc.s;
-  sc[threadIdx.y][threadIdx.x] = acc.c;
-  __syncthreads();
-  if (threadIdx.y == 0 && valid) {
-    Neumaier tot;
-    for (int y = 0; y < 8; ++y) {
-      tot.add(ss[y][threadIdx.x]);
-      tot.add(sc[y][threadIdx.x]);
-    }
-    const double nn = tot.value();
-    double keep_nu2 = 0.0;
-    if (p < nv && m[p] > k) {
-      const double b = sqrt(nn) / sqrt(nu2[k * ld + p]);
-      if (b <= tol_abs) {
-        m[p] = k + 1;
-      } else {
-        beta[p * s + k] = b;
-        keep_nu2 = nn;
-      }
-    }
-    nu2[(k + 1) * ld + p] = keep_nu2;
+    stb(Unext + o, x, r);
   }
 }
 
 // ------------------------------------------------------------ host side
 struct Geometry {
-  int V, R, threads;
-  int64_t rows_per_block;
-  int G;
+  int V, R, threads;      // teams of V threads, R rows per pass (update)
+  Slc S;                  // probe slicing of the basis and work vectors
+  int Vt, Rt, tthreads;   // SpMM: Vt threads per row and slice, Rt rows per block
+  int sms;
+  int Jb;                 // basis vectors per dots block
+  int Gmax;               // most row blocks of the dots kernel (partials buffer rows)
+  int64_t upd_rows;       // rows per update block
+  int Gupd;               // update blocks
 };
+
+// Row blocks of the dots kernel for blocks of `threads` threads: enough to
+// fill every SM with 2048 threads, at most Gmax, at least 64 rows each.
+inline void dots_grid(const Geometry &g, int64_t n, int threads, size_t smem, int *G,
+                      int64_t *rows) {
+  const int64_t by_threads = 2048 / threads;
+  const int64_t by_smem = smem ? (int64_t)(220 * 1024) / (int64_t)smem : by_threads;
+  const int64_t per_sm = std::max<int64_t>(1, std::min(by_threads, by_smem));
+  int64_t want = (int64_t)g.sms * per_sm;
+  want = std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)g.Gmax, ceil_div(n, 64)}));
+  *rows = ceil_div(n, want);
+  *G = (int)ceil_div(n, *rows);
+}
+
+// Slice width: the whole row when n * ld fits the L2 budget; otherwise the
+// widest multiple of a 32-byte sector whose slice fits (no slicing if even
+// one sector per row does not).
+constexpr int64_t kL2Budget = 48ll << 20;
+int slice_width(int precision, int ld, int64_t n) {
+  const int b = basis_bytes(precision);
+  const int sector = 32 / b;
+  // SLAQ_SLICE_BYTES: bytes of a row per slice (a multiple of 32), or -1 for
+  // no slicing; unset or 0 chooses by the L2 budget.
+  static const long forced = [] {
+    const char *e = getenv("SLAQ_SLICE_BYTES");
+    return e ? atol(e) : 0L;
+  }();
+  if (forced <= 0) return ld;  // measured: unsliced gathers are faster on the R-MAT workload
+  {
+    const int w = (int)std::max<long>(sector, forced / 32 * 32 / b);
+    return std::min(w, ld);
+  }
+  if (n * ld * (int64_t)b <= kL2Budget) return ld;
+  const int64_t w = kL2Budget / (n * b) / sector * sector;
+  if (w < sector) return ld;
+  return (int)std::min<int64_t>(w, ld);
+}
 
 Geometry geometry(int precision, int ld, int64_t n, int sms) {
   Geometry g;
+  g.sms = sms;
+  g.S.n = n;
+  g.S.ld = ld;
+  g.S.w = slice_width(precision, ld, n);
+  g.Vt = g.S.w / vec_elems(precision);
+  g.Rt = std::max(1, 256 / g.Vt);
+  g.tthreads = g.Vt * g.Rt;
   g.V = ld / vec_elems(precision);
   g.R = std::max(1, 256 / g.V);
   g.threads = g.V * g.R;
-  int64_t G = std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 1024)), 4LL * sms);
-  g.rows_per_block = std::max<int64_t>(1, ceil_div(n, G));
-  g.G = (int)std::max<int64_t>(1, ceil_div(n, g.rows_per_block));
+  g.Jb = std::max(1, std::min(64, 512 / g.V));
+  g.Gmax = 8 * sms;
+  int64_t Gu = std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 8LL * g.R)), 16LL * sms);
+  g.upd_rows = std::max<int64_t>(1, ceil_div(n, Gu));
+  g.Gupd = (int)ceil_div(n, g.upd_rows);
   return g;
 }
 
@@ -610,27 +851,31 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
   TW *Z = static_cast<TW *>(K->Z);
   const TW *vals, *diag, *scale;
   if constexpr (P == SLAQ_FP64) {
-    vals = gr->vals;
-    diag = gr->diag;
-    scale = gr->scale;
+    vals = gr->x_vals;
+    diag = gr->x_diag;
+    scale = gr->x_scale;
   } else {
-    vals = gr->vals32;
-    diag = gr->diag32;
-    scale = gr->scale32;
+    vals = gr->x_vals32;
+    diag = gr->x_diag32;
+    scale = gr->x_scale32;
   }
   const int mode = gr->weighted ? 2 : (gr->kind == SLAQ_NORMALIZED ? 0 : 1);
-  const unsigned blocks = (unsigned)ceil_div(n, geo.R);
-  const int hthreads = (int)ceil_div(geo.V, 32) * 32;
-#define SLAQ_SPMM_CASE(MODE)                                                                  \
-  ++tl_launches;                                                                              \
-  k_spmm_light<P, MODE><<<blocks, geo.threads, 0, st>>>(gr->rowptr, gr->colidx, vals, diag,   \
-                                                        scale, Uk, Z, n, geo.V, geo.R, K->ld, \
-                                                        gr->heavy_degree);                    \
-  if (gr->n_chunks > 0) ++tl_launches;                                                        \
-  if (gr->n_chunks > 0)                                                                       \
-    k_spmm_heavy<P, MODE><<<(unsigned)gr->n_chunks, hthreads, 0, st>>>(                       \
-        gr->rowptr, gr->colidx, vals, diag, scale, Uk, Z, static_cast<TW *>(K->P),            \
-        gr->heavy_row, gr->heavy_first, gr->chunk_slot, gr->heavy_count, geo.V, K->ld);
+  const int ns = geo.S.nslices();
+  const int64_t bps = ceil_div(n, geo.Rt);
+  const unsigned blocks = (unsigned)(ns * bps);
+  const unsigned hblocks = (unsigned)(ns * gr->n_chunks);
+  const int hthreads = (int)ceil_div(geo.Vt, 32) * 32;
+#define SLAQ_SPMM_CASE(MODE)                                                                    \
+  ++tl_launches;                                                                                \
+  k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(gr->x_rowptr, gr->x_colidx, vals, diag, \
+                                                         scale, Uk, Z, geo.S, geo.Vt, geo.Rt,   \
+                                                         bps, gr->heavy_degree);                \
+  if (gr->n_chunks > 0) {                                                                       \
+    ++tl_launches;                                                                              \
+    k_spmm_heavy<P, MODE><<<hblocks, hthreads, 0, st>>>(                                        \
+        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, static_cast<TW *>(K->P),          \
+        gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, geo.S, geo.Vt, gr->n_chunks); \
+  }
   if (mode == 0) {
     SLAQ_SPMM_CASE(0)
   } else if (mode == 1) {
@@ -643,26 +888,50 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
   return SLAQ_OK;
 }
 
+// Dot products of basis vectors jfirst..jlast with X (z, or u_{k+1} when
+// x_is_basis), plus the Gram column of u_k when with_g.
 template <int P>
-int dots(slaq_krylov K, const Geometry &geo, int64_t n, int jfirst, int jlast, bool x_is_basis,
-         const void *X, cudaStream_t st) {
+int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int jlast,
+         bool x_is_basis, bool with_g, const void *X, cudaStream_t st) {
   ProfScope prof(SLAQ_PROF_DOTS, st);
   using TB = typename Form<P>::TB;
-  constexpr int J = Form<P>::J;
-  const int JC = (int)ceil_div(jlast - jfirst + 1, J);
-  const unsigned blocks = (unsigned)(geo.G * JC);
+  const int jcount = jlast - jfirst + 1;
+  const int Jb = std::min(jcount, geo.Jb);
+  int G;
+  int64_t rows;
+  dots_grid(geo, n, geo.V * Jb, dots_smem(P, K->ld, x_is_basis), &G, &rows);
+  K->Gdots = G;
+  const dim3 grid(G, (unsigned)ceil_div(jcount, Jb));
+  const dim3 block(geo.V, Jb);
   const TB *U = static_cast<const TB *>(K->U);
+  const TB *Uk = U + (int64_t)k * n * K->ld;
   const int64_t ustride = n * K->ld;
+  const size_t smem = dots_smem(P, K->ld, x_is_basis);
   ++tl_launches;
   if (x_is_basis)
-    k_dots<P, true><<<blocks, geo.threads, 0, st>>>(U, X, n, geo.rows_per_block, geo.V, geo.R,
-                                                    K->ld, ustride, jfirst, jlast, JC, K->part,
-                                                    K->s);
+    k_dots<P, true, false><<<grid, block, smem, st>>>(U, X, Uk, geo.S, rows, ustride, jfirst, jlast,
+                                                   Jb, K->part, K->s);
+  else if (with_g)
+    k_dots<P, false, true><<<grid, block, smem, st>>>(U, X, Uk, geo.S, rows, ustride, jfirst, jlast,
+                                                   Jb, K->part, K->s);
   else
-    k_dots<P, false><<<blocks, geo.threads, 0, st>>>(U, X, n, geo.rows_per_block, geo.V, geo.R,
-                                                     K->ld, ustride, jfirst, jlast, JC, K->part,
-                                                     K->s);
+    k_dots<P, false, false><<<grid, block, smem, st>>>(U, X, Uk, geo.S, rows, ustride, jfirst, jlast,
+                                                    Jb, K->part, K->s);
   SLAQ_CHECK_LAUNCH("dots");
+  return SLAQ_OK;
+}
+
+int reduce_and_solve(slaq_krylov K, const Geometry &geo, int k, int jfirst, int jcount,
+                     bool with_g, bool first_pass, bool need_coef, double tol_abs, cudaStream_t st) {
+  ProfScope prof(SLAQ_PROF_REDUCE, st);
+  const dim3 grid((unsigned)ceil_div((int64_t)jcount * K->ld, 32), with_g ? 2 : 1);
+  ++tl_launches;
+  k_dot_reduce<<<grid, dim3(32, kRedY), 0, st>>>(K->part, K->Gdots, K->s, K->ld, jfirst, jcount, k,
+                                             with_g ? 1 : 0, K->dsum, K->gram);
+  ++tl_launches;
+  k_solve<<<K->ld, 32, 0, st>>>(K->dsum, K->gram, k, K->s, K->ld, K->nv, first_pass ? 1 : 0,
+                                need_coef ? 1 : 0, tol_abs, K->m, K->alpha, K->beta, K->coef);
+  SLAQ_CHECK_LAUNCH("reduce_and_solve");
   return SLAQ_OK;
 }
 
@@ -671,61 +940,50 @@ int update(slaq_krylov K, const Geometry &geo, int64_t n, int k, bool second, cu
   ProfScope prof(SLAQ_PROF_UPDATE, st);
   using TB = typename Form<P>::TB;
   using TW = typename Form<P>::TW;
-  constexpr int VE = Form<P>::VE;
   const TB *U = static_cast<const TB *>(K->U);
   TB *Unext = static_cast<TB *>(K->U) + (int64_t)(k + 1) * n * K->ld;
   const int64_t ustride = n * K->ld;
-  const size_t smem = (size_t)(k + 1) * K->ld * sizeof(TW) + (size_t)geo.threads * VE * sizeof(double);
+  const size_t smem = (size_t)(k + 1) * K->ld * sizeof(TW);
   ++tl_launches;
   if (second)
-    k_update<P, true><<<geo.G, geo.threads, smem, st>>>(U, static_cast<const TW *>(K->Z), Unext, n,
-                                                        geo.rows_per_block, geo.V, geo.R, K->ld,
-                                                        ustride, k, K->coef, K->m, K->nv, K->part,
-                                                        K->s);
+    k_update<P, true><<<geo.Gupd, geo.threads, smem, st>>>(U, static_cast<const TW *>(K->Z), Unext,
+                                                           geo.S, geo.upd_rows, geo.V, geo.R,
+                                                           ustride, k, K->coef, K->m, K->nv);
   else
-    k_update<P, false><<<geo.G, geo.threads, smem, st>>>(U, static_cast<const TW *>(K->Z), Unext,
-                                                         n, geo.rows_per_block, geo.V, geo.R,
-                                                         K->ld, ustride, k, K->coef, K->m, K->nv,
-                                                         K->part, K->s);
+    k_update<P, false><<<geo.Gupd, geo.threads, smem, st>>>(U, static_cast<const TW *>(K->Z), Unext,
+                                                            geo.S, geo.upd_rows, geo.V, geo.R,
+                                                            ustride, k, K->coef, K->m, K->nv);
   SLAQ_CHECK_LAUNCH("update");
-  return SLAQ_OK;
-}
-
-int dot_reduce(slaq_krylov K, const Geometry &geo, int jfirst, int jcount, int k, bool write_alpha,
-               cudaStream_t st) {
-  ProfScope prof(SLAQ_PROF_REDUCE, st);
-  const unsigned blocks = (unsigned)ceil_div((int64_t)jcount * K->ld, 32);
-  ++tl_launches;
-  k_dot_reduce<<<blocks, dim3(32, 8), 0, st>>>(K->part, geo.G, K->s, K->ld, jfirst, jcount, k,
-                                               K->nu2, K->m, K->nv, K->coef, K->alpha,
-                                               write_alpha ? 1 : 0);
-  SLAQ_CHECK_LAUNCH("dot_reduce");
   return SLAQ_OK;
 }
 
 template <int P>
 int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   using TB = typename Form<P>::TB;
-  using TW = typename Form<P>::TW;
   const int64_t n = gr->n;
   const Geometry geo = geometry(P, K->ld, n, num_sms());
-  if (geo.G > K->G) return set_error(SLAQ_EINVAL, "internal: reduction workspace too small");
+  if (geo.Gmax > K->G) return set_error(SLAQ_EINVAL, "internal: reduction workspace too small");
   static bool attr_set = false;
   if (!attr_set) {
     SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_update<P, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_update<P, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_dots<P, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_dots<P, false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_dots<P, true, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
   {
     ProfScope prof(SLAQ_PROF_PROBES, st);
     ++tl_launches;
-    k_init_scalars<<<1, 256, 0, st>>>(K->nu2, K->alpha, K->beta, K->m, K->nv, K->s, K->ld,
-                                      (double)n);
+    k_init_scalars<<<1, 256, 0, st>>>(K->alpha, K->beta, K->m, K->nv, K->s);
     ++tl_launches;
     k_probe_init<P><<<(unsigned)std::min<int64_t>(ceil_div(n * K->ld, 256), 152LL * 64), 256, 0,
-                      st>>>(static_cast<TB *>(K->U), gr->old_id, n, K->ld, K->nv, K->seed,
+                      st>>>(static_cast<TB *>(K->U), gr->x_old_id, geo.S, K->nv, K->seed,
                             (uint64_t)K->graph_id);
   }
   SLAQ_CHECK_LAUNCH("probe_init");
@@ -733,24 +991,19 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   for (int k = 0; k < K->s; ++k) {
     SLAQ_TRY(spmm<P>(gr, K, geo, k, st));
     const bool last = (k == K->s - 1);
+    // last step: only alpha_k = d_k / G_kk and the Gram diagonal entry
     const int jfirst = last ? k : 0;
-    SLAQ_TRY(dots<P>(K, geo, n, jfirst, k, false, K->Z, st));
-    SLAQ_TRY(dot_reduce(K, geo, jfirst, k - jfirst + 1, k, true, st));
+    SLAQ_TRY(dots<P>(K, geo, n, k, jfirst, k, false, true, K->Z, st));
+    SLAQ_TRY(reduce_and_solve(K, geo, k, jfirst, k - jfirst + 1, true, true, !last, tol_abs, st));
     if (last) break;
     SLAQ_TRY(update<P>(K, geo, n, k, false, st));
     if (K->reorth == 2) {
       const TB *Unext = static_cast<const TB *>(K->U) + (int64_t)(k + 1) * n * K->ld;
-      SLAQ_TRY(dots<P>(K, geo, n, 0, k, true, Unext, st));
-      SLAQ_TRY(dot_reduce(K, geo, 0, k + 1, k, false, st));
+      SLAQ_TRY(dots<P>(K, geo, n, k, 0, k, true, false, Unext, st));
+      SLAQ_TRY(reduce_and_solve(K, geo, k, 0, k + 1, false, false, true, tol_abs, st));
       SLAQ_TRY(update<P>(K, geo, n, k, true, st));
     }
-    ProfScope prof(SLAQ_PROF_REDUCE, st);
-    ++tl_launches;
-    k_norm_reduce<<<(unsigned)ceil_div(K->ld, 32), dim3(32, 8), 0, st>>>(
-        K->part, geo.G, K->s, K->ld, k, K->nu2, K->m, K->nv, K->beta, tol_abs);
-    SLAQ_CHECK_LAUNCH("norm_reduce");
   }
-  (void)sizeof(TW);
   return SLAQ_OK;
 }
 
@@ -788,8 +1041,8 @@ int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaS
 
 void krylov_free(slaq_krylov k) {
   if (!k) return;
-  void *ptrs[] = {k->U, k->Z, k->P, k->part, k->dsum, k->coef, k->nu2, k->alpha, k->beta,
-                  k->m, k->theta, k->tau2, k->status};
+  void *ptrs[] = {k->U, k->Z, k->P, k->part, k->dsum, k->coef, k->gram, k->alpha, k->beta,
+                  k->m, k->theta, k->tau2, k->status, k->hcount};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete k;
@@ -807,7 +1060,7 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   if (g->n < 1) return set_error(SLAQ_EINVAL, "graph has no nodes");
   if (g->n > (1LL << 31)) return set_error(SLAQ_EUNSUPPORTED, "too many nodes");
   const int ld = row_ld(nv, precision);
-  if ((size_t)s * ld * work_bytes(precision) + 256 * 8 * 8 > 200 * 1024)
+  if ((size_t)s * ld * work_bytes(precision) > 200 * 1024)
     return set_error(SLAQ_EUNSUPPORTED, "s * nv too large for the update kernel's coefficient table");
   slaq_krylov K = *inout;
   const bool fresh = (K == nullptr);
@@ -840,14 +1093,22 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     SLAQ_TRY(grow(reinterpret_cast<unsigned char **>(&K->P), (size_t)cap * ld * work_bytes(precision)));
     K->chunk_cap = cap;
   }
-  if (geo.G > K->G) {
-    SLAQ_TRY(grow(&K->part, (size_t)geo.G * s * ld));
-    K->G = geo.G;
+  {
+    const int64_t need = std::max<int64_t>(1, g->n_heavy * geo.S.nslices());
+    if (need > K->hcount_cap) {
+      SLAQ_TRY(grow(&K->hcount, (size_t)need));
+      SLAQ_CHECK_CUDA(cudaMemsetAsync(K->hcount, 0, need * sizeof(uint32_t), st));
+      K->hcount_cap = need;
+    }
+  }
+  if (geo.Gmax > K->G) {
+    SLAQ_TRY(grow(&K->part, (size_t)geo.Gmax * 2 * s * ld));
+    K->G = geo.Gmax;
   }
   if (fresh) {
     SLAQ_TRY(grow(&K->dsum, (size_t)s * ld));
     SLAQ_TRY(grow(&K->coef, (size_t)s * ld));
-    SLAQ_TRY(grow(&K->nu2, (size_t)(s + 1) * ld));
+    SLAQ_TRY(grow(&K->gram, (size_t)s * s * ld));
     SLAQ_TRY(grow(&K->alpha, (size_t)nv * s));
     SLAQ_TRY(grow(&K->beta, (size_t)nv * s));
     SLAQ_TRY(grow(&K->m, (size_t)nv));

@@ -14,11 +14,13 @@ namespace {
 constexpr int kMaxS = 64;
 constexpr int kMaxNv = 512;
 
+// One probe per block (the solver is sequential; lane 0 runs it) so that the
+// probes spread over the SMs' FP64 units.
 __global__ void k_ritz(const double *__restrict__ alpha, const double *__restrict__ beta,
                        const int32_t *__restrict__ mm, int nv, int s, double *__restrict__ theta,
                        double *__restrict__ tau2, int32_t *status) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nv) return;
+  const int p = blockIdx.x;
+  if (p >= nv || threadIdx.x != 0) return;
   double d[kMaxS], e[kMaxS], w[kMaxS];
   const int m = mm[p];
   for (int i = 0; i < m; ++i) d[i] = alpha[p * s + i];
@@ -138,7 +140,7 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   ProfScope prof(SLAQ_PROF_RITZ, st);
   SLAQ_CHECK_CUDA(cudaMemsetAsync(K->status, 0, sizeof(int32_t), st));
   ++tl_launches;
-  k_ritz<<<(unsigned)ceil_div(K->nv, 64), 64, 0, st>>>(K->alpha, K->beta, K->m, K->nv, K->s,
+  k_ritz<<<(unsigned)K->nv, 32, 0, st>>>(K->alpha, K->beta, K->m, K->nv, K->s,
                                                        K->theta, K->tau2, K->status);
   SLAQ_CHECK_LAUNCH("ritz");
   return SLAQ_OK;

@@ -177,7 +177,8 @@ def test_fp64_lanczos_and_descriptors(name, kind, drop, nv, s):
     ov, ovse = odesc.vnge(runs, lap.n, lap.trace)
     assert abs(v.item() - ov) <= RTOL64 * abs(ov) + 1e-300
     if nv > 1:
-        assert _rel(hse.cpu().numpy()[:64], ohse[:64]) < 1e-6
+        # standard errors agree; where every probe gives the same value both are rounding noise
+        assert np.all(np.abs(hse - ohse) <= 1e-6 * ohse + 1e-12 * lap.n)
     # h_0 = n' exactly up to rounding
     h0, _ = slaq.trace_heat(K, dev([0.0], torch.float64))
     assert abs(h0.item() - lap.n) < 1e-12 * lap.n
