@@ -376,26 +376,24 @@ __global__ void k_scale(const double *deg, int64_t n, int kind, double *scale, d
   }
 }
 
-// Row of every stored entry is needed for the values; the kernel walks rows.
-__global__ void k_values(const int64_t *rowptr, const uint64_t *ukey, const double *uw,
-                         const int64_t *newid, int drop, int cb, int64_t n, int kind,
-                         const double *scale, int32_t *colidx, double *vals, float *vals32) {
-  const uint64_t cmask = (cb >= 64) ? ~0ull : ((1ull << cb) - 1ull);
-  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); i < n;
-       i += (int64_t)gridDim.x * (blockDim.x / 32)) {
-    const int64_t b = rowptr[i], e = rowptr[i + 1];
-    const double si = scale[i];
-    for (int64_t j = b + (threadIdx.x & 31); j < e; j += 32) {
-      const int64_t c_old = (int64_t)(ukey[j] & cmask);
-      const int64_t c = drop ? newid[c_old] : c_old;
-      const double a = uw ? uw[j] : 1.0;
-      double v;
-      if (kind == SLAQ_NORMALIZED) v = -((a * si) * scale[c]);
-      else v = -a;
-      colidx[j] = (int32_t)c;
-      vals[j] = v;
-      if (vals32) vals32[j] = (float)v;
-    }
+// One thread per stored entry; its row and column come from the sorted key.
+__global__ void k_values(const uint64_t *ukey, const double *uw, const int64_t *newid, int drop,
+                         int cb, int64_t nnz, int kind, const double *scale, int32_t *colidx,
+                         double *vals, float *vals32) {
+  const uint64_t cmask = (1ull << cb) - 1ull;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = ukey[j];
+    const int64_t r_old = (int64_t)(key >> cb), c_old = (int64_t)(key & cmask);
+    const int64_t r = drop ? newid[r_old] : r_old;
+    const int64_t c = drop ? newid[c_old] : c_old;
+    const double a = uw ? uw[j] : 1.0;
+    double v;
+    if (kind == SLAQ_NORMALIZED) v = -((a * scale[r]) * scale[c]);
+    else v = -a;
+    colidx[j] = (int32_t)c;
+    vals[j] = v;
+    if (vals32) vals32[j] = (float)v;
   }
 }
 
@@ -446,30 +444,35 @@ __global__ void k_perm_index(const uint64_t *key, const int64_t *rowptr, int64_t
   }
 }
 
-// Execution row r is canonical row perm[r]; columns renamed through inv.
-__global__ void k_perm_rows(const int64_t *rowptr, const int32_t *colidx, const double *vals,
-                            const float *vals32, const double *diag, const double *scale,
-                            const int64_t *old_id, const int64_t *perm, const int64_t *inv,
-                            int64_t n, const int64_t *xrowptr, int32_t *xcol, double *xvals,
-                            float *xvals32, double *xdiag, double *xscale, float *xdiag32,
-                            float *xscale32, int64_t *xold) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); r < n;
-       r += (int64_t)gridDim.x * (blockDim.x / 32)) {
+// Execution row r is canonical row perm[r]; columns are renamed through inv.
+// One thread per canonical entry (its row comes from the sorted key).
+__global__ void k_perm_entries(const uint64_t *ukey, const int64_t *newid, int drop, int cb,
+                               const int64_t *rowptr, const int32_t *colidx, const double *vals,
+                               const float *vals32, const int64_t *inv, int64_t nnz,
+                               const int64_t *xrowptr, int32_t *xcol, double *xvals,
+                               float *xvals32) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r_old = (int64_t)(ukey[e] >> cb);
+    const int64_t i = drop ? newid[r_old] : r_old;
+    const int64_t x = xrowptr[inv[i]] + (e - rowptr[i]);
+    xcol[x] = (int32_t)inv[colidx[e]];
+    xvals[x] = vals[e];
+    if (xvals32) xvals32[x] = vals32[e];
+  }
+}
+
+__global__ void k_perm_nodes(const double *diag, const double *scale, const int64_t *old_id,
+                             const int64_t *perm, int64_t n, double *xdiag, double *xscale,
+                             float *xdiag32, float *xscale32, int64_t *xold) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = perm[r];
-    const int64_t b = rowptr[i], e = rowptr[i + 1], xb = xrowptr[r];
-    for (int64_t t = lane; t < e - b; t += 32) {
-      xcol[xb + t] = (int32_t)inv[colidx[b + t]];
-      xvals[xb + t] = vals[b + t];
-      if (xvals32) xvals32[xb + t] = vals32[b + t];
-    }
-    if (lane == 0) {
-      xdiag[r] = diag[i];
-      xscale[r] = scale[i];
-      xdiag32[r] = (float)diag[i];
-      xscale32[r] = (float)scale[i];
-      xold[r] = old_id[i];
-    }
+    xdiag[r] = diag[i];
+    xscale[r] = scale[i];
+    xdiag32[r] = (float)diag[i];
+    xscale32[r] = (float)scale[i];
+    xold[r] = old_id[i];
   }
 }
 
@@ -677,9 +680,8 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
                                                   g->scale32, g->diag32);
     SLAQ_CHECK_LAUNCH("scale");
     ++tl_launches;
-    k_values<<<grid_for(n_out * 32, 256), 256, 0, st>>>(g->rowptr, ukey, uw, newid,
-                                                        drop ? 1 : 0, cb, n_out, kind, g->scale,
-                                                        g->colidx, g->vals, g->vals32);
+    k_values<<<grid_for(nnz, 256), 256, 0, st>>>(ukey, uw, newid, drop ? 1 : 0, cb, nnz, kind,
+                                                 g->scale, g->colidx, g->vals, g->vals32);
     SLAQ_CHECK_LAUNCH("values");
   }
 
@@ -730,12 +732,17 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
     SLAQ_TRY(exclusive_scan(xcnt, n_out, g->x_rowptr, d_total, st));
     SLAQ_CHECK_CUDA(cudaMemcpyAsync(g->x_rowptr + n_out, d_total, sizeof(int64_t),
                                     cudaMemcpyDeviceToDevice, st));
+    if (nnz > 0) {
+      ++tl_launches;
+      k_perm_entries<<<grid_for(nnz, 256), 256, 0, st>>>(
+          ukey, newid, drop ? 1 : 0, cb, g->rowptr, g->colidx, g->vals, g->vals32, inv, nnz,
+          g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32);
+    }
     ++tl_launches;
-    k_perm_rows<<<grid_for(n_out * 32, 256), 256, 0, st>>>(
-        g->rowptr, g->colidx, g->vals, g->vals32, g->diag, g->scale, g->old_id, perm, inv, n_out,
-        g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32, g->x_diag, g->x_scale, g->x_diag32,
-        g->x_scale32, g->x_old_id);
-    SLAQ_CHECK_LAUNCH("perm_rows");
+    k_perm_nodes<<<grid_for(n_out, 256), 256, 0, st>>>(g->diag, g->scale, g->old_id, perm, n_out,
+                                                       g->x_diag, g->x_scale, g->x_diag32,
+                                                       g->x_scale32, g->x_old_id);
+    SLAQ_CHECK_LAUNCH("perm");
   } else {
     SLAQ_CHECK_CUDA(cudaMemsetAsync(g->x_rowptr, 0, sizeof(int64_t), st));
   }

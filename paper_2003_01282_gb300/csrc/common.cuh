@@ -150,6 +150,9 @@ struct slaq_krylov_s {
   int32_t *status = nullptr;  // [1] device-side error flags
   uint32_t *hcount = nullptr; // [n_heavy * slices] arrival counters of split rows (kept zero)
   int64_t hcount_cap = 0;
+  // side stream on which the split-row SpMM runs beside the light rows
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace slaq {

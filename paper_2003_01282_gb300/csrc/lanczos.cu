@@ -396,15 +396,26 @@ struct PlainD {
   __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ double value() const { return s; }
 };
-template <typename TW>
+struct PlainF {
+  float s = 0.f;
+  __device__ __forceinline__ void add(float x) { s += x; }
+  __device__ __forceinline__ double value() const { return (double)s; }
+};
+// FP64: plain FP64; FP32: Kahan; BF16 basis: plain FP32 (the basis's own
+// 2^-9 rounding dominates; saves the registers the wider vectors need).
+template <int P>
 struct Acc;
 template <>
-struct Acc<double> {
+struct Acc<SLAQ_FP64> {
   using type = PlainD;
 };
 template <>
-struct Acc<float> {
+struct Acc<SLAQ_FP32> {
   using type = KahanF;
+};
+template <>
+struct Acc<SLAQ_FP32_BF16BASIS> {
+  using type = PlainF;
 };
 
 // Neumaier-compensated FP64 pair sum.
@@ -483,7 +494,7 @@ __device__ __forceinline__ void stage_rows(T *dst, const T *src, const Slc &S, i
 }
 
 template <int P, bool X_IS_BASIS, bool WITH_G>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 2)
     k_dots(const typename Form<P>::TB *__restrict__ U, const void *__restrict__ Xv,
            const typename Form<P>::TB *__restrict__ Uk, Slc S, int64_t rows_per_block,
            int64_t ustride, int jfirst, int jlast, int Jb, double *__restrict__ part, int s) {
@@ -491,7 +502,7 @@ __global__ void __launch_bounds__(512)
   using TW = typename Form<P>::TW;
   using TX = typename std::conditional<X_IS_BASIS, TB, TW>::type;
   constexpr int VE = Form<P>::VE;
-  using A = typename Acc<TW>::type;
+  using A = typename Acc<P>::type;
   extern __shared__ __align__(16) unsigned char dyn[];
   const int ld = S.ld;
   TX *xs = reinterpret_cast<TX *>(dyn);                 // [2][kTile][ld]
@@ -535,13 +546,14 @@ __global__ void __launch_bounds__(512)
         dc[v] = TW(0);
         gc[v] = TW(0);
       }
+      constexpr int UNR = VE >= 8 ? 2 : 4;  // rows in flight per thread (register budget)
       int r = 0;
-      for (; r + 4 <= nr; r += 4) {
-        TW u[4][VE];
+      for (; r + UNR <= nr; r += UNR) {
+        TW u[UNR][VE];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ldb(Uj + (row0 + r + q) * stride, u[q]);
+        for (int q = 0; q < UNR; ++q) ldb(Uj + (row0 + r + q) * stride, u[q]);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < UNR; ++q) {
           TW x[VE];
           lds(xt + (r + q) * ld, x);
 #pragma unroll
@@ -607,11 +619,13 @@ __global__ void k_dot_reduce(const double *__restrict__ part, int G, int s, int 
   const bool valid = col < ncol && (which == 0 || with_g);
   const int j = jfirst + (valid ? col / ld : 0);
   const int p = valid ? col % ld : 0;
-  Neumaier acc;
+  // plain FP64 sums of the strided partials (a few dozen terms; FP64 is
+  // scarce on this chip), compensated combination of the kRedY sums
+  double acc = 0.0;
   if (valid)
-    for (int g = threadIdx.y; g < G; g += kRedY) acc.add(part[(((int64_t)g * 2 + which) * s + j) * ld + p]);
-  ss[threadIdx.y][threadIdx.x] = acc.s;
-  sc[threadIdx.y][threadIdx.x] = acc.c;
+    for (int g = threadIdx.y; g < G; g += kRedY) acc += part[(((int64_t)g * 2 + which) * s + j) * ld + p];
+  ss[threadIdx.y][threadIdx.x] = acc;
+  sc[threadIdx.y][threadIdx.x] = 0.0;
   __syncthreads();
   if (threadIdx.y == 0 && valid) {
     Neumaier tot;
@@ -684,29 +698,37 @@ __global__ void k_solve(const double *__restrict__ dsum, const double *__restric
     if (j <= i) A[i * K1 + j] = gram[((int64_t)i * s + j) * ld + p] * sc[i] * sc[j];
   }
   __syncthreads();
-  if (lane == 0) {
-    // Cholesky of Ghat = D^-1/2 G D^-1/2 (unit diagonal), in place
-    for (int i = 0; i < K1; ++i) {
-      for (int j = 0; j <= i; ++j) {
-        double a = A[i * K1 + j];
-        for (int q = 0; q < j; ++q) a -= A[i * K1 + q] * A[j * K1 + q];
-        if (i == j) A[i * K1 + i] = sqrt(fmax(a, 1e-300));
-        else A[i * K1 + j] = a / A[j * K1 + j];
-      }
+  // Cholesky of Ghat = D^-1/2 G D^-1/2 (unit diagonal), in place, right-looking:
+  // column c is scaled by its pivot, then the trailing block is updated by
+  // all lanes of the warp.
+  for (int c = 0; c < K1; ++c) {
+    if (lane == 0) A[c * K1 + c] = sqrt(fmax(A[c * K1 + c], 1e-300));
+    __syncwarp();
+    const double piv = A[c * K1 + c];
+    for (int i = c + 1 + lane; i < K1; i += 32) A[i * K1 + c] /= piv;
+    __syncwarp();
+    const int rem = K1 - c - 1;  // trailing rows c+1..K1-1, lower triangle
+    for (int e = lane; e < rem * rem; e += 32) {
+      const int i = c + 1 + e / rem, q = c + 1 + e % rem;
+      if (q <= i) A[i * K1 + q] -= A[i * K1 + c] * A[q * K1 + c];
     }
-    // Ghat xhat = D^-1/2 d, x = D^-1/2 xhat
-    for (int i = 0; i < K1; ++i) {
-      double a = y[i] * sc[i];
-      for (int q = 0; q < i; ++q) a -= A[i * K1 + q] * y[q];
-      y[i] = a / A[i * K1 + i];
-    }
-    for (int i = K1 - 1; i >= 0; --i) {
-      double a = y[i];
-      for (int q = i + 1; q < K1; ++q) a -= A[q * K1 + i] * y[q];
-      y[i] = a / A[i * K1 + i];
-    }
+    __syncwarp();
   }
-  __syncthreads();
+  // Ghat xhat = D^-1/2 d (column-oriented substitutions), x = D^-1/2 xhat
+  for (int i = lane; i < K1; i += 32) y[i] *= sc[i];
+  __syncwarp();
+  for (int c = 0; c < K1; ++c) {
+    if (lane == 0) y[c] /= A[c * K1 + c];
+    __syncwarp();
+    for (int i = c + 1 + lane; i < K1; i += 32) y[i] -= A[i * K1 + c] * y[c];
+    __syncwarp();
+  }
+  for (int c = K1 - 1; c >= 0; --c) {
+    if (lane == 0) y[c] /= A[c * K1 + c];
+    __syncwarp();
+    for (int i = lane; i < c; i += 32) y[i] -= A[c * K1 + i] * y[c];
+    __syncwarp();
+  }
   for (int j = lane; j < K1; j += blockDim.x) coef[j * ld + p] = y[j] * sc[j];
 }
 
@@ -784,13 +806,18 @@ struct Geometry {
   int Gupd;               // update blocks
 };
 
-// Row blocks of the dots kernel for blocks of `threads` threads: enough to
-// fill every SM with 2048 threads, at most Gmax, at least 64 rows each.
-inline void dots_grid(const Geometry &g, int64_t n, int threads, size_t smem, int *G,
+// Row blocks of the dots kernel: one full wave (every SM holds as many blocks
+// as registers, shared memory and threads allow), at most Gmax, at least 64
+// rows per block.
+template <typename Kern>
+inline void dots_grid(const Geometry &g, int64_t n, Kern kern, int threads, size_t smem, int *G,
                       int64_t *rows) {
-  const int64_t by_threads = 2048 / threads;
-  const int64_t by_smem = smem ? (int64_t)(220 * 1024) / (int64_t)smem : by_threads;
-  const int64_t per_sm = std::max<int64_t>(1, std::min(by_threads, by_smem));
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
   int64_t want = (int64_t)g.sms * per_sm;
   want = std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)g.Gmax, ceil_div(n, 64)}));
   *rows = ceil_div(n, want);
@@ -866,15 +893,21 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
   const unsigned hblocks = (unsigned)(ns * gr->n_chunks);
   const int hthreads = (int)ceil_div(geo.Vt, 32) * 32;
 #define SLAQ_SPMM_CASE(MODE)                                                                    \
+  if (gr->n_chunks > 0) {                                                                       \
+    ++tl_launches;                                                                              \
+    k_spmm_heavy<P, MODE><<<hblocks, hthreads, 0, K->side>>>(                                   \
+        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, static_cast<TW *>(K->P),          \
+        gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, geo.S, geo.Vt, gr->n_chunks); \
+  }                                                                                             \
   ++tl_launches;                                                                                \
   k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(gr->x_rowptr, gr->x_colidx, vals, diag, \
                                                          scale, Uk, Z, geo.S, geo.Vt, geo.Rt,   \
-                                                         bps, gr->heavy_degree);                \
-  if (gr->n_chunks > 0) {                                                                       \
-    ++tl_launches;                                                                              \
-    k_spmm_heavy<P, MODE><<<hblocks, hthreads, 0, st>>>(                                        \
-        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, static_cast<TW *>(K->P),          \
-        gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, geo.S, geo.Vt, gr->n_chunks); \
+                                                         bps, gr->heavy_degree);
+  // split rows on the side stream, concurrently with the light rows (the two
+  // write disjoint rows of z)
+  if (gr->n_chunks > 0) {
+    SLAQ_CHECK_CUDA(cudaEventRecord(K->ev_fork, st));
+    SLAQ_CHECK_CUDA(cudaStreamWaitEvent(K->side, K->ev_fork, 0));
   }
   if (mode == 0) {
     SLAQ_SPMM_CASE(0)
@@ -882,6 +915,10 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
     SLAQ_SPMM_CASE(1)
   } else {
     SLAQ_SPMM_CASE(2)
+  }
+  if (gr->n_chunks > 0) {
+    SLAQ_CHECK_CUDA(cudaEventRecord(K->ev_join, K->side));
+    SLAQ_CHECK_CUDA(cudaStreamWaitEvent(st, K->ev_join, 0));
   }
 #undef SLAQ_SPMM_CASE
   SLAQ_CHECK_LAUNCH("spmm");
@@ -899,14 +936,16 @@ int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int j
   const int Jb = std::min(jcount, geo.Jb);
   int G;
   int64_t rows;
-  dots_grid(geo, n, geo.V * Jb, dots_smem(P, K->ld, x_is_basis), &G, &rows);
+  const size_t smem = dots_smem(P, K->ld, x_is_basis);
+  if (x_is_basis) dots_grid(geo, n, k_dots<P, true, false>, geo.V * Jb, smem, &G, &rows);
+  else if (with_g) dots_grid(geo, n, k_dots<P, false, true>, geo.V * Jb, smem, &G, &rows);
+  else dots_grid(geo, n, k_dots<P, false, false>, geo.V * Jb, smem, &G, &rows);
   K->Gdots = G;
   const dim3 grid(G, (unsigned)ceil_div(jcount, Jb));
   const dim3 block(geo.V, Jb);
   const TB *U = static_cast<const TB *>(K->U);
   const TB *Uk = U + (int64_t)k * n * K->ld;
   const int64_t ustride = n * K->ld;
-  const size_t smem = dots_smem(P, K->ld, x_is_basis);
   ++tl_launches;
   if (x_is_basis)
     k_dots<P, true, false><<<grid, block, smem, st>>>(U, X, Uk, geo.S, rows, ustride, jfirst, jlast,
@@ -1045,6 +1084,9 @@ void krylov_free(slaq_krylov k) {
                   k->m, k->theta, k->tau2, k->status, k->hcount};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (k->ev_fork) cudaEventDestroy(k->ev_fork);
+  if (k->ev_join) cudaEventDestroy(k->ev_join);
+  if (k->side) cudaStreamDestroy(k->side);
   delete k;
 }
 
@@ -1073,6 +1115,9 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     K->precision = precision;
     K->ld = ld;
     SLAQ_CHECK_CUDA(cudaGetDevice(&K->device));
+    SLAQ_CHECK_CUDA(cudaStreamCreateWithFlags(&K->side, cudaStreamNonBlocking));
+    SLAQ_CHECK_CUDA(cudaEventCreateWithFlags(&K->ev_fork, cudaEventDisableTiming));
+    SLAQ_CHECK_CUDA(cudaEventCreateWithFlags(&K->ev_join, cudaEventDisableTiming));
   }
   struct Guard {
     slaq_krylov *K;

@@ -19,6 +19,16 @@ namespace slaq {
 #define SLAQ_HD
 #endif
 
+// 1/sqrt(x) for x > 0 (the device's reciprocal square root; FP64 division
+// and hypot are slow on GB300's small FP64 units)
+SLAQ_HD inline double rnorm(double x2) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x2);
+#else
+  return 1.0 / sqrt(x2);
+#endif
+}
+
 // d[0..m): diagonal (overwritten by the nodes), e[0..m-1): off-diagonal
 // (e[i] couples i and i+1; destroyed), w[0..m): squared first components.
 // Nodes come out in ascending order.  Returns 0, or 1 without convergence.
@@ -46,9 +56,18 @@ SLAQ_HD inline int tridiag_gauss(double *d, double *e, double *w, int m) {
     double x = d[lo] - mu, y = e[lo];
     for (int k = lo; k < hi; ++k) {
       // rotation G in plane (k, k+1) with G^T (x, y) = (r, 0)
-      const double r = hypot(x, y);
-      const double cs = r > 0.0 ? x / r : 1.0;
-      const double sn = r > 0.0 ? -y / r : 0.0;
+      const double r2 = x * x + y * y;
+      double r = 0.0, cs = 1.0, sn = 0.0;
+      if (r2 > 1e-290) {
+        const double ir = rnorm(r2);
+        r = r2 * ir;
+        cs = x * ir;
+        sn = -y * ir;
+      } else if (r2 > 0.0) {  // tiny entries: scaled form
+        r = hypot(x, y);
+        cs = x / r;
+        sn = -y / r;
+      }
       if (k > lo) e[k - 1] = r;  // bulge annihilated
       const double dk = d[k], dk1 = d[k + 1], ek = e[k];
       const double cc = cs * cs, ss = sn * sn, csn = cs * sn;
