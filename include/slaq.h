@@ -189,6 +189,37 @@ int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int6
                           double *wave_re_host, double *wave_im_host, double *vnge_host,
                           void *stream);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* Heat trace from Lanczos coefficients without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory at the time they call, for example code
+ * that must not call cudaMalloc (or a caching allocator) while it records
+ * work into a CUDA graph, or an application whose memory manager owns all
+ * device memory and hands libraries only the buffers it created.
+ * It computes what slaq_trace_heat computes after slaq_lanczos (the Gauss
+ * rule of every probe's tridiagonal, then Eq. slq for exp(-t theta)), but
+ * takes the coefficients as inputs and keeps the Gauss nodes and weights in
+ * a fixed scratch array inside the library instead of a handle:
+ *   alpha, beta  float64[nv*s] as written by slaq_krylov_export (row p holds
+ *                alpha_0..alpha_{m_p-1} and beta_0..beta_{m_p-2});
+ *   m            int32[nv]; n the node count n'; t float64[nt];
+ *   out, stderr_ float64[nt] (stderr_ may be NULL);
+ *   status       int32[1] or NULL: receives 0, or 1 if an eigensolve did
+ *                not converge.
+ * Limits: nv <= 512, s <= 64 (the scratch holds 512 x 64 nodes and
+ * weights, 512 KiB per device, kept until the process exits); larger sizes
+ * return SLAQ_EINVAL.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the one scratch array, which keeps the last
+ * call's contents: calls whose GPU work overlaps (other streams, other
+ * threads) race and must be ordered by the caller. */
+int slaq_trace_heat_tridiag_static(const double *alpha, const double *beta, const int32_t *m,
+                                   int nv, int s, int64_t n, const double *t, int nt, double *out,
+                                   double *stderr_, int32_t *status, void *stream);
+
 /* ------------------------------------------------------------- profiling */
 
 /* Kernel classes timed by the profiler. */

@@ -375,6 +375,14 @@ int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int6
   return SLAQ_OK;
 }
 
+int slaq_trace_heat_tridiag_static(const double *alpha, const double *beta, const int32_t *m,
+                                   int nv, int s, int64_t n, const double *t, int nt, double *out,
+                                   double *stderr_, int32_t *status, void *stream) {
+  SLAQ_TRY(device_check());
+  return trace_heat_static(alpha, beta, m, nv, s, n, t, nt, out, stderr_, status,
+                           as_stream(stream));
+}
+
 int slaq_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mutex);
   if (on) {

@@ -172,4 +172,7 @@ int trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im, d
                double *se_im, cudaStream_t st);
 int trace_vnge(slaq_krylov k, double *out, double *se, double *per_probe, cudaStream_t st);
 int distance(const double *a, const double *b, int nt, int kind, double *out, cudaStream_t st);
+int trace_heat_static(const double *alpha, const double *beta, const int32_t *m, int nv, int s,
+                      int64_t n, const double *t, int nt, double *out, double *se,
+                      int32_t *status_out, cudaStream_t st);
 }  // namespace slaq

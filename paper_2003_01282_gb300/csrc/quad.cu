@@ -4,6 +4,7 @@
 // All FP64.  Probe sums run in probe order, so results are deterministic.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "tridiag.cuh"
@@ -193,6 +194,68 @@ int distance(const double *a, const double *b, int nt, int kind, double *out, cu
   ++tl_launches;
   k_distance<<<1, 256, 0, st>>>(a, b, len, kind == SLAQ_DIST_VNGE ? 1 : 0, out);
   SLAQ_CHECK_LAUNCH("distance");
+  return SLAQ_OK;
+}
+
+// --------------------------------------------------- no-allocation variant
+// Gauss nodes and weights of the allocation-free heat trace live in this
+// file-scope device array (every device that loads the library holds it until
+// the process exits).  Host code must not pass the symbol itself to a kernel:
+// in host code it names a host-side stand-in, not device memory.  Its device
+// address is obtained once per device with cudaGetSymbolAddress.
+constexpr int kStaticMaxNvS = kMaxNv * kMaxS;  // 512 probes x 64 steps
+static __device__ __align__(256) double g_static_gauss[2 * kStaticMaxNvS];
+static __device__ __align__(256) int32_t g_static_status[8];
+
+namespace {
+struct StaticScratch {
+  double *gauss = nullptr;
+  int32_t *status = nullptr;
+};
+std::mutex g_static_mutex;
+StaticScratch g_static_ptr[64];
+}  // namespace
+
+int trace_heat_static(const double *alpha, const double *beta, const int32_t *m, int nv, int s,
+                      int64_t n, const double *t, int nt, double *out, double *se,
+                      int32_t *status_out, cudaStream_t st) {
+  if (!alpha || !beta || !m || !t || !out) return set_error(SLAQ_EINVAL, "NULL argument");
+  if (nv < 1 || nv > kMaxNv || s < 1 || s > kMaxS || (int64_t)nv * s > kStaticMaxNvS)
+    return set_error(SLAQ_EINVAL,
+                     "nv = %d, s = %d exceed the static scratch of this entry point "
+                     "(nv <= %d, s <= %d)",
+                     nv, s, kMaxNv, kMaxS);
+  if (nt < 1 || n < 1) return set_error(SLAQ_EINVAL, "nt and n must be >= 1");
+  int dev = -1;
+  SLAQ_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(SLAQ_ENODEVICE, "device index out of range");
+  StaticScratch sp;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mutex);
+    StaticScratch &slot = g_static_ptr[dev];
+    if (!slot.gauss) {
+      void *a = nullptr, *b = nullptr;
+      cudaError_t e1 = cudaGetSymbolAddress(&a, g_static_gauss);
+      if (e1 != cudaSuccess) return cuda_status(e1, "cudaGetSymbolAddress(scratch)");
+      cudaError_t e2 = cudaGetSymbolAddress(&b, g_static_status);
+      if (e2 != cudaSuccess) return cuda_status(e2, "cudaGetSymbolAddress(status)");
+      slot.gauss = static_cast<double *>(a);
+      slot.status = static_cast<int32_t *>(b);
+    }
+    sp = slot;
+  }
+  ProfScope prof(SLAQ_PROF_TRACE, st);
+  double *theta = sp.gauss;
+  double *tau2 = sp.gauss + (size_t)nv * s;
+  SLAQ_CHECK_CUDA(cudaMemsetAsync(sp.status, 0, sizeof(int32_t), st));  // starts at zero
+  ++tl_launches;
+  k_ritz<<<(unsigned)nv, 32, 0, st>>>(alpha, beta, m, nv, s, theta, tau2, sp.status);
+  ++tl_launches;
+  k_trace_t<0><<<nt, 128, 0, st>>>(theta, tau2, m, nv, s, (double)n, t, nt, out, se, nullptr);
+  if (status_out)
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(status_out, sp.status, sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, st));
+  SLAQ_CHECK_LAUNCH("trace_heat_static");
   return SLAQ_OK;
 }
 

@@ -57,6 +57,8 @@ _SIGNATURES = {
     "slaq_descriptors_host": (_I, [_VP, _VP, _I64, _I64, _I, _I, _I, _I, _U64, _I, _VP, _I,
                                    _VP, _VP, _VP, _VP, _VP]),
     "slaq_tridiag_gauss_host": (_I, [_VP, _VP, _I, _VP, _VP]),
+    "slaq_trace_heat_tridiag_static": (_I, [_VP, _VP, _VP, _I, _I, _I64, _VP, _I, _VP, _VP, _VP,
+                                            _VP]),
     "slaq_profile_enable": (_I, [_I]),
     "slaq_profile_read": (_I, [_I, _VP, _VP]),
 }
@@ -315,6 +317,24 @@ def tridiag_gauss_host(alpha, beta):
     _check(lib().slaq_tridiag_gauss_host(pa, pb, m, th.ctypes.data_as(C.c_void_p),
                                          t2.ctypes.data_as(C.c_void_p)))
     return th, t2
+
+
+def trace_heat_tridiag_static(alpha, beta, m, n: int, t, stream=None):
+    """Heat trace from exported Lanczos coefficients; the library allocates
+    no device memory for it (see slaq_trace_heat_tridiag_static).
+    Returns (out, stderr, status) as CUDA tensors."""
+    torch = _torch()
+    nv, s = int(alpha.shape[0]), int(alpha.shape[1])
+    nt = int(t.numel())
+    out = torch.empty(nt, dtype=torch.float64, device=t.device)
+    se = torch.empty_like(out)
+    status = torch.empty(1, dtype=torch.int32, device=t.device)
+    _check(lib().slaq_trace_heat_tridiag_static(_dev(alpha, torch.float64, "alpha"),
+                                                _dev(beta, torch.float64, "beta"),
+                                                _dev(m, torch.int32, "m"), nv, s, int(n),
+                                                _dev(t, torch.float64, "t"), nt, _dev(out), _dev(se),
+                                                _dev(status), _stream(stream)))
+    return out, se, status
 
 
 def profile_enable(on: bool = True):
