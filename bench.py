@@ -52,6 +52,12 @@ WORKLOAD = ("R-MAT scale 20 (2^20 nodes, 16Mi unique undirected edges, a,b,c,d=.
             "log-spaced t in [1e-2,1e2] + VNGE")
 CPU_PROBES = 4        # probes of the CPU-oracle sample
 REF_PROBES = 1        # probes per step of the reference (oracle) arm
+# batched workload: 5000 SBM graphs, nv = 20, s = 15, heat traces at 256 t
+SBM_GRAPHS, SBM_NV, SBM_S, SBM_SEED = 5000, 20, 15, 3
+SBM_WORKLOAD = ("5000 stochastic-block-model graphs (sizes lognormal, median 300, clipped to "
+                "[10, 5000]; 2-6 equal blocks; p_in ~ U[.05,.3], p_out = p_in/U[5,20]; seed 3), "
+                "isolated nodes dropped, normalized Laplacians as one block-diagonal batch; "
+                "nv=20, s=15; heat traces on 256 log-spaced t")
 
 
 def make_graph():
@@ -154,7 +160,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", self.gpu_id],
+                 "-lms", "100", "-i", self.gpu_id],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -202,6 +208,88 @@ def algorithmic_bytes(n, nnz, prec, nv=NV, s=S):
     dots = sum(((k + 1 if k < s - 1 else 1) * bq + bw) * vec for k in range(s))
     update = sum(((k + 1) * bq + bw + bq) * vec for k in range(s - 1))
     return {"spmm": spmm, "dots": dots, "update": update}
+
+
+def run_batched(args, dev, world=1, rank=0):
+    """The SBM batch through one set of launches per step; graphs/s.  Also
+    times the same path graph by graph on a subset (per-graph launches)."""
+    import torch
+    from paper_2003_01282_gb300 import slaq
+    graphs = synth.sbm_batch(SBM_GRAPHS, seed=SBM_SEED)
+    srcs = np.concatenate([g[0] for g in graphs])
+    dsts = np.concatenate([g[1] for g in graphs])
+    edge_off = np.zeros(len(graphs) + 1, np.int64)
+    node_off = np.zeros(len(graphs) + 1, np.int64)
+    edge_off[1:] = np.cumsum([g[0].size for g in graphs])
+    node_off[1:] = np.cumsum([g[2] for g in graphs])
+    import ctypes as C
+    src = torch.as_tensor(srcs, device=dev)
+    dst = torch.as_tensor(dsts, device=dev)
+    t = torch.as_tensor(synth.t_grid(NT), device=dev)
+    P = slaq.PRECISIONS[args.precision]
+    state = {"K": None}
+
+    def step():
+        out = C.c_void_p()
+        slaq._check(slaq.lib().slaq_build_laplacian_batch(
+            C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()), edge_off.ctypes.data_as(C.c_void_p),
+            node_off.ctypes.data_as(C.c_void_p), len(graphs), None, slaq.NORMALIZED, slaq.DROP_ISOLATED,
+            slaq._stream(None), C.byref(out)))
+        g = slaq.Graph(out)
+        state["K"] = slaq.lanczos(g, SBM_NV, SBM_S, PROBE_SEED + 1000 * rank, precision=P,
+                                  reuse=state["K"])
+        heat, _ = slaq.trace_heat(state["K"], t)
+        nnz = g.info["nnz"]
+        g.close()
+        return heat, nnz
+
+    for _ in range(2):
+        _, nnz = step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        step()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    # the same path graph by graph on a subset (every 25th graph)
+    sub = graphs[::25]
+    Ks = None
+    e0.record()
+    for (sg, dg, ng) in sub:
+        g = slaq.build_laplacian(torch.as_tensor(sg, device=dev), torch.as_tensor(dg, device=dev), ng,
+                                 flags=slaq.DROP_ISOLATED)
+        Ks = slaq.lanczos(g, SBM_NV, SBM_S, PROBE_SEED, precision=P, reuse=Ks)
+        slaq.trace_heat(Ks, t)
+        g.close()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_sub = e0.elapsed_time(e1)
+    return {"workload": SBM_WORKLOAD, "metric": "graphs/s", "value": world * SBM_GRAPHS / (ms * 1e-3),
+            "ms_per_step": ms, "nnz": int(nnz),
+            "probe_edges_per_s": world * nnz * SBM_NV * SBM_S / (ms * 1e-3),
+            "per_graph_launches": {"graphs": len(sub), "value": len(sub) / (ms_sub * 1e-3),
+                                   "unit": "graphs/s"},
+            "speedup_over_per_graph": (SBM_GRAPHS / ms) / (len(sub) / ms_sub)}
+
+
+def kernel_capture(args):
+    """Profiling driver: build the R-MAT 2^20 graph and run Lanczos
+    `--kernel-capture` times (for ncu captures of single kernels)."""
+    import torch
+    from paper_2003_01282_gb300 import slaq
+    from paper_2003_01282_gb300.build import build
+    build()
+    s_, d_, n = make_graph()
+    g = slaq.build_laplacian(torch.as_tensor(s_, device="cuda"), torch.as_tensor(d_, device="cuda"), n,
+                             flags=slaq.DROP_ISOLATED)
+    K = None
+    for _ in range(args.kernel_capture):
+        K = slaq.lanczos(g, NV, S, PROBE_SEED, precision=slaq.PRECISIONS[args.precision], reuse=K)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_capture": args.kernel_capture, "n_prime": g.info["n"], "nnz": g.info["nnz"]}))
 
 
 def run_ours(args):
@@ -371,6 +459,8 @@ def run_ours(args):
                          "d2h_bytes_per_step": int(8 * (3 * NT + 1)),
                          "ms_per_step": e2e_s * 1e3}
 
+    if not args.quick and not args.no_batched:
+        result["batched_sbm5000"] = run_batched(args, dev, world, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(src_np, dst_np, n_nodes)
     if rank == 0:
@@ -382,16 +472,22 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64", "bf16"], default="fp32")
     ap.add_argument("--quick", action="store_true", help="skip the FP64-form and end-to-end legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the SBM-batch leg")
+    ap.add_argument("--kernel-capture", type=int, default=0,
+                    help="profiling driver: run Lanczos this many times on the R-MAT graph and exit")
     ap.add_argument("--cpu-baseline-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_baseline_worker:
         cpu_baseline_worker(args.cpu_baseline_worker)
+        return
+    if args.kernel_capture:
+        kernel_capture(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -92,6 +92,26 @@ int slaq_build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges
                          int64_t n_nodes, const double *weights, int kind, int flags,
                          void *stream, slaq_graph *out);
 
+/* Build the Laplacians of a batch of G graphs as ONE block-diagonal matrix,
+ * so that every later call (slaq_lanczos, the traces) serves all graphs
+ * with the same launches.  Graph g's edges are src/dst[edge_off_host[g] ..
+ * edge_off_host[g+1]) with ids LOCAL to the graph, in [0, n_g), n_g =
+ * node_off_host[g+1] - node_off_host[g] >= 1; weights (optional) follow the
+ * edges.  kind and flags as for slaq_build_laplacian, applied per graph.
+ * 1 <= G <= 65536; offsets are host arrays of G+1 entries starting at 0.
+ * Graph g's results match a single-graph run of graph g with graph_id
+ * (of slaq_lanczos) increased by g.  Synchronizes `stream`. */
+int slaq_build_laplacian_batch(const int32_t *src, const int32_t *dst,
+                               const int64_t *edge_off_host, const int64_t *node_off_host,
+                               int n_graphs, const double *weights, int kind, int flags,
+                               void *stream, slaq_graph *out);
+
+/* Host copies of the batch size G, the kept-node offsets node_off_host[G+1]
+ * (graph g owns kept nodes [node_off[g], node_off[g+1]) in exports) and the
+ * traces trace_host[G] = tr(L_g).  Any pointer may be NULL. */
+int slaq_graph_batch_info(slaq_graph g, int *n_graphs_host, int64_t *node_off_host,
+                          double *trace_host);
+
 /* Host copies of: kept node count n', stored off-diagonal count nnz, tr(L),
  * and the n_nodes given at build time (any pointer may be NULL). */
 int slaq_graph_info(slaq_graph g, int64_t *n_host, int64_t *nnz_host,
@@ -141,6 +161,12 @@ int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, v
 /* Device copies of the Gauss nodes theta float64[nv*s] (ascending within a
  * probe's first m_p entries) and weights tau2 float64[nv*s]. */
 int slaq_ritz_export(slaq_krylov k, double *theta, double *tau2, void *stream);
+
+/* Number of graphs G of the run (1 unless the graph was a batch).  For a
+ * batch every per-probe output below gains a leading graph axis:
+ * alpha, beta, theta, tau2 [G][nv][s], m [G][nv], trace outputs [G][nt],
+ * per-probe traces [G][nv][nt], VNGE outputs [G]. */
+int slaq_krylov_batch_info(slaq_krylov k, int *n_graphs_host);
 
 /* Host copies of nv, s, precision, n'. */
 int slaq_krylov_info(slaq_krylov k, int *nv_host, int *s_host, int *precision_host,

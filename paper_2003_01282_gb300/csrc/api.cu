@@ -202,6 +202,31 @@ int slaq_build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges
   return build_laplacian(src, dst, n_edges, n_nodes, weights, kind, flags, as_stream(stream), out);
 }
 
+int slaq_build_laplacian_batch(const int32_t *src, const int32_t *dst,
+                               const int64_t *edge_off_host, const int64_t *node_off_host,
+                               int n_graphs, const double *weights, int kind, int flags,
+                               void *stream, slaq_graph *out) {
+  SLAQ_TRY(device_check());
+  if (!edge_off_host || !node_off_host || n_graphs < 1)
+    return set_error(SLAQ_EINVAL, "a batch needs n_graphs >= 1 and both offset arrays");
+  return build_laplacian(src, dst, 0, 0, weights, kind, flags, as_stream(stream), out, n_graphs,
+                         edge_off_host, node_off_host);
+}
+
+int slaq_graph_batch_info(slaq_graph g, int *n_graphs, int64_t *node_off, double *trace) {
+  if (!g) return set_error(SLAQ_EINVAL, "NULL graph");
+  if (n_graphs) *n_graphs = g->n_graphs;
+  if (node_off) std::memcpy(node_off, g->goff.data(), g->goff.size() * sizeof(int64_t));
+  if (trace) std::memcpy(trace, g->gtrace.data(), g->gtrace.size() * sizeof(double));
+  return SLAQ_OK;
+}
+
+int slaq_krylov_batch_info(slaq_krylov k, int *n_graphs) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  if (n_graphs) *n_graphs = k->n_graphs;
+  return SLAQ_OK;
+}
+
 int slaq_graph_info(slaq_graph g, int64_t *n, int64_t *nnz, double *trace, int64_t *n_input) {
   if (!g) return set_error(SLAQ_EINVAL, "NULL graph");
   if (n) *n = g->n;
@@ -257,10 +282,12 @@ int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, v
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
   cudaStream_t st = as_stream(stream);
-  const size_t ns = (size_t)k->nv * k->s;
+  const size_t ns = (size_t)k->n_graphs * k->nv * k->s;
   if (alpha) SLAQ_CHECK_CUDA(cudaMemcpyAsync(alpha, k->alpha, ns * 8, cudaMemcpyDeviceToDevice, st));
   if (beta) SLAQ_CHECK_CUDA(cudaMemcpyAsync(beta, k->beta, ns * 8, cudaMemcpyDeviceToDevice, st));
-  if (m) SLAQ_CHECK_CUDA(cudaMemcpyAsync(m, k->m, k->nv * 4, cudaMemcpyDeviceToDevice, st));
+  if (m)
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(m, k->m, (size_t)k->n_graphs * k->nv * 4,
+                                    cudaMemcpyDeviceToDevice, st));
   return SLAQ_OK;
 }
 
@@ -268,7 +295,7 @@ int slaq_ritz_export(slaq_krylov k, double *theta, double *tau2, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
   cudaStream_t st = as_stream(stream);
-  const size_t ns = (size_t)k->nv * k->s;
+  const size_t ns = (size_t)k->n_graphs * k->nv * k->s;
   if (theta) SLAQ_CHECK_CUDA(cudaMemcpyAsync(theta, k->theta, ns * 8, cudaMemcpyDeviceToDevice, st));
   if (tau2) SLAQ_CHECK_CUDA(cudaMemcpyAsync(tau2, k->tau2, ns * 8, cudaMemcpyDeviceToDevice, st));
   return SLAQ_OK;

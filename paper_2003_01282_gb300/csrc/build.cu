@@ -257,6 +257,80 @@ __global__ void k_validate(const int32_t *src, const int32_t *dst, const double 
   }
 }
 
+// Batches: edge e of graph g (edge_off[g] <= e < edge_off[g+1]) has local
+// ids in [0, n_g); write union ids (node_off[g] + local) and flag bad ids.
+__device__ __forceinline__ int find_segment(const int64_t *off, int G, int64_t x) {
+  int lo = 0, hi = G;  // off[lo] <= x < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_union_ids(const int32_t *src, const int32_t *dst, const double *w, int64_t m,
+                            const int64_t *edge_off, const int64_t *node_off, int G, int32_t *usrc,
+                            int32_t *udst, int32_t *bad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int g = find_segment(edge_off, G, e);
+    const int64_t ng = node_off[g + 1] - node_off[g];
+    const int32_t a = src[e], b = dst[e];
+    if (a < 0 || b < 0 || a >= ng || b >= ng) atomicOr(bad, 1);
+    if (w && !(w[e] > 0.0)) atomicOr(bad, 2);
+    usrc[e] = (int32_t)(node_off[g] + (a < 0 ? 0 : a));
+    udst[e] = (int32_t)(node_off[g] + (b < 0 ? 0 : b));
+  }
+}
+
+// Graph of every kept node (canonical order), its id within its graph, and
+// per-graph statistics: kept nodes, non-isolated nodes, integer degree sum,
+// largest degree (non-negative doubles order like their bit patterns).  One
+// thread per node; a warp whose nodes share one graph adds its sums once.
+__global__ void k_node_graph(const int64_t *old_id, const double *deg, int64_t n,
+                             const int64_t *node_off, int G, int32_t *gid, int64_t *local,
+                             unsigned long long *kept, unsigned long long *nonisol,
+                             unsigned long long *degsum, unsigned long long *maxdeg) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool valid = i < n;
+  int g = -1;
+  unsigned long long c_kept = 0, c_non = 0, c_sum = 0, c_max = 0;
+  if (valid) {
+    g = find_segment(node_off, G, old_id[i]);
+    gid[i] = g;
+    local[i] = old_id[i] - node_off[g];
+    const double d = deg[i];
+    c_kept = 1;
+    c_non = d > 0.0 ? 1 : 0;
+    c_sum = (unsigned long long)d;
+    c_max = (unsigned long long)__double_as_longlong(d);
+  }
+  const int g0 = __shfl_sync(0xffffffffu, g, 0);
+  const bool uniform = __all_sync(0xffffffffu, !valid || g == g0) && g0 >= 0;
+  if (uniform) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c_kept += __shfl_down_sync(0xffffffffu, c_kept, o);
+      c_non += __shfl_down_sync(0xffffffffu, c_non, o);
+      c_sum += __shfl_down_sync(0xffffffffu, c_sum, o);
+      const unsigned long long other = __shfl_down_sync(0xffffffffu, c_max, o);
+      c_max = other > c_max ? other : c_max;
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(kept + g0, c_kept);
+      if (c_non) atomicAdd(nonisol + g0, c_non);
+      atomicAdd(degsum + g0, c_sum);
+      atomicMax(maxdeg + g0, c_max);
+    }
+  } else if (valid) {
+    atomicAdd(kept + g, c_kept);
+    if (c_non) atomicAdd(nonisol + g, c_non);
+    atomicAdd(degsum + g, c_sum);
+    atomicMax(maxdeg + g, c_max);
+  }
+}
+
 // Both orientations of every non-loop edge; slots taken with one atomic per
 // warp, so the emission order is arbitrary (the sort removes it).
 __global__ void k_emit(const int32_t *src, const int32_t *dst, const double *w, int64_t m, int cb,
@@ -423,12 +497,14 @@ __global__ void k_heavy_table(const int32_t *is_heavy, const int64_t *slot_of,
   if (blockIdx.x == 0 && threadIdx.x == 0) heavy_first[n_heavy] = n_chunks;
 }
 
-// Sort key of the execution order: descending entry count, then id.
-__global__ void k_perm_keys(const int64_t *rowptr, int64_t n, int cb, uint64_t *key) {
+// Sort key of the execution order: graph, then descending entry count,
+// then id (graph | n - count | id, from high bits to low).
+__global__ void k_perm_keys(const int64_t *rowptr, const int32_t *gid, int64_t n, int cb, int db,
+                            uint64_t *key) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t cnt = (uint64_t)(rowptr[i + 1] - rowptr[i]);
-    key[i] = (((uint64_t)n - cnt) << cb) | (uint64_t)i;
+    key[i] = ((((uint64_t)gid[i] << db) | ((uint64_t)n - cnt)) << cb) | (uint64_t)i;
   }
 }
 
@@ -462,9 +538,10 @@ __global__ void k_perm_entries(const uint64_t *ukey, const int64_t *newid, int d
   }
 }
 
-__global__ void k_perm_nodes(const double *diag, const double *scale, const int64_t *old_id,
-                             const int64_t *perm, int64_t n, double *xdiag, double *xscale,
-                             float *xdiag32, float *xscale32, int64_t *xold) {
+__global__ void k_perm_nodes(const double *diag, const double *scale, const int64_t *local,
+                             const int32_t *gid, const int64_t *perm, int64_t n, double *xdiag,
+                             double *xscale, float *xdiag32, float *xscale32, int64_t *xold,
+                             int32_t *xgraph) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = perm[r];
@@ -472,7 +549,8 @@ __global__ void k_perm_nodes(const double *diag, const double *scale, const int6
     xscale[r] = scale[i];
     xdiag32[r] = (float)diag[i];
     xscale32[r] = (float)scale[i];
-    xold[r] = old_id[i];
+    xold[r] = local[i];
+    xgraph[r] = gid[i];
   }
 }
 
@@ -501,7 +579,8 @@ void graph_free(slaq_graph g) {
   void *ptrs[] = {g->rowptr, g->colidx, g->vals, g->vals32, g->diag, g->scale, g->diag32,
                   g->scale32, g->old_id, g->heavy_row, g->heavy_first, g->chunk_slot,
                   g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32, g->x_diag, g->x_scale,
-                  g->x_diag32, g->x_scale32, g->x_old_id};
+                  g->x_diag32, g->x_scale32, g->x_old_id, g->goff_dev, g->gn_dev,
+                  g->gtrace_dev, g->gbound_dev, g->x_graph};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -539,8 +618,25 @@ int persistent(T **p, size_t count) {
 
 int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
                     const double *weights, int kind, int flags, cudaStream_t st,
-                    slaq_graph *out) {
+                    slaq_graph *out, int n_graphs, const int64_t *edge_off_host,
+                    const int64_t *node_off_host) {
   if (!out) return set_error(SLAQ_EINVAL, "out is NULL");
+  const bool batch = n_graphs > 1 || edge_off_host || node_off_host;
+  std::vector<int64_t> node_off{0, n};
+  if (batch) {
+    if (n_graphs < 1 || n_graphs > 65536 || !edge_off_host || !node_off_host)
+      return set_error(SLAQ_EINVAL, "a batch needs 1..65536 graphs and both offset arrays");
+    if (edge_off_host[0] != 0 || node_off_host[0] != 0)
+      return set_error(SLAQ_EINVAL, "offsets must start at 0");
+    for (int g = 0; g < n_graphs; ++g) {
+      if (edge_off_host[g + 1] < edge_off_host[g] || node_off_host[g + 1] <= node_off_host[g])
+        return set_error(SLAQ_EINVAL, "graph %d: offsets must increase (every graph needs a node)", g);
+    }
+    m = edge_off_host[n_graphs];
+    n = node_off_host[n_graphs];
+    node_off.assign(node_off_host, node_off_host + n_graphs + 1);
+  }
+  const int G = batch ? n_graphs : 1;
   *out = nullptr;
   if (n < 0 || m < 0) return set_error(SLAQ_EINVAL, "negative n_nodes or n_edges");
   if (kind != SLAQ_NORMALIZED && kind != SLAQ_COMBINATORIAL)
@@ -554,13 +650,32 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   ProfScope prof(SLAQ_PROF_BUILD, st);
   Temps tmp(st);
 
-  // 1. validate
+  // 1. validate (batches: local ids per graph, converted to union ids)
+  int64_t *d_node_off = nullptr;
+  SLAQ_TRY(tmp.get(&d_node_off, G + 1));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_node_off, node_off.data(), (G + 1) * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, st));
   if (m > 0) {
     int32_t *bad = nullptr;
     SLAQ_TRY(tmp.get(&bad, 1));
     SLAQ_CHECK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
-    ++tl_launches;
-    k_validate<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, n, bad);
+    if (batch) {
+      int64_t *d_edge_off = nullptr;
+      int32_t *usrc = nullptr, *udst = nullptr;
+      SLAQ_TRY(tmp.get(&d_edge_off, G + 1));
+      SLAQ_TRY(tmp.get(&usrc, m));
+      SLAQ_TRY(tmp.get(&udst, m));
+      SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_edge_off, edge_off_host, (G + 1) * sizeof(int64_t),
+                                      cudaMemcpyHostToDevice, st));
+      ++tl_launches;
+      k_union_ids<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, d_edge_off, d_node_off, G,
+                                                    usrc, udst, bad);
+      src = usrc;
+      dst = udst;
+    } else {
+      ++tl_launches;
+      k_validate<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, n, bad);
+    }
     SLAQ_CHECK_LAUNCH("validate");
     int32_t hbad = 0;
     SLAQ_TRY(to_host(&hbad, bad, 1, st));
@@ -685,25 +800,72 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
     SLAQ_CHECK_LAUNCH("values");
   }
 
-  // trace and spectral bound
-  if (kind == SLAQ_NORMALIZED) {
-    g->trace = (double)n_nonisolated;
-    g->bound = 2.0;
-  } else {
+  // per-graph bookkeeping: graph of each kept node, kept counts, traces, bounds
+  int32_t *gid = nullptr;
+  int64_t *local = nullptr;
+  unsigned long long *stats = nullptr;  // [4][G]: kept, non-isolated, degree sum, max degree
+  SLAQ_TRY(tmp.get(&gid, n_out));
+  SLAQ_TRY(tmp.get(&local, n_out));
+  SLAQ_TRY(tmp.get(&stats, 4 * (size_t)G));
+  SLAQ_CHECK_CUDA(cudaMemsetAsync(stats, 0, 4 * (size_t)G * sizeof(unsigned long long), st));
+  if (n_out > 0) {
+    ++tl_launches;
+    k_node_graph<<<(unsigned)ceil_div(n_out, 256), 256, 0, st>>>(g->old_id, deg, n_out, d_node_off, G, gid,
+                                                       local, stats, stats + G, stats + 2 * G,
+                                                       stats + 3 * G);
+    SLAQ_CHECK_LAUNCH("node_graph");
+  }
+  std::vector<unsigned long long> hst(4 * (size_t)G);
+  SLAQ_TRY(to_host(hst.data(), stats, 4 * (size_t)G, st));
+  g->n_graphs = G;
+  g->goff.assign(G + 1, 0);
+  g->gtrace.assign(G, 0.0);
+  g->gbound.assign(G, 0.0);
+  for (int q = 0; q < G; ++q) {
+    g->goff[q + 1] = g->goff[q] + (int64_t)hst[q];
+    const double mx = __builtin_bit_cast(double, (long long)hst[3 * G + q]);
+    if (kind == SLAQ_NORMALIZED) {
+      g->gtrace[q] = (double)hst[G + q];
+      g->gbound[q] = 2.0;
+    } else {
+      g->gtrace[q] = (double)hst[2 * G + q];  // integer degrees: exact
+      g->gbound[q] = 2.0 * mx;
+    }
+  }
+  if (kind == SLAQ_COMBINATORIAL && weighted) {
+    // weighted degrees: Neumaier-compensated sums on the host, graph by graph
     std::vector<double> hdeg(n_out);
     if (n_out > 0) SLAQ_TRY(to_host(hdeg.data(), deg, n_out, st));
-    double s = 0.0, c = 0.0, mx = 0.0;   // Neumaier-compensated sum of degrees
-    for (double d : hdeg) {
-      double t = s + d;
-      c += std::fabs(s) >= std::fabs(d) ? (s - t) + d : (d - t) + s;
-      s = t;
-      mx = std::max(mx, d);
+    for (int q = 0; q < G; ++q) {
+      double sm = 0.0, c = 0.0;
+      for (int64_t i = g->goff[q]; i < g->goff[q + 1]; ++i) {
+        const double d = hdeg[i];
+        const double t = sm + d;
+        c += std::fabs(sm) >= std::fabs(d) ? (sm - t) + d : (d - t) + sm;
+        sm = t;
+      }
+      g->gtrace[q] = sm + c;
     }
-    g->trace = s + c;
-    g->bound = 2.0 * mx;
+  }
+  g->trace = g->gtrace[0];
+  g->bound = *std::max_element(g->gbound.begin(), g->gbound.end());
+  {
+    std::vector<double> gn(G);
+    for (int q = 0; q < G; ++q) gn[q] = (double)(g->goff[q + 1] - g->goff[q]);
+    SLAQ_TRY(persistent(&g->goff_dev, G + 1));
+    SLAQ_TRY(persistent(&g->gn_dev, G));
+    SLAQ_TRY(persistent(&g->gtrace_dev, G));
+    SLAQ_TRY(persistent(&g->gbound_dev, G));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->goff_dev, g->goff.data(), (G + 1) * sizeof(int64_t),
+                               cudaMemcpyHostToDevice));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->gn_dev, gn.data(), G * sizeof(double), cudaMemcpyHostToDevice));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->gtrace_dev, g->gtrace.data(), G * sizeof(double),
+                               cudaMemcpyHostToDevice));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->gbound_dev, g->gbound.data(), G * sizeof(double),
+                               cudaMemcpyHostToDevice));
   }
 
-  // 5. execution copy in descending-degree order
+  // 5. execution copy: graph-major, then descending degree, then id
   SLAQ_TRY(persistent(&g->x_rowptr, n_out + 1));
   SLAQ_TRY(persistent(&g->x_colidx, nnz));
   SLAQ_TRY(persistent(&g->x_vals, nnz));
@@ -713,8 +875,12 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   SLAQ_TRY(persistent(&g->x_diag32, n_out));
   SLAQ_TRY(persistent(&g->x_scale32, n_out));
   SLAQ_TRY(persistent(&g->x_old_id, n_out));
+  SLAQ_TRY(persistent(&g->x_graph, n_out));
   if (n_out > 0) {
     const int pcb = bits_for(n_out);
+    const int pdb = bits_for(n_out + 1);
+    const int pgb = G > 1 ? bits_for(G) : 0;
+    if (pcb + pdb + pgb > 64) return set_error(SLAQ_EUNSUPPORTED, "batch too large to order");
     uint64_t *pk0 = nullptr, *pk1 = nullptr;
     int64_t *perm = nullptr, *inv = nullptr, *xcnt = nullptr;
     SLAQ_TRY(tmp.get(&pk0, n_out));
@@ -723,9 +889,9 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
     SLAQ_TRY(tmp.get(&inv, n_out));
     SLAQ_TRY(tmp.get(&xcnt, n_out));
     ++tl_launches;
-    k_perm_keys<<<grid_for(n_out, 256), 256, 0, st>>>(g->rowptr, n_out, pcb, pk0);
+    k_perm_keys<<<grid_for(n_out, 256), 256, 0, st>>>(g->rowptr, gid, n_out, pcb, pdb, pk0);
     SLAQ_CHECK_LAUNCH("perm_keys");
-    SLAQ_TRY(radix_sort(&pk0, &pk1, nullptr, nullptr, n_out, pcb + bits_for(n_out + 1), st));
+    SLAQ_TRY(radix_sort(&pk0, &pk1, nullptr, nullptr, n_out, pcb + pdb + pgb, st));
     ++tl_launches;
     k_perm_index<<<grid_for(n_out, 256), 256, 0, st>>>(pk0, g->rowptr, n_out, pcb, perm, inv, xcnt);
     SLAQ_CHECK_LAUNCH("perm_index");
@@ -739,9 +905,9 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
           g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32);
     }
     ++tl_launches;
-    k_perm_nodes<<<grid_for(n_out, 256), 256, 0, st>>>(g->diag, g->scale, g->old_id, perm, n_out,
+    k_perm_nodes<<<grid_for(n_out, 256), 256, 0, st>>>(g->diag, g->scale, local, gid, perm, n_out,
                                                        g->x_diag, g->x_scale, g->x_diag32,
-                                                       g->x_scale32, g->x_old_id);
+                                                       g->x_scale32, g->x_old_id, g->x_graph);
     SLAQ_CHECK_LAUNCH("perm");
   } else {
     SLAQ_CHECK_CUDA(cudaMemsetAsync(g->x_rowptr, 0, sizeof(int64_t), st));

@@ -7,6 +7,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <vector>
 
 #include "slaq.h"
 
@@ -84,14 +85,26 @@ constexpr int kHeavyChunk = 512;   // nnz per work item of a split (heavy) row
 
 struct slaq_graph_s {
   int device = -1;
-  int64_t n_input = 0;   // n_nodes given at build time
-  int64_t n = 0;         // kept nodes n'
+  int64_t n_input = 0;   // n_nodes given at build time (sum over a batch)
+  int64_t n = 0;         // kept nodes n' (sum over a batch)
   int64_t nnz = 0;       // stored off-diagonal entries
   int kind = 0;
   int flags = 0;
   bool weighted = false;
-  double trace = 0.0;    // tr(L)
-  double bound = 0.0;    // Gershgorin bound of the spectrum
+  double trace = 0.0;    // tr(L) (of graph 0 for a batch)
+  double bound = 0.0;    // Gershgorin bound of the spectrum (largest over a batch)
+  // A batch of G graphs is one block-diagonal Laplacian; graph g owns the
+  // kept nodes [goff[g], goff[g+1]) in both the canonical and the execution
+  // order.  A single graph is the batch G = 1.
+  int n_graphs = 1;
+  std::vector<int64_t> goff;        // [G+1] host copy
+  std::vector<double> gtrace;       // [G] tr(L_g)
+  std::vector<double> gbound;       // [G] bound of the spectrum of L_g
+  int64_t *goff_dev = nullptr;      // [G+1]
+  double *gn_dev = nullptr;         // [G] node counts as double
+  double *gtrace_dev = nullptr;     // [G]
+  double *gbound_dev = nullptr;     // [G]
+  int32_t *x_graph = nullptr;       // [n] graph of each execution row
   int64_t *rowptr = nullptr;   // [n+1]
   int32_t *colidx = nullptr;   // [nnz]
   double *vals = nullptr;      // [nnz] off-diagonal values (FP64)
@@ -112,7 +125,7 @@ struct slaq_graph_s {
   float *x_vals32 = nullptr;    // [nnz] (weighted only)
   double *x_diag = nullptr, *x_scale = nullptr;    // [n]
   float *x_diag32 = nullptr, *x_scale32 = nullptr; // [n]
-  int64_t *x_old_id = nullptr;  // [n]
+  int64_t *x_old_id = nullptr;  // [n] original id within its graph
   // SpMM schedule (execution order) for rows with more than heavy_degree
   // entries: each such row is split into chunks of kHeavyChunk entries.
   int64_t heavy_degree = 0;
@@ -134,7 +147,7 @@ struct slaq_krylov_s {
   int kind = 0;
   double trace = 0.0, bound = 0.0, tol = 0.0;
   int G = 0;              // row blocks the partials buffer holds
-  int Gdots = 0;          // row blocks of the last dots launch
+  int dsub = 1;           // pieces per dots chunk in the last dots launch
   void *U = nullptr;      // [s][n_cap][ld] basis (TB)
   void *Z = nullptr;      // [n_cap][ld] L u_k (TW)
   void *P = nullptr;      // [chunk_cap][ld] partial sums of split rows (TW)
@@ -150,6 +163,20 @@ struct slaq_krylov_s {
   int32_t *status = nullptr;  // [1] device-side error flags
   uint32_t *hcount = nullptr; // [n_heavy * slices] arrival counters of split rows (kept zero)
   int64_t hcount_cap = 0;
+  // batches: G graphs; per-graph arrays are [G][...] (alpha [G][nv][s], ...)
+  int n_graphs = 1;
+  double *gn = nullptr;      // [G] node counts
+  double *gtrace = nullptr;  // [G] tr(L_g)
+  double *gbound = nullptr;  // [G] spectral bounds (breakdown tolerance)
+  int64_t gcap = 0;          // graphs the per-graph arrays hold
+  // row chunks inside one graph: dots (d*) and update (u*) kernels
+  std::vector<int64_t> hd_row0, hu_row0;
+  std::vector<int32_t> hd_rows, hd_graph, hu_rows, hu_graph;
+  std::vector<int32_t> hd_goff;  // [G+1] first dots chunk of each graph
+  int64_t *d_row0 = nullptr, *u_row0 = nullptr;
+  int32_t *d_rows = nullptr, *u_rows = nullptr, *u_graph = nullptr, *d_goff = nullptr;
+  int64_t dcap = 0, ucap = 0;
+  int n_dchunks = 0, n_uchunks = 0;
   // side stream on which the split-row SpMM runs beside the light rows
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -159,7 +186,8 @@ namespace slaq {
 // internal entry points (definitions in build.cu, lanczos.cu, quad.cu)
 int build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges, int64_t n_nodes,
                     const double *weights, int kind, int flags, cudaStream_t st,
-                    slaq_graph *out);
+                    slaq_graph *out, int n_graphs = 1, const int64_t *edge_off_host = nullptr,
+                    const int64_t *node_off_host = nullptr);
 void graph_free(slaq_graph g);
 int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
                 int reorth, cudaStream_t st, slaq_krylov *inout);

@@ -178,8 +178,9 @@ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
 }
 
 template <int P>
-__global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id, Slc S, int nv,
-                             uint64_t seed, uint64_t graph_id) {
+__global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id,
+                             const int32_t *xgraph, Slc S, int nv, uint64_t seed,
+                             uint64_t graph_id) {
   using TB = typename Form<P>::TB;
   const int64_t n = S.n;
   const int ld = S.ld;
@@ -193,7 +194,8 @@ __global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id, Sl
     const int64_t off = cbase + i * stride;
     float v = 0.0f;
     if (p < nv) {
-      const uint64_t c = (graph_id << 48) | ((uint64_t)p << 32) | (uint64_t)old_id[i];
+      const uint64_t gfield = (graph_id + (uint64_t)xgraph[i]) & 0xffffull;
+      const uint64_t c = (gfield << 48) | ((uint64_t)p << 32) | (uint64_t)old_id[i];
       const uint64_t z = splitmix64_mix(seed + 0x9E3779B97F4A7C15ull * (c + 1ull));
       v = (z >> 63) ? -1.0f : 1.0f;
     }
@@ -214,12 +216,16 @@ __global__ void k_probe_export(double *out, const int64_t *old_id, int64_t n, in
   }
 }
 
-__global__ void k_init_scalars(double *alpha, double *beta, int32_t *m, int nv, int s) {
-  for (int i = threadIdx.x; i < nv * s; i += blockDim.x) {
+__global__ void k_init_scalars(double *alpha, double *beta, int32_t *m, int64_t nvs, int64_t nvt,
+                               int s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvs;
+       i += (int64_t)gridDim.x * blockDim.x) {
     alpha[i] = 0.0;
     beta[i] = 0.0;
   }
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) m[i] = s;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvt;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m[i] = s;
 }
 
 // ------------------------------------------------------------------ SpMM
@@ -496,8 +502,9 @@ __device__ __forceinline__ void stage_rows(T *dst, const T *src, const Slc &S, i
 template <int P, bool X_IS_BASIS, bool WITH_G>
 __global__ void __launch_bounds__(512, 2)
     k_dots(const typename Form<P>::TB *__restrict__ U, const void *__restrict__ Xv,
-           const typename Form<P>::TB *__restrict__ Uk, Slc S, int64_t rows_per_block,
-           int64_t ustride, int jfirst, int jlast, int Jb, double *__restrict__ part, int s) {
+           const typename Form<P>::TB *__restrict__ Uk, Slc S, const int64_t *__restrict__ crow0,
+           const int32_t *__restrict__ crows, int sub, int64_t ustride, int jfirst, int jlast,
+           int Jb, double *__restrict__ part, int s) {
   using TB = typename Form<P>::TB;
   using TW = typename Form<P>::TW;
   using TX = typename std::conditional<X_IS_BASIS, TB, TW>::type;
@@ -514,8 +521,12 @@ __global__ void __launch_bounds__(512, 2)
   const int j = jfirst + (int)blockIdx.y * Jb + (int)threadIdx.y;
   const bool active = j <= jlast;  // idle threads still stage and synchronize
   const int col = threadIdx.x * VE;
-  const int64_t r0 = (int64_t)g * rows_per_block;
-  const int64_t r1 = min(S.n, r0 + rows_per_block);
+  // block g covers part (g % sub) of chunk (g / sub); partials are indexed by g
+  const int chunk = g / sub, piece = g - chunk * sub;
+  const int64_t cr = crows[chunk];
+  const int64_t per = (cr + sub - 1) / sub;
+  const int64_t r0 = crow0[chunk] + min(cr, per * piece);
+  const int64_t r1 = crow0[chunk] + min(cr, per * (piece + 1));
   const int ntile = (int)((r1 - r0 + kTile - 1) / kTile);
   int stride;
   const int64_t off = S.base(col, stride);
@@ -604,41 +615,42 @@ inline size_t dots_smem(int precision, int ld, bool x_is_basis) {
   return (size_t)2 * kTile * ld * (bx + basis_bytes(precision));
 }
 
-// Sum the G block partials (Neumaier, fixed order) of d_j and, with_g, of
-// g_j for j in [jfirst, jfirst + jcount).  d goes to dsum[j][p]; g_j is the
-// Gram entry (j, k), stored symmetrically in gram[j][k][p] and gram[k][j][p].
-// Block (32, kRedY): x = column, y strides over the blocks' partials.
+// Sum the partials of graph g's chunks [goff[g], goff[g+1]) of d_j and, with_g,
+// of the Gram column, for j in [jfirst, jfirst + jcount): d to dsum[g][j][p];
+// g_j is the Gram entry (j, k), stored in gram[g][j][k][p] and gram[g][k][j][p].
+// Block (32, kRedY): x = column, y strides over the chunks; grid
+// (columns / 32, 1 or 2, G).
 constexpr int kRedY = 32;
-__global__ void k_dot_reduce(const double *__restrict__ part, int G, int s, int ld, int jfirst,
-                             int jcount, int k, int with_g, double *__restrict__ dsum,
-                             double *__restrict__ gram) {
-  __shared__ double ss[kRedY][33], sc[kRedY][33];
+__global__ void k_dot_reduce(const double *__restrict__ part, const int32_t *__restrict__ goff,
+                             int sub, int s, int ld, int jfirst, int jcount, int k,
+                             double *__restrict__ dsum, double *__restrict__ gram) {
+  __shared__ double ss[kRedY][33];
   const int ncol = jcount * ld;
   const int col = blockIdx.x * 32 + threadIdx.x;
   const int which = blockIdx.y;  // 0: d, 1: g
-  const bool valid = col < ncol && (which == 0 || with_g);
+  const int gr = blockIdx.z;
+  const bool valid = col < ncol;
   const int j = jfirst + (valid ? col / ld : 0);
   const int p = valid ? col % ld : 0;
-  // plain FP64 sums of the strided partials (a few dozen terms; FP64 is
-  // scarce on this chip), compensated combination of the kRedY sums
+  // plain FP64 sums of the strided partials (few terms; FP64 is scarce on
+  // this chip), compensated combination of the kRedY sums
   double acc = 0.0;
   if (valid)
-    for (int g = threadIdx.y; g < G; g += kRedY) acc += part[(((int64_t)g * 2 + which) * s + j) * ld + p];
+    for (int c = goff[gr] * sub + threadIdx.y; c < goff[gr + 1] * sub; c += kRedY)
+      acc += part[(((int64_t)c * 2 + which) * s + j) * ld + p];
   ss[threadIdx.y][threadIdx.x] = acc;
-  sc[threadIdx.y][threadIdx.x] = 0.0;
   __syncthreads();
   if (threadIdx.y == 0 && valid) {
     Neumaier tot;
-    for (int y = 0; y < kRedY; ++y) {
-      tot.add(ss[y][threadIdx.x]);
-      tot.add(sc[y][threadIdx.x]);
-    }
+    for (int y = 0; y < kRedY; ++y) tot.add(ss[y][threadIdx.x]);
     const double v = tot.value();
+    const int64_t gs = (int64_t)gr * s;
     if (which == 0) {
-      dsum[j * ld + p] = v;
+      dsum[(gs + j) * ld + p] = v;
     } else {
-      gram[((int64_t)j * s + k) * ld + p] = v;
-      gram[((int64_t)k * s + j) * ld + p] = v;
+      double *gm = gram + (int64_t)gr * s * s * ld;
+      gm[((int64_t)j * s + k) * ld + p] = v;
+      gm[((int64_t)k * s + j) * ld + p] = v;
     }
   }
 }
@@ -655,16 +667,27 @@ __global__ void k_dot_reduce(const double *__restrict__ part, int G, int s, int 
 // (stopping the probe with m = k if beta_{k-1} <= tol_abs) and
 // alpha_k = d_k / nu_k^2.  need_coef == 0 on the last step.
 constexpr int kMaxS = 64;
-__global__ void k_solve(const double *__restrict__ dsum, const double *__restrict__ gram, int k,
-                        int s, int ld, int nv, int first_pass, int need_coef, double tol_abs,
-                        int32_t *__restrict__ m, double *__restrict__ alpha,
-                        double *__restrict__ beta, double *__restrict__ coef) {
-  __shared__ double A[kMaxS * kMaxS];  // Gram block, factored in place (lower)
-  __shared__ double y[kMaxS], sc[kMaxS];
+__global__ void k_solve(const double *__restrict__ dsum_all, const double *__restrict__ gram_all,
+                        int k, int s, int ld, int nv, int first_pass, int need_coef, double tol,
+                        const double *__restrict__ gbound, int32_t *__restrict__ m_all,
+                        double *__restrict__ alpha_all, double *__restrict__ beta_all,
+                        double *__restrict__ coef_all) {
+  extern __shared__ double sol_smem[];  // A [K1*K1], y [K1], sc [K1]
   __shared__ int run_flag;
   const int p = blockIdx.x;
+  const int gr = blockIdx.y;
   const int K1 = k + 1;
+  double *A = sol_smem;
+  double *y = A + K1 * K1;
+  double *sc = y + K1;
   const int lane = threadIdx.x;
+  const double *gram = gram_all + (int64_t)gr * s * s * ld;
+  const double *dsum = dsum_all + (int64_t)gr * s * ld;
+  double *coef = coef_all + (int64_t)gr * s * ld;
+  int32_t *m = m_all + (int64_t)gr * nv;
+  double *alpha = alpha_all + (int64_t)gr * nv * s;
+  double *beta = beta_all + (int64_t)gr * nv * s;
+  const double tol_abs = tol * gbound[gr];
   if (lane == 0) {
     bool running = p < nv && m[p] > k;
     if (running && first_pass) {
@@ -739,13 +762,17 @@ __global__ void k_solve(const double *__restrict__ dsum, const double *__restric
 template <int P, bool SECOND>
 __global__ void __launch_bounds__(256)
     k_update(const typename Form<P>::TB *__restrict__ U, const typename Form<P>::TW *__restrict__ Z,
-             typename Form<P>::TB *Unext, Slc S, int64_t rows_per_block, int V, int R,
-             int64_t ustride, int k, const double *__restrict__ coef,
-             const int32_t *__restrict__ m, int nv) {
+             typename Form<P>::TB *Unext, Slc S, const int64_t *__restrict__ crow0,
+             const int32_t *__restrict__ crows, const int32_t *__restrict__ cgraph, int V, int R,
+             int64_t ustride, int k, int s, const double *__restrict__ coef_all,
+             const int32_t *__restrict__ m_all, int nv) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   extern __shared__ __align__(16) unsigned char dyn[];
   const int ld = S.ld;
+  const int gr = cgraph[blockIdx.x];
+  const double *coef = coef_all + (int64_t)gr * s * ld;
+  const int32_t *m = m_all + (int64_t)gr * nv;
   TW *cf = reinterpret_cast<TW *>(dyn);  // [(k+1) * ld]
   for (int i = threadIdx.x; i < (k + 1) * ld; i += blockDim.x) cf[i] = (TW)coef[i];
   __syncthreads();
@@ -757,8 +784,8 @@ __global__ void __launch_bounds__(256)
     const int p = lane * VE + v;
     keep[v] = p < nv && m[p] > k;
   }
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-  const int64_t r1 = min(S.n, r0 + rows_per_block);
+  const int64_t r0 = crow0[blockIdx.x];
+  const int64_t r1 = r0 + crows[blockIdx.x];
   int stride;
   const int64_t off = S.base(lane * VE, stride);
   for (int64_t row = r0 + team; row < r1; row += R) {
@@ -795,34 +822,15 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------ host side
+constexpr int kMaxSub = 16;  // most pieces a dots chunk is split into
+
 struct Geometry {
   int V, R, threads;      // teams of V threads, R rows per pass (update)
   Slc S;                  // probe slicing of the basis and work vectors
   int Vt, Rt, tthreads;   // SpMM: Vt threads per row and slice, Rt rows per block
   int sms;
   int Jb;                 // basis vectors per dots block
-  int Gmax;               // most row blocks of the dots kernel (partials buffer rows)
-  int64_t upd_rows;       // rows per update block
-  int Gupd;               // update blocks
 };
-
-// Row blocks of the dots kernel: one full wave (every SM holds as many blocks
-// as registers, shared memory and threads allow), at most Gmax, at least 64
-// rows per block.
-template <typename Kern>
-inline void dots_grid(const Geometry &g, int64_t n, Kern kern, int threads, size_t smem, int *G,
-                      int64_t *rows) {
-  int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  int64_t want = (int64_t)g.sms * per_sm;
-  want = std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)g.Gmax, ceil_div(n, 64)}));
-  *rows = ceil_div(n, want);
-  *G = (int)ceil_div(n, *rows);
-}
 
 // Slice width: the whole row when n * ld fits the L2 budget; otherwise the
 // widest multiple of a 32-byte sector whose slice fits (no slicing if even
@@ -861,11 +869,58 @@ Geometry geometry(int precision, int ld, int64_t n, int sms) {
   g.R = std::max(1, 256 / g.V);
   g.threads = g.V * g.R;
   g.Jb = std::max(1, std::min(64, 512 / g.V));
-  g.Gmax = 8 * sms;
-  int64_t Gu = std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 8LL * g.R)), 16LL * sms);
-  g.upd_rows = std::max<int64_t>(1, ceil_div(n, Gu));
-  g.Gupd = (int)ceil_div(n, g.upd_rows);
   return g;
+}
+
+// Row chunks of about `rows` rows that never cross a graph boundary; every
+// graph gets at least one.  first[g] (optional) is graph g's first chunk.
+void make_chunks(const std::vector<int64_t> &goff, int64_t rows, std::vector<int64_t> &row0,
+                 std::vector<int32_t> &nr, std::vector<int32_t> &graph,
+                 std::vector<int32_t> *first) {
+  const int G = (int)goff.size() - 1;
+  row0.clear();
+  nr.clear();
+  graph.clear();
+  if (first) first->assign(G + 1, 0);
+  rows = std::max<int64_t>(1, rows);
+  for (int q = 0; q < G; ++q) {
+    const int64_t a = goff[q], b = goff[q + 1];
+    if (first) (*first)[q] = (int32_t)row0.size();
+    const int64_t nch = std::max<int64_t>(1, ceil_div(b - a, rows));
+    const int64_t per = std::max<int64_t>(1, ceil_div(b - a, nch));
+    for (int64_t r = a; r < b; r += per) {
+      row0.push_back(r);
+      nr.push_back((int32_t)std::min(per, b - r));
+      graph.push_back(q);
+    }
+  }
+  if (first) (*first)[G] = (int32_t)row0.size();
+}
+
+template <typename Kern>
+int blocks_per_sm(Kern kern, int threads, size_t smem) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm;
+}
+
+template <typename T>
+int grow(T **p, size_t count);
+
+template <typename T>
+int upload(T **dev, int64_t *cap, const std::vector<T> &host, cudaStream_t st) {
+  if ((int64_t)host.size() > *cap) {
+    SLAQ_TRY(grow(dev, host.size()));
+    *cap = (int64_t)host.size();
+  }
+  if (!host.empty())
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(*dev, host.data(), host.size() * sizeof(T),
+                                    cudaMemcpyHostToDevice, st));
+  return SLAQ_OK;
 }
 
 template <int P>
@@ -926,7 +981,8 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
 }
 
 // Dot products of basis vectors jfirst..jlast with X (z, or u_{k+1} when
-// x_is_basis), plus the Gram column of u_k when with_g.
+// x_is_basis), plus the Gram column of u_k when with_g; one block per dots
+// chunk and group of Jb basis vectors.
 template <int P>
 int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int jlast,
          bool x_is_basis, bool with_g, const void *X, cudaStream_t st) {
@@ -934,42 +990,48 @@ int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int j
   using TB = typename Form<P>::TB;
   const int jcount = jlast - jfirst + 1;
   const int Jb = std::min(jcount, geo.Jb);
-  int G;
-  int64_t rows;
   const size_t smem = dots_smem(P, K->ld, x_is_basis);
-  if (x_is_basis) dots_grid(geo, n, k_dots<P, true, false>, geo.V * Jb, smem, &G, &rows);
-  else if (with_g) dots_grid(geo, n, k_dots<P, false, true>, geo.V * Jb, smem, &G, &rows);
-  else dots_grid(geo, n, k_dots<P, false, false>, geo.V * Jb, smem, &G, &rows);
-  K->Gdots = G;
-  const dim3 grid(G, (unsigned)ceil_div(jcount, Jb));
+  // split every chunk so that small blocks (few basis vectors) still fill the SMs
+  int per_sm;
+  if (x_is_basis) per_sm = blocks_per_sm(k_dots<P, true, false>, geo.V * Jb, smem);
+  else if (with_g) per_sm = blocks_per_sm(k_dots<P, false, true>, geo.V * Jb, smem);
+  else per_sm = blocks_per_sm(k_dots<P, false, false>, geo.V * Jb, smem);
+  const int64_t want = (int64_t)geo.sms * per_sm;
+  const int sub = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSub, want / std::max(1, K->n_dchunks)));
+  K->dsub = sub;
+  const dim3 grid(K->n_dchunks * sub, (unsigned)ceil_div(jcount, Jb));
   const dim3 block(geo.V, Jb);
   const TB *U = static_cast<const TB *>(K->U);
   const TB *Uk = U + (int64_t)k * n * K->ld;
   const int64_t ustride = n * K->ld;
   ++tl_launches;
   if (x_is_basis)
-    k_dots<P, true, false><<<grid, block, smem, st>>>(U, X, Uk, geo.S, rows, ustride, jfirst, jlast,
-                                                   Jb, K->part, K->s);
+    k_dots<P, true, false><<<grid, block, smem, st>>>(U, X, Uk, geo.S, K->d_row0, K->d_rows, sub,
+                                                      ustride, jfirst, jlast, Jb, K->part, K->s);
   else if (with_g)
-    k_dots<P, false, true><<<grid, block, smem, st>>>(U, X, Uk, geo.S, rows, ustride, jfirst, jlast,
-                                                   Jb, K->part, K->s);
+    k_dots<P, false, true><<<grid, block, smem, st>>>(U, X, Uk, geo.S, K->d_row0, K->d_rows, sub,
+                                                      ustride, jfirst, jlast, Jb, K->part, K->s);
   else
-    k_dots<P, false, false><<<grid, block, smem, st>>>(U, X, Uk, geo.S, rows, ustride, jfirst, jlast,
-                                                    Jb, K->part, K->s);
+    k_dots<P, false, false><<<grid, block, smem, st>>>(U, X, Uk, geo.S, K->d_row0, K->d_rows, sub,
+                                                       ustride, jfirst, jlast, Jb, K->part, K->s);
   SLAQ_CHECK_LAUNCH("dots");
   return SLAQ_OK;
 }
 
-int reduce_and_solve(slaq_krylov K, const Geometry &geo, int k, int jfirst, int jcount,
-                     bool with_g, bool first_pass, bool need_coef, double tol_abs, cudaStream_t st) {
+int reduce_and_solve(slaq_krylov K, int k, int jfirst, int jcount, bool with_g, bool first_pass,
+                     bool need_coef, cudaStream_t st) {
   ProfScope prof(SLAQ_PROF_REDUCE, st);
-  const dim3 grid((unsigned)ceil_div((int64_t)jcount * K->ld, 32), with_g ? 2 : 1);
+  const dim3 grid((unsigned)ceil_div((int64_t)jcount * K->ld, 32), with_g ? 2 : 1,
+                  (unsigned)K->n_graphs);
   ++tl_launches;
-  k_dot_reduce<<<grid, dim3(32, kRedY), 0, st>>>(K->part, K->Gdots, K->s, K->ld, jfirst, jcount, k,
-                                             with_g ? 1 : 0, K->dsum, K->gram);
+  k_dot_reduce<<<grid, dim3(32, kRedY), 0, st>>>(K->part, K->d_goff, K->dsub, K->s, K->ld, jfirst,
+                                                 jcount, k, K->dsum, K->gram);
+  const int K1 = k + 1;
+  const size_t smem = (size_t)(K1 * K1 + 2 * K1) * sizeof(double);
   ++tl_launches;
-  k_solve<<<K->ld, 32, 0, st>>>(K->dsum, K->gram, k, K->s, K->ld, K->nv, first_pass ? 1 : 0,
-                                need_coef ? 1 : 0, tol_abs, K->m, K->alpha, K->beta, K->coef);
+  k_solve<<<dim3(K->ld, K->n_graphs), 32, smem, st>>>(
+      K->dsum, K->gram, k, K->s, K->ld, K->nv, first_pass ? 1 : 0, need_coef ? 1 : 0, K->tol,
+      K->gbound, K->m, K->alpha, K->beta, K->coef);
   SLAQ_CHECK_LAUNCH("reduce_and_solve");
   return SLAQ_OK;
 }
@@ -983,15 +1045,16 @@ int update(slaq_krylov K, const Geometry &geo, int64_t n, int k, bool second, cu
   TB *Unext = static_cast<TB *>(K->U) + (int64_t)(k + 1) * n * K->ld;
   const int64_t ustride = n * K->ld;
   const size_t smem = (size_t)(k + 1) * K->ld * sizeof(TW);
+  const TW *Z = static_cast<const TW *>(K->Z);
   ++tl_launches;
   if (second)
-    k_update<P, true><<<geo.Gupd, geo.threads, smem, st>>>(U, static_cast<const TW *>(K->Z), Unext,
-                                                           geo.S, geo.upd_rows, geo.V, geo.R,
-                                                           ustride, k, K->coef, K->m, K->nv);
+    k_update<P, true><<<K->n_uchunks, geo.threads, smem, st>>>(
+        U, Z, Unext, geo.S, K->u_row0, K->u_rows, K->u_graph, geo.V, geo.R, ustride, k, K->s,
+        K->coef, K->m, K->nv);
   else
-    k_update<P, false><<<geo.Gupd, geo.threads, smem, st>>>(U, static_cast<const TW *>(K->Z), Unext,
-                                                            geo.S, geo.upd_rows, geo.V, geo.R,
-                                                            ustride, k, K->coef, K->m, K->nv);
+    k_update<P, false><<<K->n_uchunks, geo.threads, smem, st>>>(
+        U, Z, Unext, geo.S, K->u_row0, K->u_rows, K->u_graph, geo.V, geo.R, ustride, k, K->s,
+        K->coef, K->m, K->nv);
   SLAQ_CHECK_LAUNCH("update");
   return SLAQ_OK;
 }
@@ -1001,7 +1064,6 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   using TB = typename Form<P>::TB;
   const int64_t n = gr->n;
   const Geometry geo = geometry(P, K->ld, n, num_sms());
-  if (geo.Gmax > K->G) return set_error(SLAQ_EINVAL, "internal: reduction workspace too small");
   static bool attr_set = false;
   if (!attr_set) {
     SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_update<P, false>,
@@ -1016,30 +1078,59 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
+  // chunk tables: dots chunks fill one wave; update chunks are smaller
+  {
+    const int Jb = std::min(K->s, geo.Jb);
+    const int per_sm = blocks_per_sm(k_dots<P, false, true>, geo.V * Jb, dots_smem(P, K->ld, false));
+    const int64_t want_d = (int64_t)geo.sms * per_sm;
+    const int64_t rows_d = std::max<int64_t>(64, ceil_div(n, want_d));
+    make_chunks(gr->goff, rows_d, K->hd_row0, K->hd_rows, K->hd_graph, &K->hd_goff);
+    const int64_t want_u = std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 8LL * geo.R)),
+                                             16LL * geo.sms);
+    const int64_t rows_u = std::max<int64_t>(1, ceil_div(n, want_u));
+    make_chunks(gr->goff, rows_u, K->hu_row0, K->hu_rows, K->hu_graph, nullptr);
+    K->n_dchunks = (int)K->hd_row0.size();
+    K->n_uchunks = (int)K->hu_row0.size();
+    int64_t c0 = K->dcap, c1 = K->dcap, c2 = K->dcap;
+    SLAQ_TRY(upload(&K->d_row0, &c0, K->hd_row0, st));
+    SLAQ_TRY(upload(&K->d_rows, &c1, K->hd_rows, st));
+    SLAQ_TRY(upload(&K->d_goff, &c2, K->hd_goff, st));
+    K->dcap = std::min({c0, c1, c2});
+    int64_t u0 = K->ucap, u1 = K->ucap, u2 = K->ucap;
+    SLAQ_TRY(upload(&K->u_row0, &u0, K->hu_row0, st));
+    SLAQ_TRY(upload(&K->u_rows, &u1, K->hu_rows, st));
+    SLAQ_TRY(upload(&K->u_graph, &u2, K->hu_graph, st));
+    K->ucap = std::min({u0, u1, u2});
+    if ((int64_t)K->n_dchunks * kMaxSub > K->G) {
+      SLAQ_TRY(grow(&K->part, (size_t)K->n_dchunks * kMaxSub * 2 * K->s * K->ld));
+      K->G = K->n_dchunks * kMaxSub;
+    }
+  }
   {
     ProfScope prof(SLAQ_PROF_PROBES, st);
+    const int64_t nvt = (int64_t)K->n_graphs * K->nv;
     ++tl_launches;
-    k_init_scalars<<<1, 256, 0, st>>>(K->alpha, K->beta, K->m, K->nv, K->s);
+    k_init_scalars<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nvt * K->s, 256), 1024)),
+                     256, 0, st>>>(K->alpha, K->beta, K->m, nvt * K->s, nvt, K->s);
     ++tl_launches;
     k_probe_init<P><<<(unsigned)std::min<int64_t>(ceil_div(n * K->ld, 256), 152LL * 64), 256, 0,
-                      st>>>(static_cast<TB *>(K->U), gr->x_old_id, geo.S, K->nv, K->seed,
-                            (uint64_t)K->graph_id);
+                      st>>>(static_cast<TB *>(K->U), gr->x_old_id, gr->x_graph, geo.S, K->nv,
+                            K->seed, (uint64_t)K->graph_id);
   }
   SLAQ_CHECK_LAUNCH("probe_init");
-  const double tol_abs = K->tol * gr->bound;
   for (int k = 0; k < K->s; ++k) {
     SLAQ_TRY(spmm<P>(gr, K, geo, k, st));
     const bool last = (k == K->s - 1);
     // last step: only alpha_k = d_k / G_kk and the Gram diagonal entry
     const int jfirst = last ? k : 0;
     SLAQ_TRY(dots<P>(K, geo, n, k, jfirst, k, false, true, K->Z, st));
-    SLAQ_TRY(reduce_and_solve(K, geo, k, jfirst, k - jfirst + 1, true, true, !last, tol_abs, st));
+    SLAQ_TRY(reduce_and_solve(K, k, jfirst, k - jfirst + 1, true, true, !last, st));
     if (last) break;
     SLAQ_TRY(update<P>(K, geo, n, k, false, st));
     if (K->reorth == 2) {
       const TB *Unext = static_cast<const TB *>(K->U) + (int64_t)(k + 1) * n * K->ld;
       SLAQ_TRY(dots<P>(K, geo, n, k, 0, k, true, false, Unext, st));
-      SLAQ_TRY(reduce_and_solve(K, geo, k, 0, k + 1, false, false, true, tol_abs, st));
+      SLAQ_TRY(reduce_and_solve(K, k, 0, k + 1, false, false, true, st));
       SLAQ_TRY(update<P>(K, geo, n, k, true, st));
     }
   }
@@ -1069,6 +1160,7 @@ int grow(T **p, size_t count) {
 int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st) {
   if (!g || !out) return set_error(SLAQ_EINVAL, "NULL graph or output");
   if (nv < 1 || graph_id < 0 || graph_id > 0xffff) return set_error(SLAQ_EINVAL, "bad nv or graph_id");
+  if (g->n_graphs != 1) return set_error(SLAQ_EUNSUPPORTED, "probe export is for single graphs");
   if (g->n == 0) return SLAQ_OK;
   ProfScope prof(SLAQ_PROF_PROBES, st);
   ++tl_launches;
@@ -1081,7 +1173,8 @@ int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaS
 void krylov_free(slaq_krylov k) {
   if (!k) return;
   void *ptrs[] = {k->U, k->Z, k->P, k->part, k->dsum, k->coef, k->gram, k->alpha, k->beta,
-                  k->m, k->theta, k->tau2, k->status, k->hcount};
+                  k->m, k->theta, k->tau2, k->status, k->hcount, k->gn, k->gtrace, k->gbound,
+                  k->d_row0, k->d_rows, k->d_goff, k->u_row0, k->u_rows, k->u_graph};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (k->ev_fork) cudaEventDestroy(k->ev_fork);
@@ -1127,6 +1220,7 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     }
   } guard{&K, fresh};
   const int64_t n = g->n;
+  const int G = g->n_graphs;
   const Geometry geo = geometry(precision, ld, n, num_sms());
   if (n > K->n_cap) {
     SLAQ_TRY(grow(reinterpret_cast<unsigned char **>(&K->U), (size_t)s * n * ld * basis_bytes(precision)));
@@ -1146,25 +1240,32 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
       K->hcount_cap = need;
     }
   }
-  if (geo.Gmax > K->G) {
-    SLAQ_TRY(grow(&K->part, (size_t)geo.Gmax * 2 * s * ld));
-    K->G = geo.Gmax;
+  if (G > K->gcap) {
+    const size_t ns = (size_t)G * nv * s;
+    SLAQ_TRY(grow(&K->dsum, (size_t)G * s * ld));
+    SLAQ_TRY(grow(&K->coef, (size_t)G * s * ld));
+    SLAQ_TRY(grow(&K->gram, (size_t)G * s * s * ld));
+    SLAQ_TRY(grow(&K->alpha, ns));
+    SLAQ_TRY(grow(&K->beta, ns));
+    SLAQ_TRY(grow(&K->m, (size_t)G * nv));
+    SLAQ_TRY(grow(&K->theta, ns));
+    SLAQ_TRY(grow(&K->tau2, ns));
+    SLAQ_TRY(grow(&K->gn, (size_t)G));
+    SLAQ_TRY(grow(&K->gtrace, (size_t)G));
+    SLAQ_TRY(grow(&K->gbound, (size_t)G));
+    K->gcap = G;
   }
-  if (fresh) {
-    SLAQ_TRY(grow(&K->dsum, (size_t)s * ld));
-    SLAQ_TRY(grow(&K->coef, (size_t)s * ld));
-    SLAQ_TRY(grow(&K->gram, (size_t)s * s * ld));
-    SLAQ_TRY(grow(&K->alpha, (size_t)nv * s));
-    SLAQ_TRY(grow(&K->beta, (size_t)nv * s));
-    SLAQ_TRY(grow(&K->m, (size_t)nv));
-    SLAQ_TRY(grow(&K->theta, (size_t)nv * s));
-    SLAQ_TRY(grow(&K->tau2, (size_t)nv * s));
-    SLAQ_TRY(grow(&K->status, 1));
-  }
+  if (!K->status) SLAQ_TRY(grow(&K->status, 1));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gn, g->gn_dev, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gtrace, g->gtrace_dev, G * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, st));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gbound, g->gbound_dev, G * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, st));
   K->seed = seed;
   K->graph_id = graph_id;
   K->reorth = reorth;
   K->n = n;
+  K->n_graphs = G;
   K->kind = g->kind;
   K->trace = g->trace;
   K->bound = g->bound;

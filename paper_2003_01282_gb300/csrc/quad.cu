@@ -15,13 +15,12 @@ namespace {
 constexpr int kMaxS = 64;
 constexpr int kMaxNv = 512;
 
-// One probe per block (the solver is sequential; lane 0 runs it) so that the
-// probes spread over the SMs' FP64 units.
+// One thread per (graph, probe) problem; problems are rows of [total][s].
 __global__ void k_ritz(const double *__restrict__ alpha, const double *__restrict__ beta,
                        const int32_t *__restrict__ mm, int nv, int s, double *__restrict__ theta,
                        double *__restrict__ tau2, int32_t *status) {
-  const int p = blockIdx.x;
-  if (p >= nv || threadIdx.x != 0) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;  // nv = number of problems
+  if (p >= nv) return;
   double d[kMaxS], e[kMaxS], w[kMaxS];
   const int m = mm[p];
   for (int i = 0; i < m; ++i) d[i] = alpha[p * s + i];
@@ -69,46 +68,56 @@ __device__ __forceinline__ double fval(double t, double th) {
   return -sin(t * th);
 }
 
-// One block per time value: g_p = n' sum_k tau2 f(t theta_k) for every probe.
+// Block (time value ti, graph gr): g_p = n_g sum_k tau2 f(t theta_k) for every
+// probe of the graph; out[gr][ti] is their mean.  n_g from gn[gr] (or n0).
 template <int FUN>
 __global__ void k_trace_t(const double *__restrict__ theta, const double *__restrict__ tau2,
-                          const int32_t *__restrict__ mm, int nv, int s, double n,
-                          const double *__restrict__ t, int nt, double *out, double *se,
-                          double *per_probe) {
+                          const int32_t *__restrict__ mm, int nv, int s,
+                          const double *__restrict__ gn, double n0, const double *__restrict__ t,
+                          int nt, double *out, double *se, double *per_probe) {
   __shared__ double g[kMaxNv];
   const int ti = blockIdx.x;
+  const int gr = blockIdx.y;
   const double tv = t[ti];
+  const double n = gn ? gn[gr] : n0;
   for (int p = threadIdx.x; p < nv; p += blockDim.x) {
+    const int64_t q = (int64_t)gr * nv + p;
     double acc = 0.0;
-    const int m = mm[p];
-    for (int k = 0; k < m; ++k) acc += tau2[p * s + k] * fval<FUN>(tv, theta[p * s + k]);
+    const int m = mm[q];
+    for (int k = 0; k < m; ++k) acc += tau2[q * s + k] * fval<FUN>(tv, theta[q * s + k]);
     g[p] = n * acc;
-    if (per_probe) per_probe[(int64_t)p * nt + ti] = n * acc;
+    if (per_probe) per_probe[q * nt + ti] = n * acc;
   }
   __syncthreads();
-  if (threadIdx.x == 0) mean_se(g, nv, out + ti, se ? se + ti : nullptr);
+  if (threadIdx.x == 0)
+    mean_se(g, nv, out + (int64_t)gr * nt + ti, se ? se + (int64_t)gr * nt + ti : nullptr);
 }
 
-// VNGE: f(theta) = -(theta/c) ln(theta/c) for theta > 0, else 0.
+// VNGE of graph blockIdx.x: f(theta) = -(theta/c) ln(theta/c) for theta > 0,
+// else 0, with c = tr(L_g).
 __global__ void k_vnge(const double *__restrict__ theta, const double *__restrict__ tau2,
-                       const int32_t *__restrict__ mm, int nv, int s, double n, double c,
+                       const int32_t *__restrict__ mm, int nv, int s,
+                       const double *__restrict__ gn, const double *__restrict__ gtrace,
                        double *out, double *se, double *per_probe) {
   __shared__ double g[kMaxNv];
+  const int gr = blockIdx.x;
+  const double n = gn[gr], c = gtrace[gr];
   for (int p = threadIdx.x; p < nv; p += blockDim.x) {
+    const int64_t q = (int64_t)gr * nv + p;
     double acc = 0.0;
-    const int m = mm[p];
+    const int m = mm[q];
     for (int k = 0; k < m; ++k) {
-      const double th = theta[p * s + k];
+      const double th = theta[q * s + k];
       if (th > 0.0 && c > 0.0) {
         const double x = th / c;
-        acc += tau2[p * s + k] * (-x * log(x));
+        acc += tau2[q * s + k] * (-x * log(x));
       }
     }
     g[p] = n * acc;
-    if (per_probe) per_probe[p] = n * acc;
+    if (per_probe) per_probe[q] = n * acc;
   }
   __syncthreads();
-  if (threadIdx.x == 0) mean_se(g, nv, out, se);
+  if (threadIdx.x == 0) mean_se(g, nv, out + gr, se ? se + gr : nullptr);
 }
 
 __global__ void k_distance(const double *a, const double *b, int len, int absdiff, double *out) {
@@ -141,8 +150,11 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   ProfScope prof(SLAQ_PROF_RITZ, st);
   SLAQ_CHECK_CUDA(cudaMemsetAsync(K->status, 0, sizeof(int32_t), st));
   ++tl_launches;
-  k_ritz<<<(unsigned)K->nv, 32, 0, st>>>(K->alpha, K->beta, K->m, K->nv, K->s,
-                                                       K->theta, K->tau2, K->status);
+  const int total = K->n_graphs * K->nv;
+  // the solver is latency-bound: few problems go one per block, over many SMs
+  const int tpb = std::max(1, std::min(32, total / std::max(1, num_sms())));
+  k_ritz<<<(unsigned)ceil_div(total, tpb), tpb, 0, st>>>(K->alpha, K->beta, K->m, total, K->s,
+                                                          K->theta, K->tau2, K->status);
   SLAQ_CHECK_LAUNCH("ritz");
   return SLAQ_OK;
 }
@@ -152,8 +164,8 @@ int trace_heat(slaq_krylov K, const double *t, int nt, double *out, double *se, 
   if (nt < 1 || !t || !out) return set_error(SLAQ_EINVAL, "heat trace needs t, nt >= 1 and out");
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
-  k_trace_t<0><<<nt, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, (double)K->n, t, nt,
-                                   out, se, per_probe);
+  k_trace_t<0><<<dim3(nt, K->n_graphs), 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s,
+                                                      K->gn, 0.0, t, nt, out, se, per_probe);
   SLAQ_CHECK_LAUNCH("trace_heat");
   return SLAQ_OK;
 }
@@ -163,11 +175,11 @@ int trace_wave(slaq_krylov K, const double *t, int nt, double *re, double *im, d
   if (nt < 1 || !t || !re || !im) return set_error(SLAQ_EINVAL, "wave trace needs t, nt, re, im");
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
-  k_trace_t<1><<<nt, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, (double)K->n, t, nt, re,
-                                   se_re, nullptr);
+  k_trace_t<1><<<dim3(nt, K->n_graphs), 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s,
+                                                      K->gn, 0.0, t, nt, re, se_re, nullptr);
   ++tl_launches;
-  k_trace_t<2><<<nt, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, (double)K->n, t, nt, im,
-                                   se_im, nullptr);
+  k_trace_t<2><<<dim3(nt, K->n_graphs), 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s,
+                                                      K->gn, 0.0, t, nt, im, se_im, nullptr);
   SLAQ_CHECK_LAUNCH("trace_wave");
   return SLAQ_OK;
 }
@@ -176,8 +188,8 @@ int trace_vnge(slaq_krylov K, double *out, double *se, double *per_probe, cudaSt
   if (!out) return set_error(SLAQ_EINVAL, "vnge needs out");
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
-  k_vnge<<<1, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, (double)K->n, K->trace, out, se,
-                            per_probe);
+  k_vnge<<<K->n_graphs, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, K->gtrace, out,
+                                       se, per_probe);
   SLAQ_CHECK_LAUNCH("trace_vnge");
   return SLAQ_OK;
 }
@@ -249,9 +261,10 @@ int trace_heat_static(const double *alpha, const double *beta, const int32_t *m,
   double *tau2 = sp.gauss + (size_t)nv * s;
   SLAQ_CHECK_CUDA(cudaMemsetAsync(sp.status, 0, sizeof(int32_t), st));  // starts at zero
   ++tl_launches;
-  k_ritz<<<(unsigned)nv, 32, 0, st>>>(alpha, beta, m, nv, s, theta, tau2, sp.status);
+  k_ritz<<<(unsigned)ceil_div(nv, 32), 32, 0, st>>>(alpha, beta, m, nv, s, theta, tau2, sp.status);
   ++tl_launches;
-  k_trace_t<0><<<nt, 128, 0, st>>>(theta, tau2, m, nv, s, (double)n, t, nt, out, se, nullptr);
+  k_trace_t<0><<<dim3(nt, 1), 128, 0, st>>>(theta, tau2, m, nv, s, nullptr, (double)n, t, nt, out,
+                                            se, nullptr);
   if (status_out)
     SLAQ_CHECK_CUDA(cudaMemcpyAsync(status_out, sp.status, sizeof(int32_t),
                                     cudaMemcpyDeviceToDevice, st));

@@ -41,6 +41,9 @@ _SIGNATURES = {
     "slaq_last_error": (_I, [C.c_char_p, _SZ]),
     "slaq_device_check": (_I, []),
     "slaq_build_laplacian": (_I, [_VP, _VP, _I64, _I64, _VP, _I, _I, _VP, _PVP]),
+    "slaq_build_laplacian_batch": (_I, [_VP, _VP, _VP, _VP, _I, _VP, _I, _I, _VP, _PVP]),
+    "slaq_graph_batch_info": (_I, [_VP, _VP, _VP, _VP]),
+    "slaq_krylov_batch_info": (_I, [_VP, _VP]),
     "slaq_graph_info": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_graph_export": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "slaq_graph_destroy": (None, [_VP]),
@@ -157,6 +160,48 @@ def build_laplacian(src, dst, n_nodes: int, weights=None, kind=NORMALIZED, flags
     return Graph(out)
 
 
+def build_laplacian_batch(graphs, weights=None, kind=NORMALIZED, flags=0, device="cuda", stream=None):
+    """Batch of graphs [(src, dst, n_nodes), ...] (numpy or CPU arrays, local
+    ids) as one block-diagonal Laplacian."""
+    torch = _torch()
+    if isinstance(kind, str):
+        kind = KINDS[kind]
+    srcs = [np.asarray(g[0], np.int32) for g in graphs]
+    dsts = [np.asarray(g[1], np.int32) for g in graphs]
+    edge_off = np.zeros(len(graphs) + 1, np.int64)
+    node_off = np.zeros(len(graphs) + 1, np.int64)
+    edge_off[1:] = np.cumsum([a.size for a in srcs])
+    node_off[1:] = np.cumsum([int(g[2]) for g in graphs])
+    src = torch.as_tensor(np.concatenate(srcs) if srcs else np.zeros(0, np.int32), device=device)
+    dst = torch.as_tensor(np.concatenate(dsts) if dsts else np.zeros(0, np.int32), device=device)
+    w = None
+    if weights is not None:
+        w = torch.as_tensor(np.concatenate([np.asarray(x, np.float64) for x in weights]), device=device)
+    out = C.c_void_p()
+    _check(lib().slaq_build_laplacian_batch(_dev(src, torch.int32, "src"), _dev(dst, torch.int32, "dst"),
+                                            edge_off.ctypes.data_as(C.c_void_p),
+                                            node_off.ctypes.data_as(C.c_void_p), len(graphs),
+                                            _dev(w, torch.float64, "weights"), int(kind), int(flags),
+                                            _stream(stream), C.byref(out)))
+    return Graph(out)
+
+
+def graph_batch_info(g) -> dict:
+    G = C.c_int()
+    _check(lib().slaq_graph_batch_info(_handle(g), C.byref(G), None, None))
+    off = np.zeros(G.value + 1, np.int64)
+    tr = np.zeros(G.value)
+    _check(lib().slaq_graph_batch_info(_handle(g), C.byref(G), off.ctypes.data_as(C.c_void_p),
+                                       tr.ctypes.data_as(C.c_void_p)))
+    return {"n_graphs": G.value, "node_off": off, "trace": tr}
+
+
+def krylov_batch_info(k) -> int:
+    G = C.c_int()
+    _check(lib().slaq_krylov_batch_info(_handle(k), C.byref(G)))
+    return G.value
+
+
 def graph_info(g) -> dict:
     n, nnz, ni = C.c_int64(), C.c_int64(), C.c_int64()
     tr = C.c_double()
@@ -217,13 +262,20 @@ def krylov_info(k) -> dict:
     return {"nv": nv.value, "s": s.value, "precision": pr.value, "n": n.value}
 
 
+def _lead(k):
+    """Leading shape of per-graph outputs: () for one graph, (G,) for a batch."""
+    G = krylov_batch_info(k)
+    return () if G == 1 else (G,)
+
+
 def krylov_export(k, stream=None):
     torch = _torch()
     info = krylov_info(k)
     nv, s = info["nv"], info["s"]
-    alpha = torch.empty(nv, s, dtype=torch.float64, device="cuda")
-    beta = torch.empty(nv, s, dtype=torch.float64, device="cuda")
-    m = torch.empty(nv, dtype=torch.int32, device="cuda")
+    lead = _lead(k)
+    alpha = torch.empty(*lead, nv, s, dtype=torch.float64, device="cuda")
+    beta = torch.empty(*lead, nv, s, dtype=torch.float64, device="cuda")
+    m = torch.empty(*lead, nv, dtype=torch.int32, device="cuda")
     _check(lib().slaq_krylov_export(_handle(k), _dev(alpha), _dev(beta), _dev(m), _stream(stream)))
     return alpha, beta, m
 
@@ -231,7 +283,7 @@ def krylov_export(k, stream=None):
 def ritz_export(k, stream=None):
     torch = _torch()
     info = krylov_info(k)
-    theta = torch.empty(info["nv"], info["s"], dtype=torch.float64, device="cuda")
+    theta = torch.empty(*_lead(k), info["nv"], info["s"], dtype=torch.float64, device="cuda")
     tau2 = torch.empty_like(theta)
     _check(lib().slaq_ritz_export(_handle(k), _dev(theta), _dev(tau2), _stream(stream)))
     return theta, tau2
@@ -240,9 +292,10 @@ def ritz_export(k, stream=None):
 def trace_heat(k, t, per_probe: bool = False, stream=None):
     torch = _torch()
     nt = int(t.numel())
-    out = torch.empty(nt, dtype=torch.float64, device="cuda")
+    lead = _lead(k)
+    out = torch.empty(*lead, nt, dtype=torch.float64, device="cuda")
     se = torch.empty_like(out)
-    pp = torch.empty(krylov_info(k)["nv"], nt, dtype=torch.float64, device="cuda") if per_probe else None
+    pp = torch.empty(*lead, krylov_info(k)["nv"], nt, dtype=torch.float64, device="cuda") if per_probe else None
     _check(lib().slaq_trace_heat(_handle(k), _dev(t, torch.float64, "t"), nt, _dev(out), _dev(se),
                                  _dev(pp), _stream(stream)))
     return (out, se, pp) if per_probe else (out, se)
@@ -251,7 +304,8 @@ def trace_heat(k, t, per_probe: bool = False, stream=None):
 def trace_wave(k, t, stream=None):
     torch = _torch()
     nt = int(t.numel())
-    re, im = (torch.empty(nt, dtype=torch.float64, device="cuda") for _ in range(2))
+    lead = _lead(k)
+    re, im = (torch.empty(*lead, nt, dtype=torch.float64, device="cuda") for _ in range(2))
     sre, sim = torch.empty_like(re), torch.empty_like(re)
     _check(lib().slaq_trace_wave(_handle(k), _dev(t, torch.float64, "t"), nt, _dev(re), _dev(im),
                                  _dev(sre), _dev(sim), _stream(stream)))
@@ -260,9 +314,10 @@ def trace_wave(k, t, stream=None):
 
 def trace_vnge(k, per_probe: bool = False, stream=None):
     torch = _torch()
-    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    lead = _lead(k)
+    out = torch.empty(*(lead or (1,)), dtype=torch.float64, device="cuda")
     se = torch.empty_like(out)
-    pp = torch.empty(krylov_info(k)["nv"], dtype=torch.float64, device="cuda") if per_probe else None
+    pp = torch.empty(*lead, krylov_info(k)["nv"], dtype=torch.float64, device="cuda") if per_probe else None
     _check(lib().slaq_trace_vnge(_handle(k), _dev(out), _dev(se), _dev(pp), _stream(stream)))
     return (out, se, pp) if per_probe else (out, se)
 

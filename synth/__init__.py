@@ -183,17 +183,52 @@ def erdos_renyi(n: int, p: float, seed: int = 0):
     return i[keep].astype(np.int32), j[keep].astype(np.int32), n
 
 
+def _tri_pair(idx, m):
+    """Pair (i, j), i < j < m, of row-major index idx in the strict upper triangle."""
+    idx = np.asarray(idx, np.int64)
+    b = 2 * m - 1
+    i = np.floor((b - np.sqrt(b * b - 8.0 * idx)) / 2).astype(np.int64)
+    # guard floating-point rounding of the closed form
+    start = i * (2 * m - i - 1) // 2
+    low = idx < start
+    i[low] -= 1
+    start = i * (2 * m - i - 1) // 2
+    nxt = (i + 1) * (2 * m - i - 2) // 2
+    high = idx >= nxt
+    i[high] += 1
+    start = i * (2 * m - i - 1) // 2
+    j = idx - start + i + 1
+    return i, j
+
+
 def sbm(sizes, p_in: float, p_out: float, seed: int = 0):
-    """Stochastic block model with the given block sizes (dense sampling of
-    the strict upper triangle; meant for graphs of up to a few thousand nodes)."""
+    """Stochastic block model with the given block sizes: for every pair of
+    blocks the number of edges is Binomial(pairs, p) and the edges are that
+    many distinct pairs drawn uniformly."""
     rng = np.random.default_rng(seed)
     sizes = np.asarray(sizes, np.int64)
-    n = int(sizes.sum())
-    block = np.repeat(np.arange(sizes.size), sizes)
-    i, j = np.triu_indices(n, 1)
-    p = np.where(block[i] == block[j], p_in, p_out)
-    keep = rng.random(i.size) < p
-    return i[keep].astype(np.int32), j[keep].astype(np.int32), n
+    start = np.concatenate([[0], np.cumsum(sizes)])
+    n = int(start[-1])
+    us, vs = [], []
+    for a in range(sizes.size):
+        for b in range(a, sizes.size):
+            sa, sb = int(sizes[a]), int(sizes[b])
+            pairs = sa * (sa - 1) // 2 if a == b else sa * sb
+            if pairs == 0:
+                continue
+            k = int(rng.binomial(pairs, p_in if a == b else p_out))
+            if k == 0:
+                continue
+            idx = rng.choice(pairs, size=k, replace=False)
+            if a == b:
+                i, j = _tri_pair(idx, sa)
+            else:
+                i, j = idx // sb, idx % sb
+            us.append(start[a] + i)
+            vs.append(start[b] + j)
+    if not us:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32), n
+    return np.concatenate(us).astype(np.int32), np.concatenate(vs).astype(np.int32), n
 
 
 def sbm_batch(n_graphs: int, seed: int = 3, median: float = 300.0,

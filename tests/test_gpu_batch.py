@@ -1,0 +1,127 @@
+"""Batches of graphs as one block-diagonal Laplacian, through the C ABI.
+
+Every graph g of a batch must give what the oracle gives for that graph on
+its own with probe graph field g (FP64: relative 1e-10), and what a
+single-graph GPU run with graph_id = g gives."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import descriptors as odesc
+from oracle.laplacian import COMBINATORIAL, NORMALIZED, build_laplacian
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2003_01282_gb300 import slaq  # noqa: E402
+from paper_2003_01282_gb300.build import build  # noqa: E402
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build()
+    slaq.lib()
+
+
+def mixed_batch():
+    return [
+        synth.barabasi_albert(300, 3, seed=1),
+        synth.sbm([40, 40, 41], 0.3, 0.02, seed=2),
+        synth.star(30),
+        synth.complete(9),
+        synth.cycle(17),
+        synth.disjoint_union(synth.path(12), synth.cycle(6), extra_isolated=4),
+        synth.path(10),
+        synth.rmat(11, 8 << 11, seed=4),
+        synth.star(2600),                  # a 2599-entry row: split into chunks
+    ]
+
+
+def _dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+@pytest.mark.parametrize("kind,drop", [(NORMALIZED, False), (NORMALIZED, True), (COMBINATORIAL, False)])
+def test_batch_matches_oracle_per_graph(kind, drop):
+    graphs = mixed_batch()
+    nv, s, seed = 6, 10, 5
+    k = slaq.NORMALIZED if kind == NORMALIZED else slaq.COMBINATORIAL
+    gb = slaq.build_laplacian_batch(graphs, kind=k, flags=slaq.DROP_ISOLATED if drop else 0)
+    info = slaq.graph_batch_info(gb)
+    assert info["n_graphs"] == len(graphs)
+    K = slaq.lanczos(gb, nv, s, seed, precision=slaq.FP64)
+    alpha, beta, m = (x.cpu().numpy() for x in slaq.krylov_export(K))
+    theta, tau2 = (x.cpu().numpy() for x in slaq.ritz_export(K))
+    t = synth.t_grid(64)
+    heat = slaq.trace_heat(K, _dev(t, torch.float64))[0].cpu().numpy()
+    vnge = slaq.trace_vnge(K)[0].cpu().numpy()
+    assert heat.shape == (len(graphs), 64) and vnge.shape == (len(graphs),)
+    for g, (src, dst, n) in enumerate(graphs):
+        lap = build_laplacian(src, dst, n, kind=kind, drop_isolated=drop)
+        assert info["node_off"][g + 1] - info["node_off"][g] == lap.n
+        assert info["trace"][g] == lap.trace
+        runs = odesc.slq_runs(lap, s, nv, seed, graph=g)
+        for p, r in enumerate(runs):
+            assert m[g, p] == r.m
+            np.testing.assert_allclose(alpha[g, p, :r.m], r.alpha, rtol=RTOL, atol=RTOL * lap.norm_bound())
+            np.testing.assert_allclose(beta[g, p, :r.m - 1], r.beta, rtol=RTOL, atol=RTOL * lap.norm_bound())
+            np.testing.assert_allclose(theta[g, p, :r.m], r.theta, rtol=RTOL, atol=RTOL * lap.norm_bound())
+        oh, _ = odesc.heat_trace(runs, lap.n, t)
+        # exp(-t theta) turns the eigensolver's absolute error eps * ||T|| into a
+        # relative error t * ||L|| * eps: widen 1e-10 where that is larger
+        # (combinatorial Laplacians with large degrees)
+        rt = np.maximum(RTOL, t * lap.norm_bound() * 1e-14)
+        assert np.all(np.abs(heat[g] - oh) <= rt * np.abs(oh)), g
+        ov, _ = odesc.vnge(runs, lap.n, lap.trace)
+        assert abs(vnge[g] - ov) <= RTOL * abs(ov) + 1e-300
+
+
+def test_batch_equals_single_graph_runs():
+    graphs = mixed_batch()
+    nv, s, seed = 8, 12, 9
+    gb = slaq.build_laplacian_batch(graphs)
+    t = _dev(synth.t_grid(), torch.float64)
+    for prec in (slaq.FP64, slaq.FP32):
+        K = slaq.lanczos(gb, nv, s, seed, graph_id=3, precision=prec)
+        hb = slaq.trace_heat(K, t)[0].cpu().numpy()
+        for g, (src, dst, n) in enumerate(graphs):
+            gs = slaq.build_laplacian(_dev(src, torch.int32), _dev(dst, torch.int32), n)
+            Ks = slaq.lanczos(gs, nv, s, seed, graph_id=3 + g, precision=prec)
+            hs = slaq.trace_heat(Ks, t)[0].cpu().numpy()
+            tol = 1e-12 if prec == slaq.FP64 else 1e-5
+            np.testing.assert_allclose(hb[g], hs, rtol=tol)
+
+
+def test_weighted_batch():
+    rng = np.random.default_rng(0)
+    graphs = [synth.barabasi_albert(120, 2, seed=i) for i in range(4)]
+    weights = [rng.uniform(0.5, 2.0, g[0].size) for g in graphs]
+    gb = slaq.build_laplacian_batch(graphs, weights=weights, kind=slaq.COMBINATORIAL)
+    K = slaq.lanczos(gb, 5, 8, 2)
+    alpha = slaq.krylov_export(K)[0].cpu().numpy()
+    for g, ((src, dst, n), w) in enumerate(zip(graphs, weights)):
+        lap = build_laplacian(src, dst, n, weights=w, kind=COMBINATORIAL)
+        runs = odesc.slq_runs(lap, 8, 5, 2, graph=g)
+        for p, r in enumerate(runs):
+            np.testing.assert_allclose(alpha[g, p, :r.m], r.alpha, rtol=RTOL)
+
+
+def test_batch_rejects_bad_local_ids():
+    graphs = [synth.path(5), (np.array([0, 7], np.int32), np.array([1, 2], np.int32), 4)]
+    with pytest.raises(slaq.SlaqError) as ei:
+        slaq.build_laplacian_batch(graphs)
+    assert ei.value.status == 1
+
+
+def test_sbm_batch_reduced_precision():
+    graphs = synth.sbm_batch(60, seed=3, median=80)
+    gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
+    t = _dev(synth.t_grid(), torch.float64)
+    h64 = slaq.trace_heat(slaq.lanczos(gb, 20, 15, 1, precision=slaq.FP64), t)[0].cpu().numpy()
+    h32 = slaq.trace_heat(slaq.lanczos(gb, 20, 15, 1, precision=slaq.FP32), t)[0].cpu().numpy()
+    assert np.max(np.abs(h32 - h64) / np.abs(h64)) < 1e-4
