@@ -248,11 +248,14 @@ def run_batched(args, dev, world=1, rank=0):
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 3
+    slaq.profile_enable(True)
     e0.record()
     for _ in range(reps):
         step()
     e1.record()
     torch.cuda.synchronize(dev)
+    prof = slaq.profile_read()
+    slaq.profile_enable(False)
     ms = e0.elapsed_time(e1) / reps
     # the same path graph by graph on a subset (every 25th graph)
     sub = graphs[::25]
@@ -270,24 +273,32 @@ def run_batched(args, dev, world=1, rank=0):
     return {"workload": SBM_WORKLOAD, "metric": "graphs/s", "value": world * SBM_GRAPHS / (ms * 1e-3),
             "ms_per_step": ms, "nnz": int(nnz),
             "probe_edges_per_s": world * nnz * SBM_NV * SBM_S / (ms * 1e-3),
+            "kernels_ms_per_step": {k: round(v[0] / reps, 3) for k, v in prof.items()},
             "per_graph_launches": {"graphs": len(sub), "value": len(sub) / (ms_sub * 1e-3),
                                    "unit": "graphs/s"},
             "speedup_over_per_graph": (SBM_GRAPHS / ms) / (len(sub) / ms_sub)}
 
 
 def kernel_capture(args):
-    """Profiling driver: build the R-MAT 2^20 graph and run Lanczos
-    `--kernel-capture` times (for ncu captures of single kernels)."""
+    """Profiling driver: build the workload's graph (R-MAT 2^20, or the SBM
+    batch with --capture-batched) and run Lanczos `--kernel-capture` times
+    (for ncu captures of single kernels)."""
     import torch
     from paper_2003_01282_gb300 import slaq
     from paper_2003_01282_gb300.build import build
     build()
-    s_, d_, n = make_graph()
-    g = slaq.build_laplacian(torch.as_tensor(s_, device="cuda"), torch.as_tensor(d_, device="cuda"), n,
-                             flags=slaq.DROP_ISOLATED)
+    if args.capture_batched:
+        g = slaq.build_laplacian_batch(synth.sbm_batch(SBM_GRAPHS, seed=SBM_SEED),
+                                       flags=slaq.DROP_ISOLATED)
+        nv, steps = SBM_NV, SBM_S
+    else:
+        s_, d_, n = make_graph()
+        g = slaq.build_laplacian(torch.as_tensor(s_, device="cuda"), torch.as_tensor(d_, device="cuda"),
+                                 n, flags=slaq.DROP_ISOLATED)
+        nv, steps = NV, S
     K = None
     for _ in range(args.kernel_capture):
-        K = slaq.lanczos(g, NV, S, PROBE_SEED, precision=slaq.PRECISIONS[args.precision], reuse=K)
+        K = slaq.lanczos(g, nv, steps, PROBE_SEED, precision=slaq.PRECISIONS[args.precision], reuse=K)
     torch.cuda.synchronize()
     print(json.dumps({"kernel_capture": args.kernel_capture, "n_prime": g.info["n"], "nnz": g.info["nnz"]}))
 
@@ -481,6 +492,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the SBM-batch leg")
     ap.add_argument("--kernel-capture", type=int, default=0,
                     help="profiling driver: run Lanczos this many times on the R-MAT graph and exit")
+    ap.add_argument("--capture-batched", action="store_true",
+                    help="with --kernel-capture: use the SBM batch instead of the R-MAT graph")
     ap.add_argument("--cpu-baseline-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_baseline_worker:

@@ -148,6 +148,7 @@ struct slaq_krylov_s {
   double trace = 0.0, bound = 0.0, tol = 0.0;
   int G = 0;              // row blocks the partials buffer holds
   int dsub = 1;           // pieces per dots chunk in the last dots launch
+  int max_chunks_per_graph = 1;
   void *U = nullptr;      // [s][n_cap][ld] basis (TB)
   void *Z = nullptr;      // [n_cap][ld] L u_k (TW)
   void *P = nullptr;      // [chunk_cap][ld] partial sums of split rows (TW)

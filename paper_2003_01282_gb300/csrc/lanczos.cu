@@ -515,8 +515,11 @@ __global__ void __launch_bounds__(512, 2)
   TX *xs = reinterpret_cast<TX *>(dyn);                 // [2][kTile][ld]
   TB *us = reinterpret_cast<TB *>(xs + 2 * kTile * ld);  // [2][kTile][ld]
   const TX *X = static_cast<const TX *>(Xv);
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int nthr = blockDim.x * blockDim.y;
+  // z = row phase: narrow probe blocks (few column vectors) split the rows of
+  // a tile over blockDim.z groups and add the groups' sums at the end
+  const int RZ = blockDim.z, rz = threadIdx.z;
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const int g = blockIdx.x;
   const int j = jfirst + (int)blockIdx.y * Jb + (int)threadIdx.y;
   const bool active = j <= jlast;  // idle threads still stage and synchronize
@@ -558,26 +561,26 @@ __global__ void __launch_bounds__(512, 2)
         gc[v] = TW(0);
       }
       constexpr int UNR = VE >= 8 ? 2 : 4;  // rows in flight per thread (register budget)
-      int r = 0;
-      for (; r + UNR <= nr; r += UNR) {
+      int r = rz;
+      for (; r + (UNR - 1) * RZ < nr; r += UNR * RZ) {
         TW u[UNR][VE];
 #pragma unroll
-        for (int q = 0; q < UNR; ++q) ldb(Uj + (row0 + r + q) * stride, u[q]);
+        for (int q = 0; q < UNR; ++q) ldb(Uj + (row0 + r + q * RZ) * stride, u[q]);
 #pragma unroll
         for (int q = 0; q < UNR; ++q) {
           TW x[VE];
-          lds(xt + (r + q) * ld, x);
+          lds(xt + (r + q * RZ) * ld, x);
 #pragma unroll
           for (int v = 0; v < VE; ++v) dc[v] = fma(u[q][v], x[v], dc[v]);
           if (WITH_G) {
             TW w[VE];
-            lds(ut + (r + q) * ld, w);
+            lds(ut + (r + q * RZ) * ld, w);
 #pragma unroll
             for (int v = 0; v < VE; ++v) gc[v] = fma(u[q][v], w[v], gc[v]);
           }
         }
       }
-      for (; r < nr; ++r) {
+      for (; r < nr; r += RZ) {
         TW u[VE], x[VE];
         ldb(Uj + (row0 + r) * stride, u);
         lds(xt + r * ld, x);
@@ -598,21 +601,44 @@ __global__ void __launch_bounds__(512, 2)
     }
     __syncthreads();  // buffer t&1 is restaged at t+2
   }
-  if (!active) return;
+  // sum the row phases in a fixed order; the staging buffers are free now
+  double *red = reinterpret_cast<double *>(dyn);  // [RZ][Jb][ld][2]
+  const int slot = ((rz * blockDim.y + threadIdx.y) * ld + col) * 2;
+  if (RZ > 1) {
+#pragma unroll
+    for (int v = 0; v < VE; ++v) {
+      red[slot + 2 * v] = d[v].value();
+      red[slot + 2 * v + 1] = WITH_G ? gg[v].value() : 0.0;
+    }
+    __syncthreads();
+  }
+  if (!active || rz != 0) return;
   double *pd = part + (((int64_t)g * 2 + 0) * s + j) * ld + col;
+  double *pg = part + (((int64_t)g * 2 + 1) * s + j) * ld + col;
 #pragma unroll
-  for (int v = 0; v < VE; ++v) pd[v] = d[v].value();
-  if (WITH_G) {
-    double *pg = part + (((int64_t)g * 2 + 1) * s + j) * ld + col;
-#pragma unroll
-    for (int v = 0; v < VE; ++v) pg[v] = gg[v].value();
+  for (int v = 0; v < VE; ++v) {
+    double dv = d[v].value(), gv = WITH_G ? gg[v].value() : 0.0;
+    for (int q = 1; q < RZ; ++q) {
+      const int sl = ((q * blockDim.y + threadIdx.y) * ld + col) * 2;
+      dv += red[sl + 2 * v];
+      gv += red[sl + 2 * v + 1];
+    }
+    pd[v] = dv;
+    if (WITH_G) pg[v] = gv;
   }
 }
 
-// dynamic shared memory of a dots block
-inline size_t dots_smem(int precision, int ld, bool x_is_basis) {
+// row phases of a dots block: narrow blocks (few column vectors and basis
+// vectors) grow along threadIdx.z up to 128 threads
+inline int dots_phases(int V, int Jb) { return std::max(1, std::min(8, 128 / (V * Jb))); }
+
+// dynamic shared memory of a dots block: staging tiles, reused at the end
+// for the row-phase sums ([rz][Jb][ld][2] doubles)
+inline size_t dots_smem(int precision, int ld, bool x_is_basis, int Jb = 0, int RZ = 1) {
   const int bx = x_is_basis ? basis_bytes(precision) : work_bytes(precision);
-  return (size_t)2 * kTile * ld * (bx + basis_bytes(precision));
+  const size_t tiles = (size_t)2 * kTile * ld * (bx + basis_bytes(precision));
+  const size_t red = RZ > 1 ? (size_t)RZ * Jb * ld * 2 * sizeof(double) : 0;
+  return std::max(tiles, red);
 }
 
 // Sum the partials of graph g's chunks [goff[g], goff[g+1]) of d_j and, with_g,
@@ -644,6 +670,35 @@ __global__ void k_dot_reduce(const double *__restrict__ part, const int32_t *__r
     Neumaier tot;
     for (int y = 0; y < kRedY; ++y) tot.add(ss[y][threadIdx.x]);
     const double v = tot.value();
+    const int64_t gs = (int64_t)gr * s;
+    if (which == 0) {
+      dsum[(gs + j) * ld + p] = v;
+    } else {
+      double *gm = gram + (int64_t)gr * s * s * ld;
+      gm[((int64_t)j * s + k) * ld + p] = v;
+      gm[((int64_t)k * s + j) * ld + p] = v;
+    }
+  }
+}
+
+// Same sums, one thread per output (graph, which, column): for batches whose
+// graphs have few partials each.
+__global__ void k_dot_reduce_narrow(const double *__restrict__ part, const int32_t *__restrict__ goff,
+                                    int sub, int s, int ld, int jfirst, int jcount, int k, int G,
+                                    int with_g, double *__restrict__ dsum,
+                                    double *__restrict__ gram) {
+  const int ncol = jcount * ld;
+  const int64_t total = (int64_t)G * (with_g ? 2 : 1) * ncol;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(o % ncol);
+    const int which = (int)((o / ncol) % (with_g ? 2 : 1));
+    const int gr = (int)(o / ((int64_t)ncol * (with_g ? 2 : 1)));
+    const int j = jfirst + col / ld, p = col % ld;
+    Neumaier acc;
+    for (int c = goff[gr] * sub; c < goff[gr + 1] * sub; ++c)
+      acc.add(part[(((int64_t)c * 2 + which) * s + j) * ld + p]);
+    const double v = acc.value();
     const int64_t gs = (int64_t)gr * s;
     if (which == 0) {
       dsum[(gs + j) * ld + p] = v;
@@ -990,17 +1045,19 @@ int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int j
   using TB = typename Form<P>::TB;
   const int jcount = jlast - jfirst + 1;
   const int Jb = std::min(jcount, geo.Jb);
-  const size_t smem = dots_smem(P, K->ld, x_is_basis);
+  const int RZ = dots_phases(geo.V, Jb);
+  const size_t smem = dots_smem(P, K->ld, x_is_basis, Jb, RZ);
+  const int threads = geo.V * Jb * RZ;
   // split every chunk so that small blocks (few basis vectors) still fill the SMs
   int per_sm;
-  if (x_is_basis) per_sm = blocks_per_sm(k_dots<P, true, false>, geo.V * Jb, smem);
-  else if (with_g) per_sm = blocks_per_sm(k_dots<P, false, true>, geo.V * Jb, smem);
-  else per_sm = blocks_per_sm(k_dots<P, false, false>, geo.V * Jb, smem);
+  if (x_is_basis) per_sm = blocks_per_sm(k_dots<P, true, false>, threads, smem);
+  else if (with_g) per_sm = blocks_per_sm(k_dots<P, false, true>, threads, smem);
+  else per_sm = blocks_per_sm(k_dots<P, false, false>, threads, smem);
   const int64_t want = (int64_t)geo.sms * per_sm;
   const int sub = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSub, want / std::max(1, K->n_dchunks)));
   K->dsub = sub;
   const dim3 grid(K->n_dchunks * sub, (unsigned)ceil_div(jcount, Jb));
-  const dim3 block(geo.V, Jb);
+  const dim3 block(geo.V, Jb, RZ);
   const TB *U = static_cast<const TB *>(K->U);
   const TB *Uk = U + (int64_t)k * n * K->ld;
   const int64_t ustride = n * K->ld;
@@ -1021,15 +1078,22 @@ int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int j
 int reduce_and_solve(slaq_krylov K, int k, int jfirst, int jcount, bool with_g, bool first_pass,
                      bool need_coef, cudaStream_t st) {
   ProfScope prof(SLAQ_PROF_REDUCE, st);
-  const dim3 grid((unsigned)ceil_div((int64_t)jcount * K->ld, 32), with_g ? 2 : 1,
-                  (unsigned)K->n_graphs);
   ++tl_launches;
-  k_dot_reduce<<<grid, dim3(32, kRedY), 0, st>>>(K->part, K->d_goff, K->dsub, K->s, K->ld, jfirst,
-                                                 jcount, k, K->dsum, K->gram);
+  if (K->max_chunks_per_graph * K->dsub >= 8) {
+    const dim3 grid((unsigned)ceil_div((int64_t)jcount * K->ld, 32), with_g ? 2 : 1,
+                    (unsigned)K->n_graphs);
+    k_dot_reduce<<<grid, dim3(32, kRedY), 0, st>>>(K->part, K->d_goff, K->dsub, K->s, K->ld, jfirst,
+                                                   jcount, k, K->dsum, K->gram);
+  } else {
+    const int64_t total = (int64_t)K->n_graphs * (with_g ? 2 : 1) * jcount * K->ld;
+    k_dot_reduce_narrow<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 65535LL * 16), 256, 0,
+                          st>>>(K->part, K->d_goff, K->dsub, K->s, K->ld, jfirst, jcount, k,
+                                K->n_graphs, with_g ? 1 : 0, K->dsum, K->gram);
+  }
   const int K1 = k + 1;
   const size_t smem = (size_t)(K1 * K1 + 2 * K1) * sizeof(double);
   ++tl_launches;
-  k_solve<<<dim3(K->ld, K->n_graphs), 32, smem, st>>>(
+  k_solve<<<dim3(K->nv, K->n_graphs), 32, smem, st>>>(
       K->dsum, K->gram, k, K->s, K->ld, K->nv, first_pass ? 1 : 0, need_coef ? 1 : 0, K->tol,
       K->gbound, K->m, K->alpha, K->beta, K->coef);
   SLAQ_CHECK_LAUNCH("reduce_and_solve");
@@ -1081,7 +1145,9 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   // chunk tables: dots chunks fill one wave; update chunks are smaller
   {
     const int Jb = std::min(K->s, geo.Jb);
-    const int per_sm = blocks_per_sm(k_dots<P, false, true>, geo.V * Jb, dots_smem(P, K->ld, false));
+    const int RZ = dots_phases(geo.V, Jb);
+    const int per_sm = blocks_per_sm(k_dots<P, false, true>, geo.V * Jb * RZ,
+                                     dots_smem(P, K->ld, false, Jb, RZ));
     const int64_t want_d = (int64_t)geo.sms * per_sm;
     const int64_t rows_d = std::max<int64_t>(64, ceil_div(n, want_d));
     make_chunks(gr->goff, rows_d, K->hd_row0, K->hd_rows, K->hd_graph, &K->hd_goff);
@@ -1091,6 +1157,9 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
     make_chunks(gr->goff, rows_u, K->hu_row0, K->hu_rows, K->hu_graph, nullptr);
     K->n_dchunks = (int)K->hd_row0.size();
     K->n_uchunks = (int)K->hu_row0.size();
+    K->max_chunks_per_graph = 1;
+    for (size_t q = 0; q + 1 < K->hd_goff.size(); ++q)
+      K->max_chunks_per_graph = std::max(K->max_chunks_per_graph, K->hd_goff[q + 1] - K->hd_goff[q]);
     int64_t c0 = K->dcap, c1 = K->dcap, c2 = K->dcap;
     SLAQ_TRY(upload(&K->d_row0, &c0, K->hd_row0, st));
     SLAQ_TRY(upload(&K->d_rows, &c1, K->hd_rows, st));
@@ -1244,6 +1313,8 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     const size_t ns = (size_t)G * nv * s;
     SLAQ_TRY(grow(&K->dsum, (size_t)G * s * ld));
     SLAQ_TRY(grow(&K->coef, (size_t)G * s * ld));
+    // padding columns of the coefficients are never written: keep them zero
+    SLAQ_CHECK_CUDA(cudaMemsetAsync(K->coef, 0, (size_t)G * s * ld * sizeof(double), st));
     SLAQ_TRY(grow(&K->gram, (size_t)G * s * s * ld));
     SLAQ_TRY(grow(&K->alpha, ns));
     SLAQ_TRY(grow(&K->beta, ns));

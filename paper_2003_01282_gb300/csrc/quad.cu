@@ -60,37 +60,80 @@ __device__ void mean_se(const double *g, int nv, double *mean_out, double *se_ou
   if (se_out) *se_out = se;
 }
 
-// FUN 0: exp(-t theta); FUN 1: cos(t theta); FUN 2: -sin(t theta)
-template <int FUN>
+// FUN 0: exp(-t theta); FUN 1: cos(t theta); FUN 2: -sin(t theta).
+// F32: the product t * theta is formed in FP64 (and reduced modulo 2 pi in
+// FP64 for cos / sin), the function is evaluated in FP32; used by the FP32
+// forms, whose Ritz values carry FP32-level errors anyway.  FP64 is scarce on
+// this chip and these evaluations dominate batched quadratures.
+template <int FUN, bool F32>
 __device__ __forceinline__ double fval(double t, double th) {
-  if (FUN == 0) return exp(-t * th);
-  if (FUN == 1) return cos(t * th);
-  return -sin(t * th);
+  const double x = t * th;
+  if (F32) {
+    if (FUN == 0) return (double)expf((float)(-x));
+    const double two_pi = 6.283185307179586, inv_two_pi = 0.15915494309189535;
+    const double r = x - two_pi * rint(x * inv_two_pi);
+    if (FUN == 1) return (double)cosf((float)r);
+    return -(double)sinf((float)r);
+  }
+  if (FUN == 0) return exp(-x);
+  if (FUN == 1) return cos(x);
+  return -sin(x);
 }
 
-// Block (time value ti, graph gr): g_p = n_g sum_k tau2 f(t theta_k) for every
-// probe of the graph; out[gr][ti] is their mean.  n_g from gn[gr] (or n0).
-template <int FUN>
-__global__ void k_trace_t(const double *__restrict__ theta, const double *__restrict__ tau2,
-                          const int32_t *__restrict__ mm, int nv, int s,
-                          const double *__restrict__ gn, double n0, const double *__restrict__ t,
-                          int nt, double *out, double *se, double *per_probe) {
-  __shared__ double g[kMaxNv];
-  const int ti = blockIdx.x;
+// Block (chunk of kTT time values, graph gr); thread (tt, pg) evaluates
+// g_p = n_g sum_k tau2 f(t theta_k) for probes p = pg, pg + kPG, ... of the
+// graph, keeping a Welford mean and squared deviation; the kPG partial states
+// are combined in a fixed order (Chan et al.), so results are deterministic.
+// out[gr][t] = mean over probes, se[gr][t] = sample std / sqrt(nv).
+constexpr int kTT = 32, kPG = 4;
+template <int FUN, bool F32>
+__global__ void __launch_bounds__(kTT * kPG)
+    k_trace_t(const double *__restrict__ theta, const double *__restrict__ tau2,
+              const int32_t *__restrict__ mm, int nv, int s, const double *__restrict__ gn,
+              double n0, const double *__restrict__ t, int nt, double *out, double *se,
+              double *per_probe) {
+  __shared__ double sh_mean[kPG][kTT], sh_m2[kPG][kTT];
+  __shared__ int sh_cnt[kPG][kTT];
+  const int tt = threadIdx.x % kTT, pg = threadIdx.x / kTT;
+  const int ti = blockIdx.x * kTT + tt;
   const int gr = blockIdx.y;
-  const double tv = t[ti];
-  const double n = gn ? gn[gr] : n0;
-  for (int p = threadIdx.x; p < nv; p += blockDim.x) {
-    const int64_t q = (int64_t)gr * nv + p;
-    double acc = 0.0;
-    const int m = mm[q];
-    for (int k = 0; k < m; ++k) acc += tau2[q * s + k] * fval<FUN>(tv, theta[q * s + k]);
-    g[p] = n * acc;
-    if (per_probe) per_probe[q * nt + ti] = n * acc;
+  double mean = 0.0, m2 = 0.0;
+  int cnt = 0;
+  if (ti < nt) {
+    const double tv = t[ti];
+    const double n = gn ? gn[gr] : n0;
+    for (int p = pg; p < nv; p += kPG) {
+      const int64_t q = (int64_t)gr * nv + p;
+      double acc = 0.0;
+      const int m = mm[q];
+      for (int k = 0; k < m; ++k) acc += tau2[q * s + k] * fval<FUN, F32>(tv, theta[q * s + k]);
+      const double x = n * acc;
+      if (per_probe) per_probe[q * nt + ti] = x;
+      ++cnt;
+      const double d = x - mean;
+      mean += d / cnt;
+      m2 += d * (x - mean);
+    }
   }
+  sh_mean[pg][tt] = mean;
+  sh_m2[pg][tt] = m2;
+  sh_cnt[pg][tt] = cnt;
   __syncthreads();
-  if (threadIdx.x == 0)
-    mean_se(g, nv, out + (int64_t)gr * nt + ti, se ? se + (int64_t)gr * nt + ti : nullptr);
+  if (pg == 0 && ti < nt) {
+    double M = sh_mean[0][tt], S2 = sh_m2[0][tt];
+    int N = sh_cnt[0][tt];
+    for (int h = 1; h < kPG; ++h) {
+      const int nb = sh_cnt[h][tt];
+      if (nb == 0) continue;
+      const double delta = sh_mean[h][tt] - M;
+      const int nn = N + nb;
+      M += delta * nb / nn;
+      S2 += sh_m2[h][tt] + delta * delta * ((double)N * nb / nn);
+      N = nn;
+    }
+    out[(int64_t)gr * nt + ti] = M;
+    if (se) se[(int64_t)gr * nt + ti] = nv > 1 ? sqrt(S2 / (nv - 1) / nv) : nan("");
+  }
 }
 
 // VNGE of graph blockIdx.x: f(theta) = -(theta/c) ln(theta/c) for theta > 0,
@@ -164,8 +207,13 @@ int trace_heat(slaq_krylov K, const double *t, int nt, double *out, double *se, 
   if (nt < 1 || !t || !out) return set_error(SLAQ_EINVAL, "heat trace needs t, nt >= 1 and out");
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
-  k_trace_t<0><<<dim3(nt, K->n_graphs), 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s,
-                                                      K->gn, 0.0, t, nt, out, se, per_probe);
+  const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
+  if (K->precision == SLAQ_FP64)
+    k_trace_t<0, false><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
+                                                     t, nt, out, se, per_probe);
+  else
+    k_trace_t<0, true><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
+                                                    t, nt, out, se, per_probe);
   SLAQ_CHECK_LAUNCH("trace_heat");
   return SLAQ_OK;
 }
@@ -175,11 +223,21 @@ int trace_wave(slaq_krylov K, const double *t, int nt, double *re, double *im, d
   if (nt < 1 || !t || !re || !im) return set_error(SLAQ_EINVAL, "wave trace needs t, nt, re, im");
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
-  k_trace_t<1><<<dim3(nt, K->n_graphs), 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s,
-                                                      K->gn, 0.0, t, nt, re, se_re, nullptr);
+  const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
+  const bool f32 = K->precision != SLAQ_FP64;
+  if (f32)
+    k_trace_t<1, true><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
+                                                    t, nt, re, se_re, nullptr);
+  else
+    k_trace_t<1, false><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
+                                                     t, nt, re, se_re, nullptr);
   ++tl_launches;
-  k_trace_t<2><<<dim3(nt, K->n_graphs), 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s,
-                                                      K->gn, 0.0, t, nt, im, se_im, nullptr);
+  if (f32)
+    k_trace_t<2, true><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
+                                                    t, nt, im, se_im, nullptr);
+  else
+    k_trace_t<2, false><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
+                                                     t, nt, im, se_im, nullptr);
   SLAQ_CHECK_LAUNCH("trace_wave");
   return SLAQ_OK;
 }
@@ -263,8 +321,8 @@ int trace_heat_static(const double *alpha, const double *beta, const int32_t *m,
   ++tl_launches;
   k_ritz<<<(unsigned)ceil_div(nv, 32), 32, 0, st>>>(alpha, beta, m, nv, s, theta, tau2, sp.status);
   ++tl_launches;
-  k_trace_t<0><<<dim3(nt, 1), 128, 0, st>>>(theta, tau2, m, nv, s, nullptr, (double)n, t, nt, out,
-                                            se, nullptr);
+  k_trace_t<0, false><<<dim3((unsigned)ceil_div(nt, kTT), 1), kTT * kPG, 0, st>>>(
+      theta, tau2, m, nv, s, nullptr, (double)n, t, nt, out, se, nullptr);
   if (status_out)
     SLAQ_CHECK_CUDA(cudaMemcpyAsync(status_out, sp.status, sizeof(int32_t),
                                     cudaMemcpyDeviceToDevice, st));
