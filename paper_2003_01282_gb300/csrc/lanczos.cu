@@ -21,6 +21,7 @@
 // classical Gram-Schmidt pass would lose it by a factor (alpha+beta)/beta
 // per step).  Deferring the normalization saves one pass over the basis.
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <cstdlib>
 #include <type_traits>
@@ -767,7 +768,7 @@ __global__ void k_solve(const double *__restrict__ dsum_all, const double *__res
     return;
   }
   for (int j = lane; j < K1; j += blockDim.x) {
-    sc[j] = 1.0 / sqrt(gram[((int64_t)j * s + j) * ld + p]);
+    sc[j] = rsqrt(gram[((int64_t)j * s + j) * ld + p]);
     y[j] = dsum[j * ld + p];
   }
   __syncthreads();
@@ -777,13 +778,13 @@ __global__ void k_solve(const double *__restrict__ dsum_all, const double *__res
   }
   __syncthreads();
   // Cholesky of Ghat = D^-1/2 G D^-1/2 (unit diagonal), in place, right-looking:
-  // column c is scaled by its pivot, then the trailing block is updated by
-  // all lanes of the warp.
+  // the diagonal keeps the inverse pivot 1/L_cc, column c is scaled by it,
+  // then the trailing block is updated by all lanes of the warp.
   for (int c = 0; c < K1; ++c) {
-    if (lane == 0) A[c * K1 + c] = sqrt(fmax(A[c * K1 + c], 1e-300));
+    if (lane == 0) A[c * K1 + c] = rsqrt(fmax(A[c * K1 + c], 1e-300));
     __syncwarp();
-    const double piv = A[c * K1 + c];
-    for (int i = c + 1 + lane; i < K1; i += 32) A[i * K1 + c] /= piv;
+    const double ipiv = A[c * K1 + c];
+    for (int i = c + 1 + lane; i < K1; i += 32) A[i * K1 + c] *= ipiv;
     __syncwarp();
     const int rem = K1 - c - 1;  // trailing rows c+1..K1-1, lower triangle
     for (int e = lane; e < rem * rem; e += 32) {
@@ -796,18 +797,116 @@ __global__ void k_solve(const double *__restrict__ dsum_all, const double *__res
   for (int i = lane; i < K1; i += 32) y[i] *= sc[i];
   __syncwarp();
   for (int c = 0; c < K1; ++c) {
-    if (lane == 0) y[c] /= A[c * K1 + c];
+    if (lane == 0) y[c] *= A[c * K1 + c];
     __syncwarp();
     for (int i = c + 1 + lane; i < K1; i += 32) y[i] -= A[i * K1 + c] * y[c];
     __syncwarp();
   }
   for (int c = K1 - 1; c >= 0; --c) {
-    if (lane == 0) y[c] /= A[c * K1 + c];
+    if (lane == 0) y[c] *= A[c * K1 + c];
     __syncwarp();
     for (int i = lane; i < c; i += 32) y[i] -= A[c * K1 + i] * y[c];
     __syncwarp();
   }
   for (int j = lane; j < K1; j += blockDim.x) coef[j * ld + p] = y[j] * sc[j];
+}
+
+// The same step for many problems at once (batches of graphs): one thread per
+// (graph, probe), all steps of the solve serial in that thread, so that every
+// lane of a warp does useful work -- on GB300's narrow FP64 pipe an
+// instruction costs the same with 1 or 32 active lanes.  Each thread keeps the
+// packed lower triangle of Ghat, y and D^-1/2 in shared memory, entry-major
+// with stride kSolveLanes, so a warp's accesses are consecutive words.  T is
+// the arithmetic of the solve: double for the FP64 form, float for the reduced
+// forms, whose update applies the coefficients in FP32 anyway.
+constexpr int kSolveLanes = 32;
+
+constexpr int64_t kSolveLanesMin = 4096;            // problems per launch
+constexpr size_t kSolveLanesSmemMax = 160 * 1024;   // bytes per block
+
+inline size_t solve_lanes_smem(int K1, int tbytes) {
+  return (size_t)kSolveLanes * ((size_t)K1 * (K1 + 1) / 2 + 2 * K1) * tbytes;
+}
+
+template <typename T>
+__device__ __forceinline__ T rsq(T x) {
+  return rsqrt(x);
+}
+template <>
+__device__ __forceinline__ float rsq<float>(float x) {
+  return rsqrtf(x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSolveLanes)
+    k_solve_lanes(const double *__restrict__ dsum_all, const double *__restrict__ gram_all, int k,
+                  int s, int ld, int nv, int n_graphs, int first_pass, int need_coef, double tol,
+                  const double *__restrict__ gbound, int32_t *__restrict__ m_all,
+                  double *__restrict__ alpha_all, double *__restrict__ beta_all,
+                  double *__restrict__ coef_all) {
+  extern __shared__ __align__(16) unsigned char sl_dyn[];
+  const int64_t t = (int64_t)blockIdx.x * kSolveLanes + threadIdx.x;
+  if (t >= (int64_t)n_graphs * nv) return;  // no block-wide barrier below
+  const int gr = (int)(t / nv), p = (int)(t - (int64_t)gr * nv);
+  const int K1 = k + 1;
+  const double *gram = gram_all + (int64_t)gr * s * s * ld;
+  const double *dsum = dsum_all + (int64_t)gr * s * ld;
+  double *coef = coef_all + (int64_t)gr * s * ld;
+  int32_t *m = m_all + (int64_t)gr * nv;
+  bool running = m[p] > k;
+  if (running && first_pass) {
+    const double nk = gram[((int64_t)k * s + k) * ld + p];
+    if (k > 0) {
+      const double b = sqrt(nk) / sqrt(gram[((int64_t)(k - 1) * s + (k - 1)) * ld + p]);
+      if (b <= tol * gbound[gr]) {
+        m[p] = k;
+        running = false;
+      } else {
+        beta_all[((int64_t)gr * nv + p) * s + k - 1] = b;
+      }
+    }
+    if (running) alpha_all[((int64_t)gr * nv + p) * s + k] = dsum[k * ld + p] / nk;
+  }
+  if (!need_coef) return;
+  if (!running) {
+    for (int j = 0; j < K1; ++j) coef[j * ld + p] = 0.0;
+    return;
+  }
+  T *A = reinterpret_cast<T *>(sl_dyn) + threadIdx.x;  // packed (i, j <= i)
+  T *y = A + (size_t)kSolveLanes * (K1 * (K1 + 1) / 2);
+  T *sc = y + (size_t)kSolveLanes * K1;
+#define SLAQ_A(i, j) A[(((i) * ((i) + 1)) / 2 + (j)) * kSolveLanes]
+  for (int i = 0; i < K1; ++i) {
+    sc[i * kSolveLanes] = (T)rsqrt(gram[((int64_t)i * s + i) * ld + p]);
+    y[i * kSolveLanes] = (T)dsum[i * ld + p] * sc[i * kSolveLanes];
+  }
+  for (int i = 0; i < K1; ++i) {
+    const T si = sc[i * kSolveLanes];
+    for (int j = 0; j <= i; ++j)
+      SLAQ_A(i, j) = (T)gram[((int64_t)i * s + j) * ld + p] * si * sc[j * kSolveLanes];
+  }
+  // right-looking Cholesky, inverse pivots on the diagonal
+  for (int c = 0; c < K1; ++c) {
+    const T ip = rsq<T>(fmax(SLAQ_A(c, c), std::numeric_limits<T>::min()));
+    SLAQ_A(c, c) = ip;
+    for (int i = c + 1; i < K1; ++i) SLAQ_A(i, c) *= ip;
+    for (int i = c + 1; i < K1; ++i) {
+      const T lic = SLAQ_A(i, c);
+      for (int q = c + 1; q <= i; ++q) SLAQ_A(i, q) -= lic * SLAQ_A(q, c);
+    }
+  }
+  for (int c = 0; c < K1; ++c) {  // L w = D^-1/2 d
+    const T wc = y[c * kSolveLanes] * SLAQ_A(c, c);
+    y[c * kSolveLanes] = wc;
+    for (int i = c + 1; i < K1; ++i) y[i * kSolveLanes] -= SLAQ_A(i, c) * wc;
+  }
+  for (int c = K1 - 1; c >= 0; --c) {  // L^T xhat = w
+    const T xc = y[c * kSolveLanes] * SLAQ_A(c, c);
+    y[c * kSolveLanes] = xc;
+    for (int i = 0; i < c; ++i) y[i * kSolveLanes] -= SLAQ_A(c, i) * xc;
+  }
+#undef SLAQ_A
+  for (int j = 0; j < K1; ++j) coef[j * ld + p] = (double)(y[j * kSolveLanes] * sc[j * kSolveLanes]);
 }
 
 // ---------------------------------------------------------------- update
@@ -1091,11 +1190,28 @@ int reduce_and_solve(slaq_krylov K, int k, int jfirst, int jcount, bool with_g, 
                                 K->n_graphs, with_g ? 1 : 0, K->dsum, K->gram);
   }
   const int K1 = k + 1;
-  const size_t smem = (size_t)(K1 * K1 + 2 * K1) * sizeof(double);
+  const int64_t problems = (int64_t)K->n_graphs * K->nv;
+  const int tbytes = K->precision == SLAQ_FP64 ? 8 : 4;
   ++tl_launches;
-  k_solve<<<dim3(K->nv, K->n_graphs), 32, smem, st>>>(
-      K->dsum, K->gram, k, K->s, K->ld, K->nv, first_pass ? 1 : 0, need_coef ? 1 : 0, K->tol,
-      K->gbound, K->m, K->alpha, K->beta, K->coef);
+  if (problems >= kSolveLanesMin && solve_lanes_smem(K1, tbytes) <= kSolveLanesSmemMax) {
+    // many small problems: thread per problem
+    const unsigned blocks = (unsigned)ceil_div(problems, kSolveLanes);
+    const size_t smem = solve_lanes_smem(K1, tbytes);
+    if (tbytes == 8)
+      k_solve_lanes<double><<<blocks, kSolveLanes, smem, st>>>(
+          K->dsum, K->gram, k, K->s, K->ld, K->nv, K->n_graphs, first_pass ? 1 : 0,
+          need_coef ? 1 : 0, K->tol, K->gbound, K->m, K->alpha, K->beta, K->coef);
+    else
+      k_solve_lanes<float><<<blocks, kSolveLanes, smem, st>>>(
+          K->dsum, K->gram, k, K->s, K->ld, K->nv, K->n_graphs, first_pass ? 1 : 0,
+          need_coef ? 1 : 0, K->tol, K->gbound, K->m, K->alpha, K->beta, K->coef);
+  } else {
+    // few problems: a warp per problem spreads them over the SMs
+    const size_t smem = (size_t)(K1 * K1 + 2 * K1) * sizeof(double);
+    k_solve<<<dim3(K->nv, K->n_graphs), 32, smem, st>>>(
+        K->dsum, K->gram, k, K->s, K->ld, K->nv, first_pass ? 1 : 0, need_coef ? 1 : 0, K->tol,
+        K->gbound, K->m, K->alpha, K->beta, K->coef);
+  }
   SLAQ_CHECK_LAUNCH("reduce_and_solve");
   return SLAQ_OK;
 }
@@ -1140,6 +1256,12 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_dots<P, true, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_solve_lanes<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSolveLanesSmemMax));
+    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_solve_lanes<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSolveLanesSmemMax));
     attr_set = true;
   }
   // chunk tables: dots chunks fill one wave; update chunks are smaller

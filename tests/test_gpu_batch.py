@@ -125,3 +125,47 @@ def test_sbm_batch_reduced_precision():
     h64 = slaq.trace_heat(slaq.lanczos(gb, 20, 15, 1, precision=slaq.FP64), t)[0].cpu().numpy()
     h32 = slaq.trace_heat(slaq.lanczos(gb, 20, 15, 1, precision=slaq.FP32), t)[0].cpu().numpy()
     assert np.max(np.abs(h32 - h64) / np.abs(h64)) < 1e-4
+
+
+def many_small_graphs(count, seed=7):
+    """A batch large enough (count x nv problems) for the thread-per-problem
+    Gram solve: small BA, ER, cycle and star graphs of 12 to 60 nodes."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(12, 61))
+        kind = i % 4
+        if kind == 0:
+            out.append(synth.barabasi_albert(n, 2, seed=seed + i))
+        elif kind == 1:
+            out.append(synth.erdos_renyi(n, 0.15, seed=seed + i))
+        elif kind == 2:
+            out.append(synth.cycle(n))
+        else:
+            out.append(synth.star(n))
+    return out
+
+
+@pytest.mark.parametrize("reorth", [1, 2])
+def test_many_problems_solve_matches_oracle(reorth):
+    graphs = many_small_graphs(272)
+    nv, s, seed = 16, 10, 13          # 272 * 16 = 4352 problems per solve
+    gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
+    K = slaq.lanczos(gb, nv, s, seed, precision=slaq.FP64, reorth_passes=reorth)
+    alpha, beta, m = (x.cpu().numpy() for x in slaq.krylov_export(K))
+    t = synth.t_grid(32)
+    heat = slaq.trace_heat(K, _dev(t, torch.float64))[0].cpu().numpy()
+    for g in range(0, len(graphs), 9):
+        src, dst, n = graphs[g]
+        lap = build_laplacian(src, dst, n, kind=NORMALIZED, drop_isolated=True)
+        runs = odesc.slq_runs(lap, s, nv, seed, graph=g, reorth_passes=reorth)
+        for p, r in enumerate(runs):
+            assert m[g, p] == r.m, (g, p)
+            np.testing.assert_allclose(alpha[g, p, :r.m], r.alpha, rtol=RTOL, atol=RTOL * lap.norm_bound())
+            np.testing.assert_allclose(beta[g, p, :r.m - 1], r.beta, rtol=RTOL, atol=RTOL * lap.norm_bound())
+        oh, _ = odesc.heat_trace(runs, lap.n, t)
+        np.testing.assert_allclose(heat[g], oh, rtol=RTOL)
+    # the FP32 solve of the reduced forms against the FP64 form
+    h32 = slaq.trace_heat(slaq.lanczos(gb, nv, s, seed, precision=slaq.FP32, reorth_passes=reorth),
+                          _dev(t, torch.float64))[0].cpu().numpy()
+    assert np.max(np.abs(h32 - heat) / np.abs(heat)) < 1e-4
