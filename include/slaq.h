@@ -139,14 +139,35 @@ void slaq_graph_destroy(slaq_graph g);
  *   vectors of its probe by classical Gram-Schmidt (reorth_passes = 1) or
  *   twice (2).  A probe whose beta_k falls to tol * bound (tol 1e-10 FP64,
  *   1e-4 FP32, 3e-2 BF16 basis; bound 2 or 2 max d) stops with m = k+1.
- *   1 <= nv <= 1024, 1 <= s <= 64, precision one of SLAQ_FP64/FP32/
- *   FP32_BF16BASIS, graph_id < 65536.
+ *   1 <= nv <= 512, 1 <= s <= 64, precision one of SLAQ_FP64/FP32/
+ *   FP32_BF16BASIS, graph_id + (graphs in g) - 1 < 65536.
  * inout: if *inout is NULL a new handle is created; otherwise *inout must
  * come from an earlier call with the same nv, s and precision, and its
  * device workspace is reused (grown if the graph is larger).
  * The graph handle must stay alive until the work on `stream` completes. */
 int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id,
                  int precision, int reorth_passes, void *stream, slaq_krylov *inout);
+
+/* slaq_lanczos for a batch of separately built graphs gs[0..count): the
+ * graphs (each a single graph or itself a batch) are concatenated on the
+ * device into one block-diagonal Laplacian owned by the Krylov handle, and
+ * all of them run through the same launches.  Graph g of the concatenation
+ * (in order, sub-graphs of batch handles expanded) gets probe graph field
+ * graph_id + g, so its results equal slaq_lanczos(gs[g], ..., graph_id + g)
+ * up to rounding order.  All graphs must share the Laplacian kind and be all
+ * weighted or all unweighted; at most 65536 graphs in total.
+ * tune_cache: NULL runs the default launch shapes.  Otherwise it names a
+ * text file: if it holds a line for this workload class (precision, nv, s,
+ * reorth_passes, log2 of n', of nnz/n' and of the graph count, SM count) the
+ * launch shapes on it are used; if not, the call first times candidate
+ * shapes on this batch (coordinate descent, about a dozen full runs), keeps
+ * the fastest and adds its line (the file is rewritten through a temporary
+ * beside it).  An unreadable or unwritable file gives SLAQ_EINVAL.
+ * The inputs gs may be destroyed once the call returns.  Synchronizes
+ * `stream`; other arguments and errors as for slaq_lanczos. */
+int slaq_lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t seed,
+                         int graph_id, int precision, int reorth_passes,
+                         const char *tune_cache, void *stream, slaq_krylov *inout);
 
 /* The probe block the Lanczos run starts from, as float64[n'][nv] (+-1),
  * generated on the device exactly as slaq_lanczos does (Eq. trace needs

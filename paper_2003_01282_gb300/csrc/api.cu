@@ -273,6 +273,21 @@ int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int p
   return SLAQ_OK;
 }
 
+int slaq_lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t seed,
+                         int graph_id, int precision, int reorth_passes, const char *tune_cache,
+                         void *stream, slaq_krylov *inout) {
+  SLAQ_TRY(device_check());
+  cudaStream_t st = as_stream(stream);
+  SLAQ_TRY(lanczos_batched(gs, count, nv, s, seed, graph_id, precision, reorth_passes, tune_cache,
+                           st, inout));
+  int32_t status = 0;
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, (*inout)->status, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
+  return SLAQ_OK;
+}
+
 int slaq_probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, void *stream) {
   SLAQ_TRY(device_check());
   return probes(g, nv, seed, graph_id, out, as_stream(stream));

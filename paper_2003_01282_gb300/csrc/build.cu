@@ -15,6 +15,7 @@
 // any correct builder's bit for bit.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -616,6 +617,42 @@ int persistent(T **p, size_t count) {
 }
 }  // namespace
 
+// SpMM schedule for rows of the execution copy with more than heavy_degree
+// entries: each is split into chunks of kHeavyChunk entries.
+static int heavy_schedule(slaq_graph g, Temps &tmp, cudaStream_t st) {
+  int64_t *d_total = nullptr;
+  SLAQ_TRY(tmp.get(&d_total, 1));
+  g->heavy_degree = 4 * kHeavyChunk;
+  if (g->n > 0) {
+    int32_t *is_heavy = nullptr;
+    int64_t *nchunk = nullptr, *slot_of = nullptr, *chunk_of = nullptr;
+    SLAQ_TRY(tmp.get(&is_heavy, g->n));
+    SLAQ_TRY(tmp.get(&nchunk, g->n));
+    SLAQ_TRY(tmp.get(&slot_of, g->n));
+    SLAQ_TRY(tmp.get(&chunk_of, g->n));
+    ++tl_launches;
+    k_heavy_flags<<<grid_for(g->n, 256), 256, 0, st>>>(g->x_rowptr, g->n, g->heavy_degree,
+                                                        is_heavy, nchunk);
+    SLAQ_CHECK_LAUNCH("heavy_flags");
+    SLAQ_TRY(exclusive_scan(is_heavy, g->n, slot_of, d_total, st));
+    SLAQ_TRY(to_host(&g->n_heavy, d_total, 1, st));
+    SLAQ_TRY(exclusive_scan(nchunk, g->n, chunk_of, d_total, st));
+    SLAQ_TRY(to_host(&g->n_chunks, d_total, 1, st));
+    if (g->n_heavy > 0) {
+      SLAQ_TRY(persistent(&g->heavy_row, g->n_heavy));
+      SLAQ_TRY(persistent(&g->heavy_first, g->n_heavy + 1));
+      SLAQ_TRY(persistent(&g->chunk_slot, g->n_chunks));
+      ++tl_launches;
+      k_heavy_table<<<grid_for(g->n, 256), 256, 0, st>>>(is_heavy, slot_of, chunk_of, nchunk,
+                                                          g->n, g->n_heavy, g->n_chunks,
+                                                          g->heavy_row, g->heavy_first,
+                                                          g->chunk_slot);
+      SLAQ_CHECK_LAUNCH("heavy_table");
+    }
+  }
+  return SLAQ_OK;
+}
+
 int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
                     const double *weights, int kind, int flags, cudaStream_t st,
                     slaq_graph *out, int n_graphs, const int64_t *edge_off_host,
@@ -914,37 +951,194 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   }
 
   // 6. SpMM schedule for heavy rows (execution order)
-  g->heavy_degree = 4 * kHeavyChunk;
-  if (n_out > 0) {
-    int32_t *is_heavy = nullptr;
-    int64_t *nchunk = nullptr, *slot_of = nullptr, *chunk_of = nullptr;
-    SLAQ_TRY(tmp.get(&is_heavy, n_out));
-    SLAQ_TRY(tmp.get(&nchunk, n_out));
-    SLAQ_TRY(tmp.get(&slot_of, n_out));
-    SLAQ_TRY(tmp.get(&chunk_of, n_out));
-    ++tl_launches;
-    k_heavy_flags<<<grid_for(n_out, 256), 256, 0, st>>>(g->x_rowptr, n_out, g->heavy_degree,
-                                                        is_heavy, nchunk);
-    SLAQ_CHECK_LAUNCH("heavy_flags");
-    SLAQ_TRY(exclusive_scan(is_heavy, n_out, slot_of, d_total, st));
-    SLAQ_TRY(to_host(&g->n_heavy, d_total, 1, st));
-    SLAQ_TRY(exclusive_scan(nchunk, n_out, chunk_of, d_total, st));
-    SLAQ_TRY(to_host(&g->n_chunks, d_total, 1, st));
-    if (g->n_heavy > 0) {
-      SLAQ_TRY(persistent(&g->heavy_row, g->n_heavy));
-      SLAQ_TRY(persistent(&g->heavy_first, g->n_heavy + 1));
-      SLAQ_TRY(persistent(&g->chunk_slot, g->n_chunks));
-      ++tl_launches;
-      k_heavy_table<<<grid_for(n_out, 256), 256, 0, st>>>(is_heavy, slot_of, chunk_of, nchunk,
-                                                          n_out, g->n_heavy, g->n_chunks,
-                                                          g->heavy_row, g->heavy_first,
-                                                          g->chunk_slot);
-      SLAQ_CHECK_LAUNCH("heavy_table");
-    }
-  }
+  SLAQ_TRY(heavy_schedule(g, tmp, st));
   SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
   *out = g;
   g = nullptr;  // ownership passed to the caller
+  return SLAQ_OK;
+}
+
+
+// --------------------------------------------------------------- unions
+namespace {
+// dst[i] = src[h][i - off[h]] + add[h] for the part h with off[h] <= i < off[h+1]
+template <typename T>
+__global__ void k_concat(const T *const *src, const int64_t *off, const T *add, int parts,
+                         int64_t total, T *dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = parts - 1;  // last part with off <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    dst[i] = src[lo][i - off[lo]] + (add ? add[lo] : T(0));
+  }
+}
+
+// Concatenates one array over the parts: part h contributes count[h]
+// elements of srcs[h], each plus add[h] (no addend if add is empty).
+template <typename T>
+int concat(Temps &tmp, const std::vector<const T *> &srcs, const std::vector<int64_t> &count,
+           const std::vector<T> &add, T *dst, cudaStream_t st) {
+  const int parts = (int)srcs.size();
+  std::vector<int64_t> off(parts + 1, 0);
+  for (int h = 0; h < parts; ++h) off[h + 1] = off[h] + count[h];
+  if (off[parts] == 0) return SLAQ_OK;
+  const T **d_src = nullptr;
+  int64_t *d_off = nullptr;
+  T *d_add = nullptr;
+  SLAQ_TRY(tmp.get(&d_src, parts));
+  SLAQ_TRY(tmp.get(&d_off, parts + 1));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_src, srcs.data(), parts * sizeof(T *), cudaMemcpyHostToDevice, st));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_off, off.data(), (parts + 1) * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, st));
+  if (!add.empty()) {
+    SLAQ_TRY(tmp.get(&d_add, parts));
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_add, add.data(), parts * sizeof(T), cudaMemcpyHostToDevice, st));
+  }
+  ++tl_launches;
+  k_concat<T><<<grid_for(off[parts], 256), 256, 0, st>>>(d_src, d_off, d_add, parts, off[parts], dst);
+  SLAQ_CHECK_LAUNCH("concat");
+  return SLAQ_OK;  // copies from pageable memory are staged before they return
+}
+}  // namespace
+
+int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *out) {
+  if (!out) return set_error(SLAQ_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!gs || count < 1) return set_error(SLAQ_EINVAL, "need at least one graph");
+  int dev = 0;
+  SLAQ_CHECK_CUDA(cudaGetDevice(&dev));
+  int64_t G = 0;
+  for (int h = 0; h < count; ++h) {
+    const slaq_graph a = gs[h];
+    if (!a) return set_error(SLAQ_EINVAL, "graph %d is NULL", h);
+    if (a->device != dev) return set_error(SLAQ_EINVAL, "graph %d lives on another device", h);
+    if (a->kind != gs[0]->kind || a->weighted != gs[0]->weighted)
+      return set_error(SLAQ_EINVAL, "graph %d: all graphs need one Laplacian kind and all or "
+                       "none weighted", h);
+    G += a->n_graphs;
+  }
+  if (G > 65536) return set_error(SLAQ_EINVAL, "a batch holds at most 65536 graphs");
+  Temps tmp(st);
+  slaq_graph g = new slaq_graph_s();
+  struct Guard {
+    slaq_graph *g;
+    ~Guard() {
+      if (*g) graph_free(*g);
+    }
+  } guard{&g};
+  g->device = dev;
+  g->kind = gs[0]->kind;
+  g->flags = gs[0]->flags;
+  g->weighted = gs[0]->weighted;
+  g->n_graphs = (int)G;
+  g->goff.assign(1, 0);
+  std::vector<int64_t> n_of(count), nnz_of(count), np1_of(count);
+  std::vector<int64_t> node_add(count), entry_add(count), input_add(count);
+  std::vector<int32_t> col_add(count), graph_add(count);
+  int64_t n = 0, nnz = 0, n_in = 0;
+  int32_t gfirst = 0;
+  for (int h = 0; h < count; ++h) {
+    const slaq_graph a = gs[h];
+    n_of[h] = a->n;
+    nnz_of[h] = a->nnz;
+    np1_of[h] = a->n;  // rowptr: the first n entries of each part, the end appended
+    node_add[h] = n;
+    col_add[h] = (int32_t)n;
+    entry_add[h] = nnz;
+    input_add[h] = n_in;
+    graph_add[h] = gfirst;
+    for (int q = 0; q < a->n_graphs; ++q) {
+      g->goff.push_back(n + a->goff[q + 1]);
+      g->gtrace.push_back(a->gtrace[q]);
+      g->gbound.push_back(a->gbound[q]);
+    }
+    n += a->n;
+    nnz += a->nnz;
+    n_in += a->n_input;
+    gfirst += a->n_graphs;
+  }
+  if (n > 0x7fffffffLL) return set_error(SLAQ_EUNSUPPORTED, "more than 2^31 - 1 nodes in a batch");
+  g->n = n;
+  g->nnz = nnz;
+  g->n_input = n_in;
+  g->trace = g->gtrace[0];
+  g->bound = *std::max_element(g->gbound.begin(), g->gbound.end());
+  const bool w = g->weighted;
+  SLAQ_TRY(persistent(&g->rowptr, n + 1));
+  SLAQ_TRY(persistent(&g->colidx, nnz));
+  SLAQ_TRY(persistent(&g->vals, nnz));
+  if (w) SLAQ_TRY(persistent(&g->vals32, nnz));
+  SLAQ_TRY(persistent(&g->diag, n));
+  SLAQ_TRY(persistent(&g->scale, n));
+  SLAQ_TRY(persistent(&g->diag32, n));
+  SLAQ_TRY(persistent(&g->scale32, n));
+  SLAQ_TRY(persistent(&g->old_id, n));
+  SLAQ_TRY(persistent(&g->x_rowptr, n + 1));
+  SLAQ_TRY(persistent(&g->x_colidx, nnz));
+  SLAQ_TRY(persistent(&g->x_vals, nnz));
+  if (w) SLAQ_TRY(persistent(&g->x_vals32, nnz));
+  SLAQ_TRY(persistent(&g->x_diag, n));
+  SLAQ_TRY(persistent(&g->x_scale, n));
+  SLAQ_TRY(persistent(&g->x_diag32, n));
+  SLAQ_TRY(persistent(&g->x_scale32, n));
+  SLAQ_TRY(persistent(&g->x_old_id, n));
+  SLAQ_TRY(persistent(&g->x_graph, n));
+  auto ptrs = [&](auto field) {
+    using T = std::remove_pointer_t<std::remove_reference_t<decltype(gs[0]->*field)>>;
+    std::vector<const T *> v(count);
+    for (int h = 0; h < count; ++h) v[h] = gs[h]->*field;
+    return v;
+  };
+  const std::vector<double> no_d;
+  const std::vector<float> no_f;
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::rowptr), np1_of, entry_add, g->rowptr, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_rowptr), np1_of, entry_add, g->x_rowptr, st));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(g->rowptr + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(g->x_rowptr + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::colidx), nnz_of, col_add, g->colidx, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_colidx), nnz_of, col_add, g->x_colidx, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::vals), nnz_of, no_d, g->vals, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_vals), nnz_of, no_d, g->x_vals, st));
+  if (w) {
+    SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::vals32), nnz_of, no_f, g->vals32, st));
+    SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_vals32), nnz_of, no_f, g->x_vals32, st));
+  }
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::diag), n_of, no_d, g->diag, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::scale), n_of, no_d, g->scale, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::diag32), n_of, no_f, g->diag32, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::scale32), n_of, no_f, g->scale32, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_diag), n_of, no_d, g->x_diag, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_scale), n_of, no_d, g->x_scale, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_diag32), n_of, no_f, g->x_diag32, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_scale32), n_of, no_f, g->x_scale32, st));
+  // canonical ids live in the union's input numbering, execution ids stay
+  // local to their graph (the probe signs), graph numbers are shifted
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::old_id), n_of, input_add, g->old_id, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_old_id), n_of, std::vector<int64_t>(), g->x_old_id, st));
+  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_graph), n_of, graph_add, g->x_graph, st));
+  {
+    std::vector<double> gn(G);
+    for (int64_t q = 0; q < G; ++q) gn[q] = (double)(g->goff[q + 1] - g->goff[q]);
+    SLAQ_TRY(persistent(&g->goff_dev, G + 1));
+    SLAQ_TRY(persistent(&g->gn_dev, G));
+    SLAQ_TRY(persistent(&g->gtrace_dev, G));
+    SLAQ_TRY(persistent(&g->gbound_dev, G));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->goff_dev, g->goff.data(), (G + 1) * sizeof(int64_t),
+                               cudaMemcpyHostToDevice));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->gn_dev, gn.data(), G * sizeof(double), cudaMemcpyHostToDevice));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->gtrace_dev, g->gtrace.data(), G * sizeof(double),
+                               cudaMemcpyHostToDevice));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->gbound_dev, g->gbound.data(), G * sizeof(double),
+                               cudaMemcpyHostToDevice));
+  }
+  SLAQ_TRY(heavy_schedule(g, tmp, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  *out = g;
+  g = nullptr;
   return SLAQ_OK;
 }
 

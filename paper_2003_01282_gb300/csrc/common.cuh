@@ -136,6 +136,15 @@ struct slaq_graph_s {
   int32_t *chunk_slot = nullptr;     // [n_chunks] heavy slot of each chunk
 };
 
+// Launch shapes of the Lanczos kernels; slaq_lanczos_batched's autotuner
+// picks them per workload, every other call uses these defaults.
+struct slaq_tuning {
+  int spmm_threads = 256;  // threads of a light-row SpMM block
+  int upd_threads = 256;   // threads of an update block
+  int dots_threads = 128;  // narrow dots blocks grow row phases up to this many threads
+  int slice_bytes = 0;     // bytes of a basis row per probe slice (0: whole rows)
+};
+
 struct slaq_krylov_s {
   int device = -1;
   int nv = 0, s = 0, ld = 0, precision = 0, reorth = 1;
@@ -181,6 +190,8 @@ struct slaq_krylov_s {
   // side stream on which the split-row SpMM runs beside the light rows
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  slaq_tuning tune;                // launch shapes of the last run
+  slaq_graph owned = nullptr;      // union of a slaq_lanczos_batched call
 };
 
 namespace slaq {
@@ -191,7 +202,12 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges, int
                     const int64_t *node_off_host = nullptr);
 void graph_free(slaq_graph g);
 int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
-                int reorth, cudaStream_t st, slaq_krylov *inout);
+                int reorth, cudaStream_t st, slaq_krylov *inout,
+                const slaq_tuning *tune = nullptr);
+int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *out);
+int lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t seed, int graph_id,
+                    int precision, int reorth, const char *tune_cache, cudaStream_t st,
+                    slaq_krylov *inout);
 void krylov_free(slaq_krylov k);
 int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st);
 int run_ritz(slaq_krylov k, cudaStream_t st);

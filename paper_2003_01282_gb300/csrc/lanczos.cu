@@ -292,7 +292,7 @@ __device__ __forceinline__ void finish_row(int64_t row, const typename Form<P>::
 // team of Vt = w / VE threads per row, each owning VE probe columns.  Blocks
 // run slice-major, so one slice of u_k is gathered at a time.
 template <int P, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     k_spmm_light(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                  const typename Form<P>::TW *__restrict__ vals,
                  const typename Form<P>::TW *__restrict__ diag,
@@ -630,8 +630,10 @@ __global__ void __launch_bounds__(512, 2)
 }
 
 // row phases of a dots block: narrow blocks (few column vectors and basis
-// vectors) grow along threadIdx.z up to 128 threads
-inline int dots_phases(int V, int Jb) { return std::max(1, std::min(8, 128 / (V * Jb))); }
+// vectors) grow along threadIdx.z up to `target` threads
+inline int dots_phases(int V, int Jb, int target) {
+  return std::max(1, std::min(8, target / (V * Jb)));
+}
 
 // dynamic shared memory of a dots block: staging tiles, reused at the end
 // for the row-phase sums ([rz][Jb][ld][2] doubles)
@@ -914,7 +916,7 @@ __global__ void __launch_bounds__(kSolveLanes)
 // u_{k+1} (second pass, in place), rounded to the basis type; stopped probes
 // and padding columns get 0.  A pure streaming pass over the basis.
 template <int P, bool SECOND>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     k_update(const typename Form<P>::TB *__restrict__ U, const typename Form<P>::TW *__restrict__ Z,
              typename Form<P>::TB *Unext, Slc S, const int64_t *__restrict__ crow0,
              const int32_t *__restrict__ crows, const int32_t *__restrict__ cgraph, int V, int R,
@@ -984,44 +986,32 @@ struct Geometry {
   int Vt, Rt, tthreads;   // SpMM: Vt threads per row and slice, Rt rows per block
   int sms;
   int Jb;                 // basis vectors per dots block
+  int dots_threads;       // row phases fill narrow dots blocks up to this
 };
 
-// Slice width: the whole row when n * ld fits the L2 budget; otherwise the
-// widest multiple of a 32-byte sector whose slice fits (no slicing if even
-// one sector per row does not).
-constexpr int64_t kL2Budget = 48ll << 20;
-int slice_width(int precision, int ld, int64_t n) {
+// Slice width in elements: whole rows unless the tuning asks for slices of
+// slice_bytes (rounded down to whole 32-byte sectors).  Measured on R-MAT
+// 2^20, unsliced gathers are the fastest, so that is the default.
+int slice_width(int precision, int ld, int slice_bytes) {
+  if (slice_bytes <= 0) return ld;
   const int b = basis_bytes(precision);
-  const int sector = 32 / b;
-  // SLAQ_SLICE_BYTES: bytes of a row per slice (a multiple of 32), or -1 for
-  // no slicing; unset or 0 chooses by the L2 budget.
-  static const long forced = [] {
-    const char *e = getenv("SLAQ_SLICE_BYTES");
-    return e ? atol(e) : 0L;
-  }();
-  if (forced <= 0) return ld;  // measured: unsliced gathers are faster on the R-MAT workload
-  {
-    const int w = (int)std::max<long>(sector, forced / 32 * 32 / b);
-    return std::min(w, ld);
-  }
-  if (n * ld * (int64_t)b <= kL2Budget) return ld;
-  const int64_t w = kL2Budget / (n * b) / sector * sector;
-  if (w < sector) return ld;
-  return (int)std::min<int64_t>(w, ld);
+  const int w = std::max(32 / b, slice_bytes / 32 * 32 / b);
+  return std::min(w, ld);
 }
 
-Geometry geometry(int precision, int ld, int64_t n, int sms) {
+Geometry geometry(int precision, int ld, int64_t n, int sms, const slaq_tuning &t) {
   Geometry g;
   g.sms = sms;
   g.S.n = n;
   g.S.ld = ld;
-  g.S.w = slice_width(precision, ld, n);
+  g.S.w = slice_width(precision, ld, t.slice_bytes);
   g.Vt = g.S.w / vec_elems(precision);
-  g.Rt = std::max(1, 256 / g.Vt);
+  g.Rt = std::max(1, std::min(t.spmm_threads, 512) / g.Vt);
   g.tthreads = g.Vt * g.Rt;
   g.V = ld / vec_elems(precision);
-  g.R = std::max(1, 256 / g.V);
+  g.R = std::max(1, std::min(t.upd_threads, 512) / g.V);
   g.threads = g.V * g.R;
+  g.dots_threads = std::max(32, std::min(t.dots_threads, 512));
   g.Jb = std::max(1, std::min(64, 512 / g.V));
   return g;
 }
@@ -1144,7 +1134,7 @@ int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int j
   using TB = typename Form<P>::TB;
   const int jcount = jlast - jfirst + 1;
   const int Jb = std::min(jcount, geo.Jb);
-  const int RZ = dots_phases(geo.V, Jb);
+  const int RZ = dots_phases(geo.V, Jb, geo.dots_threads);
   const size_t smem = dots_smem(P, K->ld, x_is_basis, Jb, RZ);
   const int threads = geo.V * Jb * RZ;
   // split every chunk so that small blocks (few basis vectors) still fill the SMs
@@ -1243,7 +1233,7 @@ template <int P>
 int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   using TB = typename Form<P>::TB;
   const int64_t n = gr->n;
-  const Geometry geo = geometry(P, K->ld, n, num_sms());
+  const Geometry geo = geometry(P, K->ld, n, num_sms(), K->tune);
   static bool attr_set = false;
   if (!attr_set) {
     SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_update<P, false>,
@@ -1267,7 +1257,7 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   // chunk tables: dots chunks fill one wave; update chunks are smaller
   {
     const int Jb = std::min(K->s, geo.Jb);
-    const int RZ = dots_phases(geo.V, Jb);
+    const int RZ = dots_phases(geo.V, Jb, geo.dots_threads);
     const int per_sm = blocks_per_sm(k_dots<P, false, true>, geo.V * Jb * RZ,
                                      dots_smem(P, K->ld, false, Jb, RZ));
     const int64_t want_d = (int64_t)geo.sms * per_sm;
@@ -1371,11 +1361,12 @@ void krylov_free(slaq_krylov k) {
   if (k->ev_fork) cudaEventDestroy(k->ev_fork);
   if (k->ev_join) cudaEventDestroy(k->ev_join);
   if (k->side) cudaStreamDestroy(k->side);
+  graph_free(k->owned);
   delete k;
 }
 
 int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
-                int reorth, cudaStream_t st, slaq_krylov *inout) {
+                int reorth, cudaStream_t st, slaq_krylov *inout, const slaq_tuning *tune) {
   if (!g || !inout) return set_error(SLAQ_EINVAL, "NULL graph or output handle");
   if (nv < 1 || nv > 512) return set_error(SLAQ_EINVAL, "nv must be in [1, 512]");
   if (s < 1 || s > 64) return set_error(SLAQ_EINVAL, "s must be in [1, 64]");
@@ -1410,9 +1401,12 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
       if (fresh && *K) krylov_free(*K);
     }
   } guard{&K, fresh};
+  if (graph_id + g->n_graphs - 1 > 0xffff)
+    return set_error(SLAQ_EINVAL, "graph_id + n_graphs - 1 must be < 65536");
+  K->tune = tune ? *tune : slaq_tuning();
   const int64_t n = g->n;
   const int G = g->n_graphs;
-  const Geometry geo = geometry(precision, ld, n, num_sms());
+  const Geometry geo = geometry(precision, ld, n, num_sms(), K->tune);
   if (n > K->n_cap) {
     SLAQ_TRY(grow(reinterpret_cast<unsigned char **>(&K->U), (size_t)s * n * ld * basis_bytes(precision)));
     SLAQ_TRY(grow(reinterpret_cast<unsigned char **>(&K->Z), (size_t)n * ld * work_bytes(precision)));

@@ -48,6 +48,7 @@ _SIGNATURES = {
     "slaq_graph_export": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "slaq_graph_destroy": (None, [_VP]),
     "slaq_lanczos": (_I, [_VP, _I, _I, _U64, _I, _I, _I, _VP, _PVP]),
+    "slaq_lanczos_batched": (_I, [_VP, _I, _I, _I, _U64, _I, _I, _I, C.c_char_p, _VP, _PVP]),
     "slaq_probes": (_I, [_VP, _I, _U64, _I, _VP, _VP]),
     "slaq_krylov_export": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_ritz_export": (_I, [_VP, _VP, _VP, _VP]),
@@ -241,6 +242,24 @@ def lanczos(g, nv: int, s: int, seed: int, graph_id: int = 0, precision=FP64, re
     _check(lib().slaq_lanczos(_handle(g), int(nv), int(s), C.c_uint64(int(seed) & (2**64 - 1)),
                               int(graph_id), int(precision), int(reorth_passes), _stream(stream),
                               C.byref(h)))
+    if reuse is not None:
+        return reuse
+    return Krylov(h)
+
+
+def lanczos_batched(graphs, nv: int, s: int, seed: int, graph_id: int = 0, precision=FP64,
+                    reorth_passes: int = 1, tune_cache=None, stream=None, reuse=None):
+    """slaq_lanczos_batched: one Lanczos run over the concatenation of the
+    graph handles `graphs` (the handle owns the concatenation)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    arr = (C.c_void_p * len(graphs))(*[_handle(g).value for g in graphs])
+    h = C.c_void_p(reuse.ptr.value if reuse is not None else None)
+    cache = None if tune_cache is None else os.fsencode(tune_cache)
+    _check(lib().slaq_lanczos_batched(C.cast(arr, C.c_void_p), len(graphs), int(nv), int(s),
+                                      C.c_uint64(int(seed) & (2**64 - 1)), int(graph_id),
+                                      int(precision), int(reorth_passes), cache, _stream(stream),
+                                      C.byref(h)))
     if reuse is not None:
         return reuse
     return Krylov(h)

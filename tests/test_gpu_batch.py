@@ -169,3 +169,76 @@ def test_many_problems_solve_matches_oracle(reorth):
     h32 = slaq.trace_heat(slaq.lanczos(gb, nv, s, seed, precision=slaq.FP32, reorth_passes=reorth),
                           _dev(t, torch.float64))[0].cpu().numpy()
     assert np.max(np.abs(h32 - heat) / np.abs(heat)) < 1e-4
+
+
+def _single_handles(graphs, kind=slaq.NORMALIZED, flags=0):
+    return [slaq.build_laplacian(_dev(s, torch.int32), _dev(d, torch.int32), n, kind=kind, flags=flags)
+            for s, d, n in graphs]
+
+
+@pytest.mark.parametrize("prec", [slaq.FP64, slaq.FP32, slaq.FP32_BF16BASIS])
+def test_lanczos_batched_equals_batch_build(prec):
+    """The device-side concatenation of separately built graphs is the same
+    block-diagonal Laplacian the batch builder makes, so the runs agree bit
+    for bit."""
+    graphs = mixed_batch()
+    nv, s, seed = 6, 12, 21
+    gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
+    want = slaq.krylov_export(slaq.lanczos(gb, nv, s, seed, graph_id=2, precision=prec))
+    hs = _single_handles(graphs, flags=slaq.DROP_ISOLATED)
+    K = slaq.lanczos_batched(hs, nv, s, seed, graph_id=2, precision=prec)
+    del hs  # the Krylov handle owns the concatenation
+    got = slaq.krylov_export(K)
+    for a, b in zip(got, want):
+        assert torch.equal(a, b)
+    t = _dev(synth.t_grid(), torch.float64)
+    assert slaq.trace_heat(K, t)[0].shape == (len(graphs), t.numel())
+
+
+def test_lanczos_batched_expands_batch_handles():
+    graphs = mixed_batch()
+    nv, s, seed = 5, 10, 3
+    whole = slaq.build_laplacian_batch(graphs)
+    parts = [slaq.build_laplacian_batch(graphs[:4]), *_single_handles(graphs[4:6]),
+             slaq.build_laplacian_batch(graphs[6:])]
+    a = slaq.krylov_export(slaq.lanczos(whole, nv, s, seed))
+    b = slaq.krylov_export(slaq.lanczos_batched(parts, nv, s, seed))
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_lanczos_batched_tune_cache(tmp_path):
+    graphs = mixed_batch()
+    nv, s, seed = 8, 12, 4
+    hs = _single_handles(graphs)
+    cache = tmp_path / "tune.txt"
+    K1 = slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP64, tune_cache=str(cache))
+    lines = [ln for ln in cache.read_text().splitlines() if ln and not ln.startswith("#")]
+    assert len(lines) == 1 and "nv=8 s=12" in lines[0]
+    shape = [int(x) for x in lines[0].split("|")[1].split()]
+    assert len(shape) == 4 and shape[0] in (128, 256, 512) and shape[2] in (64, 128, 256)
+    K2 = slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP64, tune_cache=str(cache))
+    assert cache.read_text().splitlines()[1:] == lines        # read, not re-tuned
+    for x, y in zip(slaq.krylov_export(K1), slaq.krylov_export(K2)):
+        assert torch.equal(x, y)
+    # tuned launch shapes change only the rounding order
+    ref = slaq.krylov_export(slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP64))
+    for x, y in zip(slaq.krylov_export(K1)[:2], ref[:2]):
+        np.testing.assert_allclose(x.cpu().numpy(), y.cpu().numpy(), rtol=RTOL, atol=RTOL * 2)
+    # every launch shape in the candidate lists runs correctly
+    for line in ("256 256 128 0", "512 128 64 128", "128 512 256 256"):
+        cache.write_text(lines[0].split("|")[0] + "| " + line + "\n")
+        K3 = slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP32, tune_cache=str(cache))
+        h3 = slaq.trace_heat(K3, _dev(synth.t_grid(), torch.float64))[0].cpu().numpy()
+        h64 = slaq.trace_heat(K1, _dev(synth.t_grid(), torch.float64))[0].cpu().numpy()
+        assert np.max(np.abs(h3 - h64) / np.abs(h64)) < 1e-4, line
+
+
+def test_lanczos_batched_rejects_mixed_kinds():
+    graphs = mixed_batch()[:2]
+    hs = _single_handles(graphs[:1]) + _single_handles(graphs[1:], kind=slaq.COMBINATORIAL)
+    with pytest.raises(slaq.SlaqError) as ei:
+        slaq.lanczos_batched(hs, 4, 5, 1)
+    assert ei.value.status == 1
+    with pytest.raises(slaq.SlaqError):
+        slaq.lanczos_batched([], 4, 5, 1)
