@@ -159,7 +159,8 @@ int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id,
  * tune_cache: NULL runs the default launch shapes.  Otherwise it names a
  * text file: if it holds a line for this workload class (precision, nv, s,
  * reorth_passes, log2 of n', of nnz/n' and of the graph count, SM count) the
- * launch shapes on it are used; if not, the call first times candidate
+ * launch shapes on it are used (line format "<class> | spmm_threads
+ * update_threads dots_threads slice_bytes spmm_align"); if not, the call first times candidate
  * shapes on this batch (coordinate descent, about a dozen full runs), keeps
  * the fastest and adds its line (the file is rewritten through a temporary
  * beside it).  An unreadable or unwritable file gives SLAQ_EINVAL.

@@ -4,7 +4,8 @@
 // Pipeline, all on the device:
 //   1. validate ids; emit both orientations of every non-loop edge as 64-bit
 //      keys (row << cb | col), with the weight as payload;
-//   2. stable LSD radix sort of the keys (8-bit digits, reduce-then-scan);
+//   2. stable LSD radix sort of the keys (8-bit digits, reduce-then-scan,
+//      tiles reordered by digit in shared memory before the scatter);
 //   3. merge duplicates (largest weight kept), rowptr from the sorted rows;
 //   4. degrees, optional removal of isolated nodes with order-preserving
 //      renumbering, scales s_i = 1/sqrt(d_i) and off-diagonal values;
@@ -134,49 +135,64 @@ int exclusive_scan(const TI *in, int64_t n, int64_t *out, int64_t *total_dev, cu
 }
 
 // ------------------------------------------------------------- radix sort
-constexpr int kRsThreads = 256;
+constexpr int kRsThreads = 512;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsRounds = 16;                       // 32-key rounds per warp
-constexpr int kRsTile = kRsThreads * kRsRounds;     // 4096 keys per block
+constexpr int kRsTile = kRsThreads * kRsRounds;     // 8192 keys per block
+constexpr int kRsHistThreads = 256;
 
-__global__ void k_radix_hist(const uint64_t *keys, int64_t n, int shift, uint32_t *counts,
-                             int64_t ntiles) {
+__global__ void __launch_bounds__(kRsHistThreads)
+    k_radix_hist(const uint64_t *keys, int64_t n, int shift, uint32_t *counts, int64_t ntiles) {
   __shared__ uint32_t hist[256];
   hist[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kRsTile;
 #pragma unroll 4
-  for (int it = 0; it < kRsRounds; ++it) {
-    int64_t i = base + (int64_t)it * kRsThreads + threadIdx.x;
+  for (int it = 0; it < kRsTile / kRsHistThreads; ++it) {
+    int64_t i = base + (int64_t)it * kRsHistThreads + threadIdx.x;
     if (i < n) atomicAdd(&hist[(keys[i] >> shift) & 255u], 1u);
   }
   __syncthreads();
   counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
 }
 
-// Stable scatter: warp w of a block owns keys [tile + 512 w, tile + 512 (w+1))
+// Stable scatter of one tile.  Warp w owns keys [tile + 512 w, tile + 512 (w+1))
 // and ranks them round by round (32 keys per round, lane order), so equal
 // digits keep their input order inside the warp; warps are ordered by a
-// per-digit prefix over warps, tiles by the digit-major global scan.
+// per-digit prefix over warps.  The tile is first reordered by digit in
+// shared memory, then written out run by run, so that consecutive threads
+// store consecutive addresses of one digit's run; tiles are ordered by the
+// digit-major global scan of the per-tile counts.
 template <bool PAYLOAD>
-__global__ void __launch_bounds__(kRsThreads)
+__global__ void __launch_bounds__(kRsThreads, 2)
     k_radix_scatter(const uint64_t *__restrict__ kin, const double *__restrict__ pin,
                     uint64_t *__restrict__ kout, double *__restrict__ pout, int64_t n, int shift,
                     const int64_t *__restrict__ offsets, int64_t ntiles) {
   __shared__ uint32_t whist[kRsWarps][256];
-  __shared__ int64_t gbase[256];
+  __shared__ uint32_t dstart[256];  // first slot of each digit in the reordered tile
+  __shared__ int64_t gbase[256];    // first output slot of each digit of this tile
+  __shared__ uint32_t wsum[8];
+  extern __shared__ __align__(16) unsigned char rs_dyn[];
+  uint64_t *skey = reinterpret_cast<uint64_t *>(rs_dyn);      // [kRsTile]
+  double *spay = reinterpret_cast<double *>(skey + kRsTile);  // [kRsTile] (PAYLOAD)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&whist[0][0])[i] = 0;
   __syncthreads();
-  const int64_t seg = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * (32 * kRsRounds);
+  const int64_t tile0 = (int64_t)blockIdx.x * kRsTile;
+  const int64_t seg = tile0 + (int64_t)warp * (32 * kRsRounds);
   const unsigned lt_mask = (1u << lane) - 1u;
   uint64_t key[kRsRounds];
-  uint32_t local[kRsRounds];
+  uint32_t local[kRsRounds / 2];  // ranks within the warp (< 512), two per word
+  // all loads first: the ranking below synchronizes the warp every round
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    const int64_t i = seg + r * 32 + lane;
+    key[r] = i < n ? kin[i] : 0ull;
+  }
 #pragma unroll
   for (int r = 0; r < kRsRounds; ++r) {
     const int64_t i = seg + r * 32 + lane;
     const bool valid = i < n;
-    key[r] = valid ? kin[i] : 0ull;
     const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & 255u) : 256u;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const uint32_t rank = __popc(peers & lt_mask);
@@ -184,19 +200,35 @@ __global__ void __launch_bounds__(kRsThreads)
     __syncwarp();
     if (d < 256u && rank == 0) whist[warp][d] = before + __popc(peers);
     __syncwarp();
-    local[r] = before + rank;
+    if (r & 1) local[r >> 1] |= (before + rank) << 16;
+    else local[r >> 1] = before + rank;
   }
   __syncthreads();
-  {
-    const int d = threadIdx.x;  // 256 threads, one digit each
+  if (threadIdx.x < 256) {
+    const int d = threadIdx.x;  // one digit per thread: prefix over warps
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kRsWarps; ++w) {
-      uint32_t c = whist[w][d];
+      const uint32_t c = whist[w][d];
       whist[w][d] = run;
       run += c;
     }
     gbase[d] = offsets[(int64_t)d * ntiles + blockIdx.x];
+    // exclusive scan of the digit totals over the 256 threads (8 warps)
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    dstart[d] = inc - run;  // within the warp; warp offsets added below
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    uint32_t add = 0;
+    for (int w = 0; w < warp; ++w) add += wsum[w];
+    dstart[threadIdx.x] += add;
   }
   __syncthreads();
 #pragma unroll
@@ -204,11 +236,24 @@ __global__ void __launch_bounds__(kRsThreads)
     const int64_t i = seg + r * 32 + lane;
     if (i < n) {
       const uint32_t d = (uint32_t)((key[r] >> shift) & 255u);
-      const int64_t pos = gbase[d] + whist[warp][d] + local[r];
-      kout[pos] = key[r];
-      if (PAYLOAD) pout[pos] = pin[i];
+      const uint32_t slot = dstart[d] + whist[warp][d] + ((local[r >> 1] >> (16 * (r & 1))) & 0xffffu);
+      skey[slot] = key[r];
+      if (PAYLOAD) spay[slot] = pin[i];
     }
   }
+  __syncthreads();
+  const int count = (int)min((int64_t)kRsTile, n - tile0);
+  for (int q = threadIdx.x; q < count; q += kRsThreads) {
+    const uint64_t k = skey[q];
+    const uint32_t d = (uint32_t)((k >> shift) & 255u);
+    const int64_t pos = gbase[d] + (q - (int)dstart[d]);
+    kout[pos] = k;
+    if (PAYLOAD) pout[pos] = spay[q];
+  }
+}
+
+inline size_t rs_smem(bool payload) {
+  return (size_t)kRsTile * (sizeof(uint64_t) + (payload ? sizeof(double) : 0));
 }
 
 // Sorts n keys on their low `bits` bits.  Result in *keys (buffers swapped
@@ -223,19 +268,29 @@ int radix_sort(uint64_t **keys, uint64_t **keys_alt, double **pay, double **pay_
   SLAQ_TRY(dalloc_t(&offsets, 256 * ntiles, st));
   SLAQ_TRY(dalloc_t(&total, 1, st));
   const bool with_pay = pay && *pay;
+  static bool attr_set = false;
+  if (!attr_set) {
+    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_radix_scatter<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rs_smem(true)));
+    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_radix_scatter<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rs_smem(false)));
+    attr_set = true;
+  }
   for (int shift = 0; shift < bits; shift += 8) {
     ++tl_launches;
-    k_radix_hist<<<(unsigned)ntiles, kRsThreads, 0, st>>>(*keys, n, shift, counts, ntiles);
+    k_radix_hist<<<(unsigned)ntiles, kRsHistThreads, 0, st>>>(*keys, n, shift, counts, ntiles);
     SLAQ_CHECK_LAUNCH("radix_hist");
     SLAQ_TRY(exclusive_scan(counts, 256 * ntiles, offsets, total, st));
     if (with_pay) {
       ++tl_launches;
-      k_radix_scatter<true><<<(unsigned)ntiles, kRsThreads, 0, st>>>(
+      k_radix_scatter<true><<<(unsigned)ntiles, kRsThreads, rs_smem(true), st>>>(
           *keys, *pay, *keys_alt, *pay_alt, n, shift, offsets, ntiles);
       std::swap(*pay, *pay_alt);
     } else {
       ++tl_launches;
-      k_radix_scatter<false><<<(unsigned)ntiles, kRsThreads, 0, st>>>(
+      k_radix_scatter<false><<<(unsigned)ntiles, kRsThreads, rs_smem(false), st>>>(
           *keys, nullptr, *keys_alt, nullptr, n, shift, offsets, ntiles);
     }
     SLAQ_CHECK_LAUNCH("radix_scatter");
@@ -248,14 +303,24 @@ int radix_sort(uint64_t **keys, uint64_t **keys_alt, double **pay, double **pay_
 }
 
 // ---------------------------------------------------------- CSR kernels
+// Adds a warp's self-loop count to *loops (no atomic when it is zero, so
+// loop-free inputs cost nothing).
+__device__ __forceinline__ void add_loops(unsigned cnt, unsigned long long *loops) {
+  const unsigned tot = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(loops, (unsigned long long)tot);
+}
+
 __global__ void k_validate(const int32_t *src, const int32_t *dst, const double *w, int64_t m,
-                           int64_t n, int32_t *bad) {
+                           int64_t n, int32_t *bad, unsigned long long *loops) {
+  unsigned cnt = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
     int32_t a = src[e], b = dst[e];
     if (a < 0 || b < 0 || a >= n || b >= n) atomicOr(bad, 1);
     if (w && !(w[e] > 0.0)) atomicOr(bad, 2);
+    cnt += a == b;
   }
+  add_loops(cnt, loops);
 }
 
 // Batches: edge e of graph g (edge_off[g] <= e < edge_off[g+1]) has local
@@ -272,7 +337,8 @@ __device__ __forceinline__ int find_segment(const int64_t *off, int G, int64_t x
 
 __global__ void k_union_ids(const int32_t *src, const int32_t *dst, const double *w, int64_t m,
                             const int64_t *edge_off, const int64_t *node_off, int G, int32_t *usrc,
-                            int32_t *udst, int32_t *bad) {
+                            int32_t *udst, int32_t *bad, unsigned long long *loops) {
+  unsigned cnt = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int g = find_segment(edge_off, G, e);
@@ -282,7 +348,9 @@ __global__ void k_union_ids(const int32_t *src, const int32_t *dst, const double
     if (w && !(w[e] > 0.0)) atomicOr(bad, 2);
     usrc[e] = (int32_t)(node_off[g] + (a < 0 ? 0 : a));
     udst[e] = (int32_t)(node_off[g] + (b < 0 ? 0 : b));
+    cnt += a == b;
   }
+  add_loops(cnt, loops);
 }
 
 // Graph of every kept node (canonical order), its id within its graph, and
@@ -362,6 +430,17 @@ __global__ void k_emit(const int32_t *src, const int32_t *dst, const double *w, 
         pay[pos + 1] = w[e];
       }
     }
+  }
+}
+
+// Loop-free input: edge e gives keys 2e and 2e+1.
+__global__ void k_emit_direct(const int32_t *src, const int32_t *dst, const double *w, int64_t m,
+                              int cb, uint64_t *keys, double *pay) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = (uint32_t)src[e], b = (uint32_t)dst[e];
+    reinterpret_cast<ulonglong2 *>(keys)[e] = make_ulonglong2((a << cb) | b, (b << cb) | a);
+    if (pay) reinterpret_cast<double2 *>(pay)[e] = make_double2(w[e], w[e]);
   }
 }
 
@@ -692,10 +771,14 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   SLAQ_TRY(tmp.get(&d_node_off, G + 1));
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_node_off, node_off.data(), (G + 1) * sizeof(int64_t),
                                   cudaMemcpyHostToDevice, st));
+  unsigned long long n_loops = 0;
   if (m > 0) {
     int32_t *bad = nullptr;
+    unsigned long long *loops = nullptr;
     SLAQ_TRY(tmp.get(&bad, 1));
+    SLAQ_TRY(tmp.get(&loops, 1));
     SLAQ_CHECK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+    SLAQ_CHECK_CUDA(cudaMemsetAsync(loops, 0, sizeof(unsigned long long), st));
     if (batch) {
       int64_t *d_edge_off = nullptr;
       int32_t *usrc = nullptr, *udst = nullptr;
@@ -706,18 +789,19 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
                                       cudaMemcpyHostToDevice, st));
       ++tl_launches;
       k_union_ids<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, d_edge_off, d_node_off, G,
-                                                    usrc, udst, bad);
+                                                    usrc, udst, bad, loops);
       src = usrc;
       dst = udst;
     } else {
       ++tl_launches;
-      k_validate<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, n, bad);
+      k_validate<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, n, bad, loops);
     }
     SLAQ_CHECK_LAUNCH("validate");
     int32_t hbad = 0;
     SLAQ_TRY(to_host(&hbad, bad, 1, st));
     if (hbad & 1) return set_error(SLAQ_EINVAL, "edge endpoint outside [0, n_nodes)");
     if (hbad & 2) return set_error(SLAQ_EINVAL, "edge weights must be positive");
+    SLAQ_TRY(to_host(&n_loops, loops, 1, st));
   }
 
   // 2. emit and sort
@@ -733,14 +817,16 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   }
   SLAQ_TRY(tmp.get(&counter, 1));
   SLAQ_CHECK_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
-  if (m > 0) {
+  if (m > 0 && n_loops == 0) {
+    ++tl_launches;
+    k_emit_direct<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, cb, k0, p0);
+    SLAQ_CHECK_LAUNCH("emit");
+  } else if (m > 0) {
     ++tl_launches;
     k_emit<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, cb, k0, p0, counter);
     SLAQ_CHECK_LAUNCH("emit");
   }
-  unsigned long long hm2 = 0;
-  SLAQ_TRY(to_host(&hm2, counter, 1, st));
-  const int64_t m2 = (int64_t)hm2;
+  const int64_t m2 = 2 * (m - (int64_t)n_loops);
   {
     uint64_t *ka = k0, *kb = k1;
     double *pa = p0, *pb = p1;

@@ -289,8 +289,12 @@ __device__ __forceinline__ void finish_row(int64_t row, const typename Form<P>::
 }
 
 // Probe slice sl = blockIdx.x / bps, rows (blockIdx.x % bps) * R + team:
-// team of Vt = w / VE threads per row, each owning VE probe columns.  Blocks
-// run slice-major, so one slice of u_k is gathered at a time.
+// a team of Tw threads per row, Vt = w / VE of them active, each owning VE
+// probe columns.  Tw is Vt rounded up to a power of two (or to whole warps),
+// so a row is never split between two warps: a split row costs an extra L1
+// wavefront for the 128-byte line both warps touch, and the gathers are
+// bound by L1 wavefronts.  Blocks run slice-major, so one slice of u_k is
+// gathered at a time.
 template <int P, int MODE>
 __global__ void __launch_bounds__(512)
     k_spmm_light(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
@@ -298,13 +302,13 @@ __global__ void __launch_bounds__(512)
                  const typename Form<P>::TW *__restrict__ diag,
                  const typename Form<P>::TW *__restrict__ scale,
                  const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
-                 Slc S, int Vt, int R, int64_t bps, int64_t heavy_degree) {
+                 Slc S, int Vt, int Tw, int R, int64_t bps, int64_t heavy_degree) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   const int sl = (int)(blockIdx.x / bps);
   const int64_t rb = blockIdx.x - (int64_t)sl * bps;
-  const int team = threadIdx.x / Vt, lane = threadIdx.x - team * Vt;
-  if (team >= R) return;
+  const int team = threadIdx.x / Tw, lane = threadIdx.x - team * Tw;
+  if (team >= R || lane >= Vt) return;
   const int c = sl * S.w + lane * VE;
   if (c >= S.ld) return;  // narrower last slice
   const int64_t row = rb * R + team;
@@ -983,7 +987,7 @@ constexpr int kMaxSub = 16;  // most pieces a dots chunk is split into
 struct Geometry {
   int V, R, threads;      // teams of V threads, R rows per pass (update)
   Slc S;                  // probe slicing of the basis and work vectors
-  int Vt, Rt, tthreads;   // SpMM: Vt threads per row and slice, Rt rows per block
+  int Vt, Tw, Rt, tthreads;  // SpMM: Vt active of Tw threads per row and slice, Rt rows per block
   int sms;
   int Jb;                 // basis vectors per dots block
   int dots_threads;       // row phases fill narrow dots blocks up to this
@@ -1006,8 +1010,14 @@ Geometry geometry(int precision, int ld, int64_t n, int sms, const slaq_tuning &
   g.S.ld = ld;
   g.S.w = slice_width(precision, ld, t.slice_bytes);
   g.Vt = g.S.w / vec_elems(precision);
-  g.Rt = std::max(1, std::min(t.spmm_threads, 512) / g.Vt);
-  g.tthreads = g.Vt * g.Rt;
+  g.Tw = g.Vt;
+  if (t.spmm_align) {
+    g.Tw = 1;
+    while (g.Tw < g.Vt && g.Tw < 32) g.Tw *= 2;
+    if (g.Vt > 32) g.Tw = (g.Vt + 31) / 32 * 32;
+  }
+  g.Rt = std::max(1, std::min(t.spmm_threads, 512) / g.Tw);
+  g.tthreads = g.Tw * g.Rt;
   g.V = ld / vec_elems(precision);
   g.R = std::max(1, std::min(t.upd_threads, 512) / g.V);
   g.threads = g.V * g.R;
@@ -1100,8 +1110,8 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
   }                                                                                             \
   ++tl_launches;                                                                                \
   k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(gr->x_rowptr, gr->x_colidx, vals, diag, \
-                                                         scale, Uk, Z, geo.S, geo.Vt, geo.Rt,   \
-                                                         bps, gr->heavy_degree);
+                                                         scale, Uk, Z, geo.S, geo.Vt, geo.Tw,   \
+                                                         geo.Rt, bps, gr->heavy_degree);
   // split rows on the side stream, concurrently with the light rows (the two
   // write disjoint rows of z)
   if (gr->n_chunks > 0) {

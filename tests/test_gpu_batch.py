@@ -216,7 +216,7 @@ def test_lanczos_batched_tune_cache(tmp_path):
     lines = [ln for ln in cache.read_text().splitlines() if ln and not ln.startswith("#")]
     assert len(lines) == 1 and "nv=8 s=12" in lines[0]
     shape = [int(x) for x in lines[0].split("|")[1].split()]
-    assert len(shape) == 4 and shape[0] in (128, 256, 512) and shape[2] in (64, 128, 256)
+    assert len(shape) == 5 and shape[0] in (128, 256, 512) and shape[2] in (64, 128, 256)
     K2 = slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP64, tune_cache=str(cache))
     assert cache.read_text().splitlines()[1:] == lines        # read, not re-tuned
     for x, y in zip(slaq.krylov_export(K1), slaq.krylov_export(K2)):
@@ -226,7 +226,7 @@ def test_lanczos_batched_tune_cache(tmp_path):
     for x, y in zip(slaq.krylov_export(K1)[:2], ref[:2]):
         np.testing.assert_allclose(x.cpu().numpy(), y.cpu().numpy(), rtol=RTOL, atol=RTOL * 2)
     # every launch shape in the candidate lists runs correctly
-    for line in ("256 256 128 0", "512 128 64 128", "128 512 256 256"):
+    for line in ("256 256 128 0 1", "512 128 64 128 0", "128 512 256 256 1"):
         cache.write_text(lines[0].split("|")[0] + "| " + line + "\n")
         K3 = slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP32, tune_cache=str(cache))
         h3 = slaq.trace_heat(K3, _dev(synth.t_grid(), torch.float64))[0].cpu().numpy()
