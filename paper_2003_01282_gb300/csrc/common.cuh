@@ -141,7 +141,9 @@ struct slaq_graph_s {
 struct slaq_tuning {
   int spmm_threads = 256;  // threads of a light-row SpMM block
   int upd_threads = 256;   // threads of an update block
-  int dots_threads = 256;  // narrow dots blocks grow row phases up to this many threads
+  int dots_threads = 0;    // narrow dots blocks grow row phases up to this many threads
+                           // (0: 256 for the BF16 basis, whose threads hold half the rows
+                           // in flight, else 128)
   int slice_bytes = 0;     // bytes of a basis row per probe slice (0: whole rows)
   int spmm_align = 1;      // 1: SpMM row teams never straddle two warps
 };

@@ -1021,7 +1021,8 @@ Geometry geometry(int precision, int ld, int64_t n, int sms, const slaq_tuning &
   g.V = ld / vec_elems(precision);
   g.R = std::max(1, std::min(t.upd_threads, 512) / g.V);
   g.threads = g.V * g.R;
-  g.dots_threads = std::max(32, std::min(t.dots_threads, 512));
+  const int dt = t.dots_threads > 0 ? t.dots_threads : (precision == SLAQ_FP32_BF16BASIS ? 256 : 128);
+  g.dots_threads = std::max(32, std::min(dt, 512));
   g.Jb = std::max(1, std::min(64, 512 / g.V));
   return g;
 }
