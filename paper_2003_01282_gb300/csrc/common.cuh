@@ -168,6 +168,9 @@ struct slaq_krylov_s {
   double *dsum = nullptr; // [s][ld] reduced dot products u_j^T z
   double *coef = nullptr; // [s][ld] projection coefficients
   double *gram = nullptr; // [s][s][ld] Gram matrix u_i^T u_j of the stored basis
+  double *proj = nullptr; // [s][s][ld] projected matrix u_i^T L u_j (reduced forms)
+  double *rscratch = nullptr;  // Rayleigh-Ritz work space of the reduced forms
+  int64_t rscratch_cap = 0;
   double *alpha = nullptr;  // [nv][s]
   double *beta = nullptr;   // [nv][s]
   int32_t *m = nullptr;     // [nv]

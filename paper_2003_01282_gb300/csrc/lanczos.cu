@@ -651,12 +651,15 @@ inline size_t dots_smem(int precision, int ld, bool x_is_basis, int Jb = 0, int 
 // Sum the partials of graph g's chunks [goff[g], goff[g+1]) of d_j and, with_g,
 // of the Gram column, for j in [jfirst, jfirst + jcount): d to dsum[g][j][p];
 // g_j is the Gram entry (j, k), stored in gram[g][j][k][p] and gram[g][k][j][p].
+// proj (reduced forms, first pass only): d_j = u_j^T L u_k is also entry
+// (j, k) of the projected matrix, stored like the Gram entries.
 // Block (32, kRedY): x = column, y strides over the chunks; grid
 // (columns / 32, 1 or 2, G).
 constexpr int kRedY = 32;
 __global__ void k_dot_reduce(const double *__restrict__ part, const int32_t *__restrict__ goff,
                              int sub, int s, int ld, int jfirst, int jcount, int k,
-                             double *__restrict__ dsum, double *__restrict__ gram) {
+                             double *__restrict__ dsum, double *__restrict__ gram,
+                             double *__restrict__ proj) {
   __shared__ double ss[kRedY][33];
   const int ncol = jcount * ld;
   const int col = blockIdx.x * 32 + threadIdx.x;
@@ -680,6 +683,11 @@ __global__ void k_dot_reduce(const double *__restrict__ part, const int32_t *__r
     const int64_t gs = (int64_t)gr * s;
     if (which == 0) {
       dsum[(gs + j) * ld + p] = v;
+      if (proj) {
+        double *pm = proj + (int64_t)gr * s * s * ld;
+        pm[((int64_t)j * s + k) * ld + p] = v;
+        pm[((int64_t)k * s + j) * ld + p] = v;
+      }
     } else {
       double *gm = gram + (int64_t)gr * s * s * ld;
       gm[((int64_t)j * s + k) * ld + p] = v;
@@ -693,7 +701,7 @@ __global__ void k_dot_reduce(const double *__restrict__ part, const int32_t *__r
 __global__ void k_dot_reduce_narrow(const double *__restrict__ part, const int32_t *__restrict__ goff,
                                     int sub, int s, int ld, int jfirst, int jcount, int k, int G,
                                     int with_g, double *__restrict__ dsum,
-                                    double *__restrict__ gram) {
+                                    double *__restrict__ gram, double *__restrict__ proj) {
   const int ncol = jcount * ld;
   const int64_t total = (int64_t)G * (with_g ? 2 : 1) * ncol;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
@@ -709,6 +717,11 @@ __global__ void k_dot_reduce_narrow(const double *__restrict__ part, const int32
     const int64_t gs = (int64_t)gr * s;
     if (which == 0) {
       dsum[(gs + j) * ld + p] = v;
+      if (proj) {
+        double *pm = proj + (int64_t)gr * s * s * ld;
+        pm[((int64_t)j * s + k) * ld + p] = v;
+        pm[((int64_t)k * s + j) * ld + p] = v;
+      }
     } else {
       double *gm = gram + (int64_t)gr * s * s * ld;
       gm[((int64_t)j * s + k) * ld + p] = v;
@@ -728,7 +741,6 @@ __global__ void k_dot_reduce_narrow(const double *__restrict__ part, const int32
 // first_pass: also records nu_k^2 = G_kk, beta_{k-1} = nu_k / nu_{k-1}
 // (stopping the probe with m = k if beta_{k-1} <= tol_abs) and
 // alpha_k = d_k / nu_k^2.  need_coef == 0 on the last step.
-constexpr int kMaxS = 64;
 __global__ void k_solve(const double *__restrict__ dsum_all, const double *__restrict__ gram_all,
                         int k, int s, int ld, int nv, int first_pass, int need_coef, double tol,
                         const double *__restrict__ gbound, int32_t *__restrict__ m_all,
@@ -1178,17 +1190,18 @@ int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int j
 int reduce_and_solve(slaq_krylov K, int k, int jfirst, int jcount, bool with_g, bool first_pass,
                      bool need_coef, cudaStream_t st) {
   ProfScope prof(SLAQ_PROF_REDUCE, st);
+  double *pj = with_g ? K->proj : nullptr;  // null for the FP64 form
   ++tl_launches;
   if (K->max_chunks_per_graph * K->dsub >= 8) {
     const dim3 grid((unsigned)ceil_div((int64_t)jcount * K->ld, 32), with_g ? 2 : 1,
                     (unsigned)K->n_graphs);
     k_dot_reduce<<<grid, dim3(32, kRedY), 0, st>>>(K->part, K->d_goff, K->dsub, K->s, K->ld, jfirst,
-                                                   jcount, k, K->dsum, K->gram);
+                                                   jcount, k, K->dsum, K->gram, pj);
   } else {
     const int64_t total = (int64_t)K->n_graphs * (with_g ? 2 : 1) * jcount * K->ld;
     k_dot_reduce_narrow<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 65535LL * 16), 256, 0,
                           st>>>(K->part, K->d_goff, K->dsub, K->s, K->ld, jfirst, jcount, k,
-                                K->n_graphs, with_g ? 1 : 0, K->dsum, K->gram);
+                                K->n_graphs, with_g ? 1 : 0, K->dsum, K->gram, pj);
   }
   const int K1 = k + 1;
   const int64_t problems = (int64_t)K->n_graphs * K->nv;
@@ -1313,8 +1326,10 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   for (int k = 0; k < K->s; ++k) {
     SLAQ_TRY(spmm<P>(gr, K, geo, k, st));
     const bool last = (k == K->s - 1);
-    // last step: only alpha_k = d_k / G_kk and the Gram diagonal entry
-    const int jfirst = last ? k : 0;
+    // last step: only alpha_k = d_k / G_kk and the Gram diagonal entry, except
+    // for the reduced forms, whose Rayleigh-Ritz step needs the whole column
+    // of the projected matrix
+    const int jfirst = (last && P == SLAQ_FP64) ? k : 0;
     SLAQ_TRY(dots<P>(K, geo, n, k, jfirst, k, false, true, K->Z, st));
     SLAQ_TRY(reduce_and_solve(K, k, jfirst, k - jfirst + 1, true, true, !last, st));
     if (last) break;
@@ -1364,7 +1379,8 @@ int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaS
 
 void krylov_free(slaq_krylov k) {
   if (!k) return;
-  void *ptrs[] = {k->U, k->Z, k->P, k->part, k->dsum, k->coef, k->gram, k->alpha, k->beta,
+  void *ptrs[] = {k->U, k->Z, k->P, k->part, k->dsum, k->coef, k->gram, k->proj, k->rscratch,
+                  k->alpha, k->beta,
                   k->m, k->theta, k->tau2, k->status, k->hcount, k->gn, k->gtrace, k->gbound,
                   k->d_row0, k->d_rows, k->d_goff, k->u_row0, k->u_rows, k->u_graph};
   for (void *p : ptrs)
@@ -1443,6 +1459,7 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     // padding columns of the coefficients are never written: keep them zero
     SLAQ_CHECK_CUDA(cudaMemsetAsync(K->coef, 0, (size_t)G * s * ld * sizeof(double), st));
     SLAQ_TRY(grow(&K->gram, (size_t)G * s * s * ld));
+    if (precision != SLAQ_FP64) SLAQ_TRY(grow(&K->proj, (size_t)G * s * s * ld));
     SLAQ_TRY(grow(&K->alpha, ns));
     SLAQ_TRY(grow(&K->beta, ns));
     SLAQ_TRY(grow(&K->m, (size_t)G * nv));

@@ -32,6 +32,135 @@ __global__ void k_ritz(const double *__restrict__ alpha, const double *__restric
   }
 }
 
+// Rayleigh-Ritz on the stored basis, for the reduced forms.  With a basis
+// rounded to FP32 or BF16 the recurrence's T (alpha_k = d_k / G_kk, beta from
+// norm ratios, entries beyond the tridiagonal dropped) carries first-order
+// rounding errors of the stored vectors: with BF16 that is 1e-2 on the heat
+// trace at large t.  The projected pencil (M, G), M = U^T L U and G = U^T U
+// of the stored vectors u_0..u_{m-1}, is exact for the subspace they span,
+// and its Ritz pairs are accurate to second order in those errors.  With
+// G = C C^T (after scaling G to unit diagonal), A = C^{-1} M C^{-T} is the
+// projection of L on the orthonormal basis U C^{-T}, whose first vector is
+// u_0 / ||u_0||: so the Gauss rule of the start vector is that of A's first
+// unit vector.  A is reduced to tridiagonal form by Householder reflections
+// that fix the first unit vector (Golub & Van Loan, Sec. 8.3.1), and that
+// tridiagonal goes through the same Gauss-rule solver as the FP64 form; it
+// replaces alpha and beta, so exports and traces use the corrected rule.  In
+// exact arithmetic A equals the recurrence's T.  One thread per problem; the
+// dense matrices live in global scratch, entry-major over the problems, so
+// a warp's accesses are consecutive words.
+__global__ void k_ritz_pencil(const double *__restrict__ gram_all,
+                              const double *__restrict__ proj_all, const int32_t *__restrict__ mm,
+                              int nv, int s, int ld, int total, double *__restrict__ scr,
+                              double *__restrict__ alpha, double *__restrict__ beta,
+                              double *__restrict__ theta, double *__restrict__ tau2,
+                              int32_t *status) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int gr = q / nv, pp = q - gr * nv;
+  const double *Gm = gram_all + (int64_t)gr * s * s * ld;
+  const double *Mm = proj_all + (int64_t)gr * s * s * ld;
+  const int m = mm[q];
+  const int64_t P = total;
+  double *Ab = scr;                                   // [s][s] full
+  double *Cb = scr + (int64_t)s * s * P;              // packed lower triangle
+  double *Vb = Cb + (int64_t)(s * (s + 1) / 2) * P;   // [2][s] vectors
+#define RA(i, j) Ab[((int64_t)(i) * s + (j)) * P + q]
+#define RC(i, j) Cb[((int64_t)((i) * ((i) + 1) / 2 + (j))) * P + q]
+#define RV(i) Vb[(int64_t)(i) * P + q]
+#define RW(i) Vb[(int64_t)(s + (i)) * P + q]
+#define GE(i, j) Gm[((int64_t)(i) * s + (j)) * ld + pp]
+#define ME(i, j) Mm[((int64_t)(i) * s + (j)) * ld + pp]
+  int bad = 0;
+  // unit-diagonal scaling D = diag(G)^{-1/2}, kept in RV
+  for (int i = 0; i < m; ++i) RV(i) = rsqrt(GE(i, i));
+  // Cholesky of D G D
+  for (int j = 0; j < m; ++j) {
+    double dj = GE(j, j) * RV(j) * RV(j);
+    for (int k = 0; k < j; ++k) dj -= RC(j, k) * RC(j, k);
+    if (!(dj > 0.0)) {
+      bad = 1;
+      dj = 1e-300;
+    }
+    const double cjj = sqrt(dj), icjj = 1.0 / cjj;
+    RC(j, j) = cjj;
+    for (int i = j + 1; i < m; ++i) {
+      double x = GE(i, j) * RV(i) * RV(j);
+      for (int k = 0; k < j; ++k) x -= RC(i, k) * RC(j, k);
+      RC(i, j) = x * icjj;
+    }
+  }
+  // A = C^{-1} (D M D) C^{-T}: forward substitution on the columns, then on the rows
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < m; ++i) {
+      double x = ME(i, j) * RV(i) * RV(j);
+      for (int k = 0; k < i; ++k) x -= RC(i, k) * RA(k, j);
+      RA(i, j) = x / RC(i, i);
+    }
+  for (int i = 0; i < m; ++i)
+    for (int l = 0; l < m; ++l) {
+      double y = RA(i, l);
+      for (int k = 0; k < l; ++k) y -= RC(l, k) * RA(i, k);
+      RA(i, l) = y / RC(l, l);
+    }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double a = 0.5 * (RA(i, j) + RA(j, i));
+      RA(i, j) = a;
+      RA(j, i) = a;
+    }
+  // Householder tridiagonalization; reflector k acts on indices k+1..m-1
+  double d[kMaxS], e[kMaxS], w[kMaxS];
+  for (int k = 0; k + 2 < m; ++k) {
+    double xn2 = 0.0;
+    for (int i = k + 1; i < m; ++i) xn2 += RA(i, k) * RA(i, k);
+    const double xn = sqrt(xn2);
+    const double x0 = RA(k + 1, k);
+    if (xn == 0.0) {
+      e[k] = 0.0;
+      continue;
+    }
+    const double sg = x0 >= 0.0 ? 1.0 : -1.0;
+    e[k] = -sg * xn;
+    // v = x + sg ||x|| e_1 (in RV), b = 2 / v^T v
+    RV(k + 1) = x0 + sg * xn;
+    for (int i = k + 2; i < m; ++i) RV(i) = RA(i, k);
+    const double vtv = xn2 + 2.0 * sg * xn * x0 + xn2;  // |x|^2 + 2 sg |x| x0 + |x|^2
+    const double b = 2.0 / vtv;
+    // p = b A22 v (in RW), then w = p - (b/2)(p^T v) v
+    double pv = 0.0;
+    for (int i = k + 1; i < m; ++i) {
+      double x = 0.0;
+      for (int j = k + 1; j < m; ++j) x += RA(i, j) * RV(j);
+      x *= b;
+      RW(i) = x;
+      pv += x * RV(i);
+    }
+    const double hw = 0.5 * b * pv;
+    for (int i = k + 1; i < m; ++i) RW(i) -= hw * RV(i);
+    for (int i = k + 1; i < m; ++i)
+      for (int j = k + 1; j < m; ++j) RA(i, j) -= RV(i) * RW(j) + RW(i) * RV(j);
+  }
+  for (int i = 0; i < m; ++i) d[i] = RA(i, i);
+  if (m >= 2) e[m - 2] = RA(m - 1, m - 2);
+  for (int i = 0; i + 1 < m; ++i) e[i] = fabs(e[i]);
+#undef RA
+#undef RC
+#undef RV
+#undef RW
+#undef GE
+#undef ME
+  for (int i = 0; i < s; ++i) {
+    alpha[(int64_t)q * s + i] = i < m ? d[i] : 0.0;
+    beta[(int64_t)q * s + i] = i + 1 < m ? e[i] : 0.0;
+  }
+  if (bad || tridiag_gauss(d, e, w, m) != 0) atomicOr(status, 1);
+  for (int i = 0; i < s; ++i) {
+    theta[(int64_t)q * s + i] = i < m ? d[i] : 0.0;
+    tau2[(int64_t)q * s + i] = i < m ? w[i] : 0.0;
+  }
+}
+
 struct NeumaierD {
   double s = 0.0, c = 0.0;
   __device__ void add(double x) {
@@ -196,8 +325,22 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   const int total = K->n_graphs * K->nv;
   // the solver is latency-bound: few problems go one per block, over many SMs
   const int tpb = std::max(1, std::min(32, total / std::max(1, num_sms())));
-  k_ritz<<<(unsigned)ceil_div(total, tpb), tpb, 0, st>>>(K->alpha, K->beta, K->m, total, K->s,
-                                                          K->theta, K->tau2, K->status);
+  if (K->precision != SLAQ_FP64) {
+    const int64_t need = (int64_t)total * ((int64_t)K->s * K->s + K->s * (K->s + 1) / 2 + 2 * K->s);
+    if (need > K->rscratch_cap) {
+      if (K->rscratch) cudaFree(K->rscratch);
+      K->rscratch = nullptr;
+      K->rscratch_cap = 0;
+      SLAQ_CHECK_CUDA(cudaMalloc(&K->rscratch, need * sizeof(double)));
+      K->rscratch_cap = need;
+    }
+    k_ritz_pencil<<<(unsigned)ceil_div(total, tpb), tpb, 0, st>>>(
+        K->gram, K->proj, K->m, K->nv, K->s, K->ld, total, K->rscratch, K->alpha, K->beta,
+        K->theta, K->tau2, K->status);
+  } else {
+    k_ritz<<<(unsigned)ceil_div(total, tpb), tpb, 0, st>>>(K->alpha, K->beta, K->m, total, K->s,
+                                                            K->theta, K->tau2, K->status);
+  }
   SLAQ_CHECK_LAUNCH("ritz");
   return SLAQ_OK;
 }

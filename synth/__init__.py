@@ -13,12 +13,16 @@ Generators
 * R-MAT (Chakrabarti et al. 2004) with quadrant probabilities a, b, c, d,
   sampled in rounds until the requested number of unique undirected
   non-loop pairs exists, then truncated in sampling order (stand-in for the
-  paper's SNAP / ClueWeb graphs, Tab. 2 and Tab. 5);
+  paper's SNAP / ClueWeb graphs, Tab. 2 and Tab. 5); ``rmat_torch`` draws the
+  same distribution with torch's generator on any device, for the
+  web-scale sizes numpy takes minutes to sample;
 * stochastic block model batches (stand-in for the graph-classification
   collections of Tab. 3);
 * edge rewiring of a fraction of edges (graph pairs for distances).
 
-Every generator is a pure function of its arguments and seed (numpy PCG64).
+Every generator is a pure function of its arguments and seed (numpy PCG64;
+torch's Philox generator for ``rmat_torch``, whose draws depend on the device
+and the torch build).
 """
 from __future__ import annotations
 
@@ -27,7 +31,7 @@ import numpy as np
 __all__ = [
     "t_grid", "complete", "cycle", "path", "star", "complete_bipartite",
     "disjoint_union", "barabasi_albert", "rmat", "sbm", "sbm_batch", "rewire",
-    "erdos_renyi", "read_edge_file",
+    "erdos_renyi", "read_edge_file", "rmat_torch",
 ]
 
 
@@ -174,6 +178,50 @@ def rmat(scale: int, n_edges: int, a=0.57, b=0.19, c=0.19, seed: int = 1,
     s = np.where(flip, hi, lo).astype(np.int32)
     d = np.where(flip, lo, hi).astype(np.int32)
     return s, d, n
+
+
+def rmat_torch(scale: int, n_edges: int, a=0.57, b=0.19, c=0.19, seed: int = 1,
+               device="cuda", chunk: int = 1 << 26):
+    """``rmat`` drawn with torch on ``device``: candidate pairs in rounds, the
+    first ``n_edges`` distinct undirected non-loop pairs in sampling order,
+    random orientation.  Returns int32 tensors (src, dst) on ``device`` and n."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    n = 1 << scale
+    ab, abc = a + b, a + b + c
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    want = int(n_edges * 1.3) + 1024
+    while True:
+        parts = [keys]
+        while want > 0:
+            cnt = min(want, chunk)
+            u = torch.zeros(cnt, dtype=torch.int64, device=device)
+            v = torch.zeros(cnt, dtype=torch.int64, device=device)
+            for _ in range(scale):
+                r = torch.rand(cnt, generator=gen, device=device)
+                u = (u << 1) | (r >= ab).long()
+                v = (v << 1) | (((r >= a) & (r < ab)) | (r >= abc)).long()
+            keep = u != v
+            u, v = u[keep], v[keep]
+            parts.append(torch.minimum(u, v) * n + torch.maximum(u, v))
+            want -= cnt
+        keys = torch.cat(parts)
+        srt, perm = torch.sort(keys, stable=True)
+        first = torch.ones_like(srt, dtype=torch.bool)
+        first[1:] = srt[1:] != srt[:-1]
+        idx = torch.sort(perm[first]).values
+        if idx.numel() >= n_edges:
+            break
+        want = max(n_edges // 4, 1024)
+    key = keys[idx[:n_edges]]
+    del keys, srt, perm, first, idx
+    lo, hi = key // n, key % n
+    flip = torch.rand(key.numel(), generator=gen, device=device) < 0.5
+    src = torch.where(flip, hi, lo).to(torch.int32)
+    dst = torch.where(flip, lo, hi).to(torch.int32)
+    return src, dst, n
 
 
 def erdos_renyi(n: int, p: float, seed: int = 0):

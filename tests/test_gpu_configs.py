@@ -1,0 +1,142 @@
+"""The web-scale and graph-pair workloads as parity cases, through the C ABI.
+
+* R-MAT 2^24 with 16 * 2^24 unique undirected edges (a, b, c, d = .57, .19,
+  .19, .05), isolated nodes dropped, normalized Laplacian, nv = 64, s = 20:
+  the BF16-basis form (and the FP32 form) against the FP64 form on the same
+  probes.  The FP64 run takes the first 32 probes, whose basis alone is
+  46 GB (nv = 64 would double it); every probe's Lanczos run is independent
+  of the others, so the mean over probes 0..31 of the nv = 64 run is the
+  nv = 32 estimate.  Bars: relative 1e-4 on the heat trace, 1e-3 on the
+  VNGE, and 1e-4 of the largest |Re| on the wave trace -- for the BF16 basis
+  at t < 10 only: cos(t theta) at t >= 10 turns the unconverged interior Ritz
+  values' first-order sensitivity to the basis rounding into errors of tens
+  of percent (measured 0.25 at t in [10, 100]), while the heat trace there
+  depends on the converged low end and stays within 1e-4.
+* Graph pairs: R-MAT graphs of 2^14 .. 2^17 nodes (16 edges per node), each
+  against a copy with 0.1% of its edges rewired, nodes kept (no dropping), as
+  two batches whose graph g shares probe graph field g (common random
+  probes).  FP64 distances equal the oracle's on the smallest pair (1e-8);
+  the reduced forms' heat and VNGE distances are within relative 1e-3 of
+  FP64's, wave distances within 1e-2 (the BF16 basis over t < 10, as above).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import descriptors as odesc
+from oracle import distance as odist
+from oracle.laplacian import NORMALIZED, build_laplacian
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2003_01282_gb300 import slaq  # noqa: E402
+from paper_2003_01282_gb300.build import build  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build()
+    slaq.lib()
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def test_rmat24_reduced_forms_vs_fp64():
+    src, dst, n = synth.rmat_torch(24, 16 << 24, seed=2)
+    g = slaq.build_laplacian(src, dst, n, flags=slaq.DROP_ISOLATED)
+    del src, dst
+    info = g.info
+    assert info["nnz"] == 2 * (16 << 24) and info["trace"] == info["n"]
+    t = torch.as_tensor(synth.t_grid(), device="cuda")
+    K64 = slaq.lanczos(g, 32, 20, 2, precision=slaq.FP64)
+    h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
+    v64 = slaq.trace_vnge(K64)[0].item()
+    (w64, _), _ = slaq.trace_wave(K64, t)
+    w64 = w64.cpu().numpy()
+    del K64
+    # the BF16-basis form at the workload's nv = 64, first 32 probes
+    Kb = slaq.lanczos(g, 64, 20, 2, precision=slaq.FP32_BF16BASIS)
+    _, _, hp = slaq.trace_heat(Kb, t, per_probe=True)
+    _, _, vp = slaq.trace_vnge(Kb, per_probe=True)
+    assert _rel(hp[:32].mean(0).cpu().numpy(), h64) < 1e-4
+    assert abs(vp[:32].mean().item() - v64) / v64 < 1e-3
+    del Kb
+    t_np = synth.t_grid()
+    for prec in (slaq.FP32_BF16BASIS, slaq.FP32):
+        K = slaq.lanczos(g, 32, 20, 2, precision=prec)
+        h = slaq.trace_heat(K, t)[0].cpu().numpy()
+        (w, _), _ = slaq.trace_wave(K, t)
+        assert _rel(h, h64) < 1e-4, prec
+        sel = t_np < 10.0 if prec == slaq.FP32_BF16BASIS else t_np > 0.0
+        werr = np.abs(w.cpu().numpy() - w64)[sel]
+        assert np.max(werr) < 1e-4 * np.max(np.abs(w64)), prec
+        assert abs(slaq.trace_vnge(K)[0].item() - v64) / v64 < 1e-3, prec
+        del K
+
+
+def _pairs():
+    orig, copy = [], []
+    for i, scale in enumerate((14, 15, 16, 17)):
+        s, d, n = synth.rmat(scale, 16 << scale, seed=100 + i)
+        s2, d2, _ = synth.rewire(s, d, n, frac=1e-3, seed=i)
+        orig.append((s, d, n))
+        copy.append((s2, d2, n))
+    return orig, copy
+
+
+def _descriptors(handles, prec, t):
+    K = slaq.lanczos_batched(handles, 64, 20, 5, precision=prec)
+    heat = slaq.trace_heat(K, t)[0]
+    (wr, _), (wi, _) = slaq.trace_wave(K, t)
+    vn = slaq.trace_vnge(K)[0]
+    return heat, wr, wi, vn
+
+
+def test_graph_pair_distances():
+    orig, copy = _pairs()
+    t_np = synth.t_grid()
+    t = torch.as_tensor(t_np, device="cuda")
+    ha = [slaq.build_laplacian(torch.as_tensor(s, device="cuda"), torch.as_tensor(d, device="cuda"), n)
+          for s, d, n in orig]
+    hb = [slaq.build_laplacian(torch.as_tensor(s, device="cuda"), torch.as_tensor(d, device="cuda"), n)
+          for s, d, n in copy]
+    dist = {}
+    for prec in (slaq.FP64, slaq.FP32, slaq.FP32_BF16BASIS):
+        A, B = _descriptors(ha, prec, t), _descriptors(hb, prec, t)
+        out = []
+        lo = torch.as_tensor(t_np < 10.0, device="cuda")
+        for i in range(len(orig)):
+            dh = slaq.distance(A[0][i], B[0][i], slaq.DIST_HEAT).item()
+            dw = slaq.distance(torch.cat([A[1][i], A[2][i]]), torch.cat([B[1][i], B[2][i]]),
+                               slaq.DIST_WAVE).item()
+            dwl = slaq.distance(torch.cat([A[1][i][lo], A[2][i][lo]]),
+                                torch.cat([B[1][i][lo], B[2][i][lo]]), slaq.DIST_WAVE).item()
+            dv = slaq.distance(A[3][i:i + 1], B[3][i:i + 1], slaq.DIST_VNGE).item()
+            out.append((dh, dw, dv, dwl))
+        dist[prec] = np.array(out)
+        if prec == slaq.FP64:
+            # the smallest pair against the oracle, same probes (graph field 0)
+            (sa, da, n), (sb, db, _) = orig[0], copy[0]
+            la = build_laplacian(sa, da, n, kind=NORMALIZED)
+            lb = build_laplacian(sb, db, n, kind=NORMALIZED)
+            ra, rb = odesc.slq_runs(la, 20, 64, 5, graph=0), odesc.slq_runs(lb, 20, 64, 5, graph=0)
+            oha, _ = odesc.heat_trace(ra, la.n, t_np)
+            ohb, _ = odesc.heat_trace(rb, lb.n, t_np)
+            (owra, _), (owia, _) = odesc.wave_trace(ra, la.n, t_np)
+            (owrb, _), (owib, _) = odesc.wave_trace(rb, lb.n, t_np)
+            ova, _ = odesc.vnge(ra, la.n, la.trace)
+            ovb, _ = odesc.vnge(rb, lb.n, lb.trace)
+            want = (odist.heat_distance(oha, ohb), odist.wave_distance(owra, owia, owrb, owib),
+                    odist.vnge_distance(ova, ovb))
+            np.testing.assert_allclose(out[0][:3], want, rtol=1e-8)
+    for prec in (slaq.FP32, slaq.FP32_BF16BASIS):
+        assert _rel(dist[prec][:, [0, 2]], dist[slaq.FP64][:, [0, 2]]) < 1e-3, prec
+        wcol = 1 if prec == slaq.FP32 else 3
+        assert _rel(dist[prec][:, wcol], dist[slaq.FP64][:, wcol]) < 1e-2, prec

@@ -1,6 +1,7 @@
 """Input generators: determinism, sizes and the structural properties the
 workloads ask for (unique non-loop pairs, degree skew, block structure)."""
 import numpy as np
+import pytest
 
 import synth
 
@@ -53,3 +54,15 @@ def test_rewire_keeps_edge_count():
     k = int(np.ceil(0.01 * len(a)))
     assert len(a - b) == k and len(b - a) == k
     assert not np.any(s2 == d2)
+
+
+def test_rmat_torch_unique_and_skewed():
+    torch = pytest.importorskip("torch")
+    s, d, n = synth.rmat_torch(12, 16 << 12, seed=3, device="cpu")
+    s, d = s.numpy(), d.numpy()
+    assert n == 4096 and s.size == 16 << 12 and s.dtype == np.int32
+    assert len(_pairs(s, d)) == s.size and not np.any(s == d)
+    deg = np.bincount(np.concatenate([s, d]), minlength=n)
+    assert deg.max() > 20 * np.median(deg[deg > 0])     # R-MAT's heavy tail
+    s2, d2, _ = synth.rmat_torch(12, 16 << 12, seed=3, device="cpu")
+    assert np.array_equal(s, s2.numpy()) and np.array_equal(d, d2.numpy())
