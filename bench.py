@@ -279,6 +279,23 @@ def run_batched(args, dev, world=1, rank=0):
             "speedup_over_per_graph": (SBM_GRAPHS / ms) / (len(sub) / ms_sub)}
 
 
+def rel_errors(a, b, t_np):
+    """Error of descriptors a against the FP64 run b (both [heat | wave re |
+    wave im | vnge]): heat relative per t, wave relative to its largest
+    magnitude (over all t and over t < 10), VNGE relative."""
+    lo = t_np < 10.0
+    h, h64 = a[:NT], b[:NT]
+    wr, wr64 = a[NT:2 * NT], b[NT:2 * NT]
+    wi, wi64 = a[2 * NT:3 * NT], b[2 * NT:3 * NT]
+    return {
+        "heat_max": float(np.max(np.abs(h - h64) / np.abs(h64))),
+        "wave_re_max": float(np.max(np.abs(wr - wr64)) / np.max(np.abs(wr64))),
+        "wave_im_max": float(np.max(np.abs(wi - wi64)) / np.max(np.abs(wi64))),
+        "wave_re_max_t_lt_10": float(np.max(np.abs(wr - wr64)[lo]) / np.max(np.abs(wr64))),
+        "vnge": float(abs(a[-1] - b[-1]) / abs(b[-1])),
+    }
+
+
 def kernel_capture(args):
     """Profiling driver: build the workload's graph (R-MAT 2^20, or the SBM
     batch with --capture-batched) and run Lanczos `--kernel-capture` times
@@ -441,16 +458,23 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms64 = e0.elapsed_time(e1) / 2
-        a, b = desc.double().cpu().numpy(), d64.cpu().numpy()
-        h, h64 = a[:NT], b[:NT]
+        b = d64.cpu().numpy()
         result["fp64_form"] = {"ms_per_step": ms64, "value": world * pe_step / (ms64 * 1e-3),
                                "speedup_of_headline": ms64 / ms}
-        result["rel_err_vs_fp64"] = {
-            "heat_max": float(np.max(np.abs(h - h64) / np.abs(h64))),
-            "wave_re_max": float(np.max(np.abs(a[NT:2 * NT] - b[NT:2 * NT])) / np.max(np.abs(b[NT:2 * NT]))),
-            "wave_im_max": float(np.max(np.abs(a[2 * NT:3 * NT] - b[2 * NT:3 * NT])) / np.max(np.abs(b[2 * NT:3 * NT]))),
-            "vnge": float(abs(a[-1] - b[-1]) / abs(b[-1])),
-        }
+        result["rel_err_vs_fp64"] = rel_errors(desc.double().cpu().numpy(), b, t_np)
+        # the BF16-basis form of the same step, against the same FP64 run
+        if prec != "bf16":
+            step(slaq.FP32_BF16BASIS, "Kbf")
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(2):
+                dbf, _, _ = step(slaq.FP32_BF16BASIS, "Kbf")
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            msbf = e0.elapsed_time(e1) / 2
+            result["bf16_form"] = {"ms_per_step": msbf, "value": world * pe_step / (msbf * 1e-3),
+                                   "speedup_over_fp64_form": ms64 / msbf,
+                                   "rel_err_vs_fp64": rel_errors(dbf.cpu().numpy(), b, t_np)}
 
     # end to end through the host-memory entry point (pinned buffers)
     if not args.quick:

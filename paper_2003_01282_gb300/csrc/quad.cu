@@ -161,6 +161,144 @@ __global__ void k_ritz_pencil(const double *__restrict__ gram_all,
   }
 }
 
+// The same Rayleigh-Ritz step with one warp per problem, for runs with few
+// problems (one graph): the lanes share the dense work (Cholesky, the two
+// triangular solves, the Householder products and rank-2 updates) in shared
+// memory, and lane 0 runs the tridiagonal Gauss rule.
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+inline size_t ritz_warp_smem(int s) { return ((size_t)2 * s * s + 3 * s) * sizeof(double); }
+
+__global__ void __launch_bounds__(32)
+    k_ritz_pencil_warp(const double *__restrict__ gram_all, const double *__restrict__ proj_all,
+                       const int32_t *__restrict__ mm, int nv, int s, int ld,
+                       double *__restrict__ alpha, double *__restrict__ beta,
+                       double *__restrict__ theta, double *__restrict__ tau2, int32_t *status) {
+  extern __shared__ double rw_smem[];
+  double *A = rw_smem;           // [s][s]
+  double *C = A + s * s;         // [s][s], lower triangle
+  double *V = C + s * s;         // [s] Householder vector
+  double *W = V + s;             // [s]
+  double *D = W + s;             // [s] unit-diagonal scaling
+  const int q = blockIdx.x, lane = threadIdx.x;
+  const int gr = q / nv, pp = q - gr * nv;
+  const double *Gm = gram_all + (int64_t)gr * s * s * ld;
+  const double *Mm = proj_all + (int64_t)gr * s * s * ld;
+  const int m = mm[q];
+  for (int i = lane; i < m; i += 32) D[i] = rsqrt(Gm[((int64_t)i * s + i) * ld + pp]);
+  __syncwarp();
+  for (int e = lane; e < m * m; e += 32) {
+    const int i = e / m, j = e - i * m;
+    const double sij = D[i] * D[j];
+    A[i * s + j] = Mm[((int64_t)i * s + j) * ld + pp] * sij;
+    if (j <= i) C[i * s + j] = Gm[((int64_t)i * s + j) * ld + pp] * sij;
+  }
+  __syncwarp();
+  int bad = 0;
+  for (int j = 0; j < m; ++j) {  // right-looking Cholesky
+    const double cjj = C[j * s + j];
+    if (!(cjj > 0.0)) bad = 1;
+    const double r = sqrt(cjj > 0.0 ? cjj : 1e-300);
+    __syncwarp();
+    if (lane == 0) C[j * s + j] = r;
+    for (int i = j + 1 + lane; i < m; i += 32) C[i * s + j] /= r;
+    __syncwarp();
+    const int rem = m - j - 1;
+    for (int e = lane; e < rem * rem; e += 32) {
+      const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+      if (k <= i) C[i * s + k] -= C[i * s + j] * C[k * s + j];
+    }
+    __syncwarp();
+  }
+  for (int i = 0; i < m; ++i) {  // A := C^{-1} A, row by row
+    const double cii = C[i * s + i];
+    for (int j = lane; j < m; j += 32) A[i * s + j] /= cii;
+    __syncwarp();
+    const int rem = m - i - 1;
+    for (int e = lane; e < rem * m; e += 32) {
+      const int r = i + 1 + e / m, j = e % m;
+      A[r * s + j] -= C[r * s + i] * A[i * s + j];
+    }
+    __syncwarp();
+  }
+  for (int l = 0; l < m; ++l) {  // A := A C^{-T}, column by column
+    const double cll = C[l * s + l];
+    for (int i = lane; i < m; i += 32) A[i * s + l] /= cll;
+    __syncwarp();
+    const int rem = m - l - 1;
+    for (int e = lane; e < rem * m; e += 32) {
+      const int i = e / rem, r = l + 1 + e % rem;
+      A[i * s + r] -= C[r * s + l] * A[i * s + l];
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < m * m; e += 32) {  // symmetrize
+    const int i = e / m, j = e - i * m;
+    if (j < i) {
+      const double a = 0.5 * (A[i * s + j] + A[j * s + i]);
+      A[i * s + j] = a;
+      A[j * s + i] = a;
+    }
+  }
+  __syncwarp();
+  // Householder reduction; e_k goes to C[k] (row 0 of C, free after the solves)
+  for (int k = 0; k + 2 < m; ++k) {
+    double part = 0.0;
+    for (int i = k + 1 + lane; i < m; i += 32) part += A[i * s + k] * A[i * s + k];
+    const double xn2 = warp_sum(part);
+    const double xn = sqrt(xn2);
+    const double x0 = A[(k + 1) * s + k];
+    __syncwarp();
+    if (xn == 0.0) {
+      if (lane == 0) C[k] = 0.0;
+      __syncwarp();
+      continue;
+    }
+    const double sg = x0 >= 0.0 ? 1.0 : -1.0;
+    if (lane == 0) C[k] = -sg * xn;
+    for (int i = k + 1 + lane; i < m; i += 32) V[i] = (i == k + 1) ? x0 + sg * xn : A[i * s + k];
+    __syncwarp();
+    const double b = 2.0 / (2.0 * xn2 + 2.0 * sg * xn * x0);
+    double pv_part = 0.0;
+    for (int i = k + 1 + lane; i < m; i += 32) {
+      double x = 0.0;
+      for (int j = k + 1; j < m; ++j) x += A[i * s + j] * V[j];
+      x *= b;
+      W[i] = x;
+      pv_part += x * V[i];
+    }
+    const double hw = 0.5 * b * warp_sum(pv_part);
+    __syncwarp();
+    for (int i = k + 1 + lane; i < m; i += 32) W[i] -= hw * V[i];
+    __syncwarp();
+    const int rem = m - k - 1;
+    for (int e = lane; e < rem * rem; e += 32) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      A[i * s + j] -= V[i] * W[j] + W[i] * V[j];
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    double d[kMaxS], e[kMaxS], w[kMaxS];
+    for (int i = 0; i < m; ++i) d[i] = A[i * s + i];
+    for (int i = 0; i + 2 < m; ++i) e[i] = fabs(C[i]);
+    if (m >= 2) e[m - 2] = fabs(A[(m - 1) * s + (m - 2)]);
+    for (int i = 0; i < s; ++i) {
+      alpha[(int64_t)q * s + i] = i < m ? d[i] : 0.0;
+      beta[(int64_t)q * s + i] = i + 1 < m ? e[i] : 0.0;
+    }
+    if (bad || tridiag_gauss(d, e, w, m) != 0) atomicOr(status, 1);
+    for (int i = 0; i < s; ++i) {
+      theta[(int64_t)q * s + i] = i < m ? d[i] : 0.0;
+      tau2[(int64_t)q * s + i] = i < m ? w[i] : 0.0;
+    }
+  }
+}
+
 struct NeumaierD {
   double s = 0.0, c = 0.0;
   __device__ void add(double x) {
@@ -325,7 +463,18 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   const int total = K->n_graphs * K->nv;
   // the solver is latency-bound: few problems go one per block, over many SMs
   const int tpb = std::max(1, std::min(32, total / std::max(1, num_sms())));
-  if (K->precision != SLAQ_FP64) {
+  if (K->precision != SLAQ_FP64 && total < 4096) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_ritz_pencil_warp,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ritz_warp_smem(kMaxS)));
+      attr_set = true;
+    }
+    k_ritz_pencil_warp<<<(unsigned)total, 32, ritz_warp_smem(K->s), st>>>(
+        K->gram, K->proj, K->m, K->nv, K->s, K->ld, K->alpha, K->beta, K->theta, K->tau2,
+        K->status);
+  } else if (K->precision != SLAQ_FP64) {
     const int64_t need = (int64_t)total * ((int64_t)K->s * K->s + K->s * (K->s + 1) / 2 + 2 * K->s);
     if (need > K->rscratch_cap) {
       if (K->rscratch) cudaFree(K->rscratch);
