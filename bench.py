@@ -199,13 +199,33 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ our arm
+# DRAM traffic of one SpMM (k_spmm_light + k_spmm_heavy, step 16) of the FP32
+# R-MAT 2^20 workload, from the ncu capture summarised in
+# profiles/kernels_rmat20_fp32_k16.md; it describes the kernels only while
+# csrc/lanczos.cu is byte-identical to the source that was captured.
+SPMM_TRAFFIC = {
+    "bytes_per_spmm": 1739706000 + 236616192 + 573578000 + 8204032,
+    "source_sha256": "4b80d55696acc78c4ffe085c1a00017c92b5ee80dc679103384b86e76715c35c",
+}
+
+
+def spmm_traffic(prec):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2003_01282_gb300", "csrc", "lanczos.cu")
+    with open(src, "rb") as f:
+        same = hashlib.sha256(f.read()).hexdigest() == SPMM_TRAFFIC["source_sha256"]
+    return SPMM_TRAFFIC["bytes_per_spmm"] if (same and prec == "fp32") else None
+
+
 def algorithmic_bytes(n, nnz, prec, nv=NV, s=S):
     """Algorithmic bytes of one run, per kernel class (useful nv columns)."""
     bq = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
     bw = 8 if prec == "fp64" else 4
     vec = n * nv
     spmm = s * (8 * (n + 1) + 4 * nnz + vec * (bq + bw) + n * 2 * bw)
-    dots = sum(((k + 1 if k < s - 1 else 1) * bq + bw) * vec for k in range(s))
+    # the FP64 form reads only u_{s-1} on the last step; the reduced forms
+    # read the whole basis there (the last column of the projected matrix)
+    dots = sum(((k + 1 if (k < s - 1 or prec != "fp64") else 1) * bq + bw) * vec for k in range(s))
     update = sum(((k + 1) * bq + bw + bq) * vec for k in range(s - 1))
     return {"spmm": spmm, "dots": dots, "update": update}
 
@@ -424,7 +444,13 @@ def run_ours(args):
         kernels[name] = entry
     dom = max(("spmm", "dots", "update"), key=lambda k: prof[k][0])
     dom_ms, dom_launch = prof[dom]
-    achieved = alg[dom] * args.steps / (dom_ms * 1e-3) / 1e9
+    # unit of work: one SpMM (light and split-row kernels, overlapped), one
+    # dots pass or one update pass; S, S and S - 1 of them per Lanczos run
+    units = {"spmm": S, "dots": S, "update": S - 1}[dom]
+    unit_ms = dom_ms / (args.steps * units)
+    unit_bytes = alg[dom] / units
+    achieved = unit_bytes / (unit_ms * 1e-3) / 1e9
+    traffic = spmm_traffic(prec) if dom == "spmm" else None
     launches = sum(v[1] for v in prof.values())
 
     result = {
@@ -439,8 +465,11 @@ def run_ours(args):
                        src.numel() * 8 / 1e6)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None,
-                     "algorithmic_bytes_per_launch": alg[dom] / max(1, dom_launch / args.steps)},
+                     "traffic": traffic,
+                     "unit_of_work": {"spmm": "one SpMM z = L u_k (light-row and split-row kernels)",
+                                      "dots": "one dots pass", "update": "one update pass"}[dom],
+                     "algorithmic_bytes_per_unit": unit_bytes, "ms_per_unit": unit_ms,
+                     "launches_per_unit": dom_launch / (args.steps * units)},
         "kernels": kernels,
         "gpu_launches": int(launches),
         "clocks": clocks.summary(tw0, tw1),
