@@ -145,7 +145,8 @@ struct slaq_tuning {
                            // (0: 256 for the BF16 basis, whose threads hold half the rows
                            // in flight, else 128)
   int slice_bytes = 0;     // bytes of a basis row per probe slice (0: whole rows)
-  int spmm_align = 1;      // 1: SpMM row teams never straddle two warps
+  int spmm_align = -1;     // 1: SpMM row teams never straddle two warps, 0: packed
+                           // (-1: packed for the BF16 basis, aligned otherwise; measured)
 };
 
 struct slaq_krylov_s {

@@ -296,7 +296,7 @@ __device__ __forceinline__ void finish_row(int64_t row, const typename Form<P>::
 // bound by L1 wavefronts.  Blocks run slice-major, so one slice of u_k is
 // gathered at a time.
 template <int P, int MODE>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, P == SLAQ_FP32 ? 4 : 1)  // FP32: 32 registers, full occupancy
     k_spmm_light(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                  const typename Form<P>::TW *__restrict__ vals,
                  const typename Form<P>::TW *__restrict__ diag,
@@ -387,6 +387,75 @@ __global__ void __launch_bounds__(256)
     finish_row<P, MODE>(row, diag, scale, Ul, stride, acc, Z + off + row * stride);
   }
   if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch
+}
+
+// Split rows with rows of at most 32 active threads (Vt <= 32): one chunk
+// per warp, kHeavyWarps chunks per block, so that more than one warp per
+// block is resident (a 32-thread block per chunk caps the SM at 32 warps).
+// The last warp to finish a row's slice sums the chunk partials in chunk
+// order, as in k_spmm_heavy.
+constexpr int kHeavyWarps = 4;
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(32 * kHeavyWarps)
+    k_spmm_heavy_warps(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                       const typename Form<P>::TW *__restrict__ vals,
+                       const typename Form<P>::TW *__restrict__ diag,
+                       const typename Form<P>::TW *__restrict__ scale,
+                       const typename Form<P>::TB *__restrict__ U,
+                       typename Form<P>::TW *__restrict__ Z, typename Form<P>::TW *__restrict__ part,
+                       const int32_t *__restrict__ heavy_row,
+                       const int64_t *__restrict__ heavy_first,
+                       const int32_t *__restrict__ chunk_slot, uint32_t *__restrict__ heavy_count,
+                       Slc S, int Vt, int64_t n_chunks) {
+  using TW = typename Form<P>::TW;
+  constexpr int VE = Form<P>::VE;
+  const int64_t bpc = (n_chunks + kHeavyWarps - 1) / kHeavyWarps;  // blocks per slice
+  const int sl = (int)(blockIdx.x / bpc);
+  const int64_t q = (blockIdx.x - (int64_t)sl * bpc) * kHeavyWarps + (threadIdx.x >> 5);
+  if (q >= n_chunks) return;  // whole warp; no block barrier below
+  const int lane = threadIdx.x & 31;
+  const int slot = chunk_slot[q];
+  const int64_t row = heavy_row[slot];
+  const int64_t first = heavy_first[slot];
+  const int64_t nch = heavy_first[slot + 1] - first;
+  const int64_t c = q - first;
+  const int64_t rb = rowptr[row], re = rowptr[row + 1];
+  const int64_t b = rb + c * kHeavyChunk;
+  const int64_t e = min(b + (int64_t)kHeavyChunk, re);
+  const int cc0 = sl * S.w + lane * VE;
+  const bool active = lane < Vt && cc0 < S.ld;
+  int stride = 1;
+  const int64_t off = active ? S.base(cc0, stride) : 0;
+  const auto *Ul = U + off;
+  if (active) {
+    TW acc[VE];
+#pragma unroll
+    for (int v = 0; v < VE; ++v) acc[v] = TW(0);
+    gather_rows<P, MODE>(col, vals, scale, Ul, stride, b, e, acc);
+    stw<TW, VE>(part + q * S.ld + cc0, acc);
+  }
+  __threadfence();
+  __syncwarp();
+  uint32_t *counter = heavy_count + (int64_t)slot * S.nslices() + sl;
+  unsigned prev = 0;
+  if (lane == 0) prev = atomicAdd(counter, 1u);
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev != (unsigned)(nch - 1)) return;
+  __threadfence();
+  if (active) {
+    TW acc[VE];
+#pragma unroll
+    for (int v = 0; v < VE; ++v) acc[v] = TW(0);
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      TW x[VE];
+      ldw_cg<TW, VE>(part + (first + ch) * S.ld + cc0, x);
+#pragma unroll
+      for (int v = 0; v < VE; ++v) acc[v] += x[v];
+    }
+    finish_row<P, MODE>(row, diag, scale, Ul, stride, acc, Z + off + row * stride);
+  }
+  if (lane == 0) *counter = 0u;  // ready for the next launch
 }
 
 // ------------------------------------------------------ compensated sums
@@ -1023,7 +1092,8 @@ Geometry geometry(int precision, int ld, int64_t n, int sms, const slaq_tuning &
   g.S.w = slice_width(precision, ld, t.slice_bytes);
   g.Vt = g.S.w / vec_elems(precision);
   g.Tw = g.Vt;
-  if (t.spmm_align) {
+  const bool align = t.spmm_align < 0 ? precision != SLAQ_FP32_BF16BASIS : t.spmm_align != 0;
+  if (align) {
     g.Tw = 1;
     while (g.Tw < g.Vt && g.Tw < 32) g.Tw *= 2;
     if (g.Vt > 32) g.Tw = (g.Vt + 31) / 32 * 32;
@@ -1114,8 +1184,14 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
   const unsigned blocks = (unsigned)(ns * bps);
   const unsigned hblocks = (unsigned)(ns * gr->n_chunks);
   const int hthreads = (int)ceil_div(geo.Vt, 32) * 32;
+  const unsigned hwblocks = (unsigned)(ns * ceil_div(gr->n_chunks, (int64_t)kHeavyWarps));
 #define SLAQ_SPMM_CASE(MODE)                                                                    \
-  if (gr->n_chunks > 0) {                                                                       \
+  if (gr->n_chunks > 0 && hthreads == 32) {                                                     \
+    ++tl_launches;                                                                              \
+    k_spmm_heavy_warps<P, MODE><<<hwblocks, 32 * kHeavyWarps, 0, K->side>>>(                    \
+        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, static_cast<TW *>(K->P),          \
+        gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, geo.S, geo.Vt, gr->n_chunks); \
+  } else if (gr->n_chunks > 0) {                                                                \
     ++tl_launches;                                                                              \
     k_spmm_heavy<P, MODE><<<hblocks, hthreads, 0, K->side>>>(                                   \
         gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, static_cast<TW *>(K->P),          \

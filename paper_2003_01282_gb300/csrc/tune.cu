@@ -113,7 +113,7 @@ int autotune(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int preci
     std::vector<int> values;
   };
   std::vector<Knob> knobs = {
-      {&slaq_tuning::spmm_align, {1, 0}},
+      {&slaq_tuning::spmm_align, {-1, 1, 0}},
       {&slaq_tuning::spmm_threads, {128, 256, 512}},
       {&slaq_tuning::dots_threads, {0, 64, 128, 256}},
       {&slaq_tuning::upd_threads, {128, 256, 512}},
