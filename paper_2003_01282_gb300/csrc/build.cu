@@ -3,7 +3,9 @@
 //
 // Pipeline, all on the device:
 //   1. validate ids; emit both orientations of every non-loop edge as 64-bit
-//      keys (row << cb | col), with the weight as payload;
+//      keys (row << cs | col), with the weight as payload; in a batch the
+//      column field holds the graph-local id (its graph follows from the
+//      row), which saves sort bits;
 //   2. stable LSD radix sort of the keys (8-bit digits, reduce-then-scan,
 //      tiles reordered by digit in shared memory before the scatter);
 //   3. merge duplicates (largest weight kept), rowptr from the sorted rows;
@@ -402,18 +404,21 @@ __global__ void k_node_graph(const int64_t *old_id, const double *deg, int64_t n
 
 // Both orientations of every non-loop edge; slots taken with one atomic per
 // warp, so the emission order is arbitrary (the sort removes it).
-__global__ void k_emit(const int32_t *src, const int32_t *dst, const double *w, int64_t m, int cb,
-                       uint64_t *keys, double *pay, unsigned long long *counter) {
+__global__ void k_emit(const int32_t *src, const int32_t *dst, const int32_t *csrc,
+                       const int32_t *cdst, const double *w, int64_t m, int cs, uint64_t *keys,
+                       double *pay, unsigned long long *counter) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x; e0 < m; e0 += stride) {
     const int64_t e = e0 + threadIdx.x;
     bool emit = false;
-    uint64_t a = 0, b = 0;
+    uint64_t a = 0, b = 0, ca = 0, cbv = 0;
     if (e < m) {
       a = (uint32_t)src[e];
       b = (uint32_t)dst[e];
       emit = a != b;
+      ca = (uint32_t)csrc[e];
+      cbv = (uint32_t)cdst[e];
     }
     const unsigned mask = __ballot_sync(0xffffffffu, emit);
     if (mask == 0) continue;
@@ -423,8 +428,8 @@ __global__ void k_emit(const int32_t *src, const int32_t *dst, const double *w, 
     base = __shfl_sync(0xffffffffu, base, leader);
     if (emit) {
       const unsigned long long pos = base + 2ull * __popc(mask & ((1u << lane) - 1u));
-      keys[pos] = (a << cb) | b;
-      keys[pos + 1] = (b << cb) | a;
+      keys[pos] = (a << cs) | cbv;
+      keys[pos + 1] = (b << cs) | ca;
       if (pay) {
         pay[pos] = w[e];
         pay[pos + 1] = w[e];
@@ -434,12 +439,14 @@ __global__ void k_emit(const int32_t *src, const int32_t *dst, const double *w, 
 }
 
 // Loop-free input: edge e gives keys 2e and 2e+1.
-__global__ void k_emit_direct(const int32_t *src, const int32_t *dst, const double *w, int64_t m,
-                              int cb, uint64_t *keys, double *pay) {
+__global__ void k_emit_direct(const int32_t *src, const int32_t *dst, const int32_t *csrc,
+                              const int32_t *cdst, const double *w, int64_t m, int cs,
+                              uint64_t *keys, double *pay) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t a = (uint32_t)src[e], b = (uint32_t)dst[e];
-    reinterpret_cast<ulonglong2 *>(keys)[e] = make_ulonglong2((a << cb) | b, (b << cb) | a);
+    const uint64_t ca = (uint32_t)csrc[e], cbv = (uint32_t)cdst[e];
+    reinterpret_cast<ulonglong2 *>(keys)[e] = make_ulonglong2((a << cs) | cbv, (b << cs) | ca);
     if (pay) reinterpret_cast<double2 *>(pay)[e] = make_double2(w[e], w[e]);
   }
 }
@@ -465,12 +472,13 @@ __global__ void k_unique(const uint64_t *k, const double *pay, int64_t m, const 
   }
 }
 
-// rowptr[r] = index of the first key with row >= r (rows = key >> cb).
-__global__ void k_rowptr(const uint64_t *ukey, int64_t nnz, int cb, int64_t n, int64_t *rowptr) {
+// rowptr[r] = index of the first key with row >= r (rows = key >> shift).
+__global__ void k_rowptr(const uint64_t *ukey, int64_t nnz, int shift, int64_t n,
+                         int64_t *rowptr) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nnz;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r_prev = i == 0 ? -1 : (int64_t)(ukey[i - 1] >> cb);
-    const int64_t r_cur = i == nnz ? n : (int64_t)(ukey[i] >> cb);
+    const int64_t r_prev = i == 0 ? -1 : (int64_t)(ukey[i - 1] >> shift);
+    const int64_t r_cur = i == nnz ? n : (int64_t)(ukey[i] >> shift);
     for (int64_t r = r_prev + 1; r <= r_cur; ++r) rowptr[r] = i;
   }
 }
@@ -531,14 +539,30 @@ __global__ void k_scale(const double *deg, int64_t n, int kind, double *scale, d
 }
 
 // One thread per stored entry; its row and column come from the sorted key.
+// Batches: first union id of the graph of every input node (keys carry
+// graph-local column ids).
+__global__ void k_row_base(const int64_t *node_off, int G, int64_t n, int64_t *rowbase) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = G;  // node_off[lo] <= i < node_off[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (node_off[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    rowbase[i] = node_off[lo];
+  }
+}
+
 __global__ void k_values(const uint64_t *ukey, const double *uw, const int64_t *newid, int drop,
-                         int cb, int64_t nnz, int kind, const double *scale, int32_t *colidx,
-                         double *vals, float *vals32) {
-  const uint64_t cmask = (1ull << cb) - 1ull;
+                         int cs, const int64_t *rowbase, int64_t nnz, int kind,
+                         const double *scale, int32_t *colidx, double *vals, float *vals32) {
+  const uint64_t cmask = (1ull << cs) - 1ull;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz;
        j += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = ukey[j];
-    const int64_t r_old = (int64_t)(key >> cb), c_old = (int64_t)(key & cmask);
+    const int64_t r_old = (int64_t)(key >> cs);
+    const int64_t c_old = (rowbase ? rowbase[r_old] : 0) + (int64_t)(key & cmask);
     const int64_t r = drop ? newid[r_old] : r_old;
     const int64_t c = drop ? newid[c_old] : c_old;
     const double a = uw ? uw[j] : 1.0;
@@ -602,14 +626,14 @@ __global__ void k_perm_index(const uint64_t *key, const int64_t *rowptr, int64_t
 
 // Execution row r is canonical row perm[r]; columns are renamed through inv.
 // One thread per canonical entry (its row comes from the sorted key).
-__global__ void k_perm_entries(const uint64_t *ukey, const int64_t *newid, int drop, int cb,
+__global__ void k_perm_entries(const uint64_t *ukey, const int64_t *newid, int drop, int shift,
                                const int64_t *rowptr, const int32_t *colidx, const double *vals,
                                const float *vals32, const int64_t *inv, int64_t nnz,
                                const int64_t *xrowptr, int32_t *xcol, double *xvals,
                                float *xvals32) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r_old = (int64_t)(ukey[e] >> cb);
+    const int64_t r_old = (int64_t)(ukey[e] >> shift);
     const int64_t i = drop ? newid[r_old] : r_old;
     const int64_t x = xrowptr[inv[i]] + (e - rowptr[i]);
     xcol[x] = (int32_t)inv[colidx[e]];
@@ -772,6 +796,9 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_node_off, node_off.data(), (G + 1) * sizeof(int64_t),
                                   cudaMemcpyHostToDevice, st));
   unsigned long long n_loops = 0;
+  // keys are row << cs | column, with graph-local columns in a batch (fewer
+  // sort bits); csrc / cdst hold the ids that go into the column field
+  const int32_t *csrc = src, *cdst = dst;
   if (m > 0) {
     int32_t *bad = nullptr;
     unsigned long long *loops = nullptr;
@@ -791,7 +818,7 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
       k_union_ids<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, d_edge_off, d_node_off, G,
                                                     usrc, udst, bad, loops);
       src = usrc;
-      dst = udst;
+      dst = udst;  // csrc / cdst keep the local ids
     } else {
       ++tl_launches;
       k_validate<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, n, bad, loops);
@@ -806,6 +833,17 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
 
   // 2. emit and sort
   const int cb = bits_for(n);
+  int cs = cb;
+  int64_t *rowbase = nullptr;
+  if (batch) {
+    int64_t gmax = 1;
+    for (int g = 0; g < G; ++g) gmax = std::max(gmax, node_off[g + 1] - node_off[g]);
+    cs = bits_for(gmax);
+    SLAQ_TRY(tmp.get(&rowbase, n));
+    ++tl_launches;
+    k_row_base<<<grid_for(n, 256), 256, 0, st>>>(d_node_off, G, n, rowbase);
+    SLAQ_CHECK_LAUNCH("row_base");
+  }
   uint64_t *k0 = nullptr, *k1 = nullptr;
   double *p0 = nullptr, *p1 = nullptr;
   unsigned long long *counter = nullptr;
@@ -819,18 +857,18 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   SLAQ_CHECK_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   if (m > 0 && n_loops == 0) {
     ++tl_launches;
-    k_emit_direct<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, cb, k0, p0);
+    k_emit_direct<<<grid_for(m, 256), 256, 0, st>>>(src, dst, csrc, cdst, weights, m, cs, k0, p0);
     SLAQ_CHECK_LAUNCH("emit");
   } else if (m > 0) {
     ++tl_launches;
-    k_emit<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, cb, k0, p0, counter);
+    k_emit<<<grid_for(m, 256), 256, 0, st>>>(src, dst, csrc, cdst, weights, m, cs, k0, p0, counter);
     SLAQ_CHECK_LAUNCH("emit");
   }
   const int64_t m2 = 2 * (m - (int64_t)n_loops);
   {
     uint64_t *ka = k0, *kb = k1;
     double *pa = p0, *pb = p1;
-    SLAQ_TRY(radix_sort(&ka, &kb, weighted ? &pa : nullptr, &pb, m2, 2 * cb, st));
+    SLAQ_TRY(radix_sort(&ka, &kb, weighted ? &pa : nullptr, &pb, m2, cb + cs, st));
     k0 = ka;
     k1 = kb;
     p0 = pa;
@@ -866,7 +904,7 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   SLAQ_TRY(tmp.get(&deg_full, n));
   SLAQ_TRY(tmp.get(&keep, n));
   ++tl_launches;
-  k_rowptr<<<grid_for(nnz + 1, 256), 256, 0, st>>>(ukey, nnz, cb, n, rowptr_full);
+  k_rowptr<<<grid_for(nnz + 1, 256), 256, 0, st>>>(ukey, nnz, cs, n, rowptr_full);
   SLAQ_CHECK_LAUNCH("rowptr");
   if (n > 0) {
     ++tl_launches;
@@ -918,8 +956,8 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
                                                   g->scale32, g->diag32);
     SLAQ_CHECK_LAUNCH("scale");
     ++tl_launches;
-    k_values<<<grid_for(nnz, 256), 256, 0, st>>>(ukey, uw, newid, drop ? 1 : 0, cb, nnz, kind,
-                                                 g->scale, g->colidx, g->vals, g->vals32);
+    k_values<<<grid_for(nnz, 256), 256, 0, st>>>(ukey, uw, newid, drop ? 1 : 0, cs, rowbase, nnz,
+                                                 kind, g->scale, g->colidx, g->vals, g->vals32);
     SLAQ_CHECK_LAUNCH("values");
   }
 
@@ -1024,7 +1062,7 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
     if (nnz > 0) {
       ++tl_launches;
       k_perm_entries<<<grid_for(nnz, 256), 256, 0, st>>>(
-          ukey, newid, drop ? 1 : 0, cb, g->rowptr, g->colidx, g->vals, g->vals32, inv, nnz,
+          ukey, newid, drop ? 1 : 0, cs, g->rowptr, g->colidx, g->vals, g->vals32, inv, nnz,
           g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32);
     }
     ++tl_launches;
