@@ -146,7 +146,7 @@ struct slaq_tuning {
                            // in flight, else 128)
   int slice_bytes = 0;     // bytes of a basis row per probe slice (0: whole rows)
   int spmm_align = -1;     // 1: SpMM row teams never straddle two warps, 0: packed
-                           // (-1: packed for the BF16 basis, aligned otherwise; measured)
+                           // (-1: aligned when a row takes more than 16 threads)
 };
 
 struct slaq_krylov_s {
@@ -164,6 +164,9 @@ struct slaq_krylov_s {
   int max_chunks_per_graph = 1;
   void *U = nullptr;      // [s][n_cap][ld] basis (TB)
   void *Z = nullptr;      // [n_cap][ld] L u_k (TW)
+  float *Y = nullptr;     // [n_cap][ld] s_i u_k[i] (FP32 form, normalized unweighted)
+  bool ymode = false;     // the last run gathered Y instead of scale[j] u_k[j]
+  const float *yscale = nullptr;  // the run's s_i (execution order), for Y
   void *P = nullptr;      // [chunk_cap][ld] partial sums of split rows (TW)
   double *part = nullptr; // [G][2][s][ld] per-block partial sums (dots, Gram column)
   double *dsum = nullptr; // [s][ld] reduced dot products u_j^T z

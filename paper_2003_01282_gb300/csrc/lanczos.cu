@@ -181,7 +181,7 @@ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
 template <int P>
 __global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id,
                              const int32_t *xgraph, Slc S, int nv, uint64_t seed,
-                             uint64_t graph_id) {
+                             uint64_t graph_id, const float *yscale, float *Y0) {
   using TB = typename Form<P>::TB;
   const int64_t n = S.n;
   const int ld = S.ld;
@@ -201,6 +201,7 @@ __global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id,
       v = (z >> 63) ? -1.0f : 1.0f;
     }
     U0[off] = (TB)v;
+    if (Y0) Y0[off] = yscale[i] * v;
   }
 }
 
@@ -233,6 +234,9 @@ __global__ void k_init_scalars(double *alpha, double *beta, int32_t *m, int64_t 
 // MODE 0: normalized, unweighted   z_i = diag_i u_i - s_i sum_j s_j u_j
 // MODE 1: combinatorial, unweighted z_i = d_i u_i - sum_j u_j
 // MODE 2: weighted                  z_i = diag_i u_i + sum_j val_ij u_j
+// MODE 3: normalized, unweighted, with the gathered rows pre-scaled:
+//         z_i = diag_i u_i - s_i sum_j y_j, y_j = s_j u_j written by the kernel
+//         that produced u_k (FP32 form: saves the per-entry gather of s_j)
 template <int P, int MODE>
 __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
                                             const typename Form<P>::TW *__restrict__ vals,
@@ -280,7 +284,7 @@ __device__ __forceinline__ void finish_row(int64_t row, const typename Form<P>::
   TW y[VE];
   ldb(Ul + row * stride, y);
   const TW g = diag[row];
-  const TW sr = MODE == 0 ? scale[row] : TW(1);
+  const TW sr = (MODE == 0 || MODE == 3) ? scale[row] : TW(1);
   TW z[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v)
@@ -302,7 +306,8 @@ __global__ void __launch_bounds__(512, P == SLAQ_FP32 ? 4 : 1)  // FP32: 32 regi
                  const typename Form<P>::TW *__restrict__ diag,
                  const typename Form<P>::TW *__restrict__ scale,
                  const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
-                 Slc S, int Vt, int Tw, int R, int64_t bps, int64_t heavy_degree) {
+                 const typename Form<P>::TB *__restrict__ Yg, Slc S, int Vt, int Tw, int R,
+                 int64_t bps, int64_t heavy_degree) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   const int sl = (int)(blockIdx.x / bps);
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(512, P == SLAQ_FP32 ? 4 : 1)  // FP32: 32 regi
   TW acc[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v) acc[v] = TW(0);
-  gather_rows<P, MODE>(col, vals, scale, Ul, stride, b, e, acc);
+  gather_rows<P, MODE>(col, vals, scale, MODE == 3 ? Yg + off : Ul, stride, b, e, acc);
   finish_row<P, MODE>(row, diag, scale, Ul, stride, acc, Z + off + row * stride);
 }
 
@@ -337,7 +342,8 @@ __global__ void __launch_bounds__(256)
                  const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
                  typename Form<P>::TW *__restrict__ part, const int32_t *__restrict__ heavy_row,
                  const int64_t *__restrict__ heavy_first, const int32_t *__restrict__ chunk_slot,
-                 uint32_t *__restrict__ heavy_count, Slc S, int Vt, int64_t n_chunks) {
+                 uint32_t *__restrict__ heavy_count, const typename Form<P>::TB *__restrict__ Yg,
+                 Slc S, int Vt, int64_t n_chunks) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   __shared__ int is_last;
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(256)
     TW acc[VE];
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc[v] = TW(0);
-    gather_rows<P, MODE>(col, vals, scale, Ul, stride, b, e, acc);
+    gather_rows<P, MODE>(col, vals, scale, MODE == 3 ? Yg + off : Ul, stride, b, e, acc);
     stw<TW, VE>(part + q * S.ld + cc0, acc);
   }
   __threadfence();
@@ -407,7 +413,8 @@ __global__ void __launch_bounds__(32 * kHeavyWarps)
                        const int32_t *__restrict__ heavy_row,
                        const int64_t *__restrict__ heavy_first,
                        const int32_t *__restrict__ chunk_slot, uint32_t *__restrict__ heavy_count,
-                       Slc S, int Vt, int64_t n_chunks) {
+                       const typename Form<P>::TB *__restrict__ Yg, Slc S, int Vt,
+                       int64_t n_chunks) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   const int64_t bpc = (n_chunks + kHeavyWarps - 1) / kHeavyWarps;  // blocks per slice
@@ -432,7 +439,7 @@ __global__ void __launch_bounds__(32 * kHeavyWarps)
     TW acc[VE];
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc[v] = TW(0);
-    gather_rows<P, MODE>(col, vals, scale, Ul, stride, b, e, acc);
+    gather_rows<P, MODE>(col, vals, scale, MODE == 3 ? Yg + off : Ul, stride, b, e, acc);
     stw<TW, VE>(part + q * S.ld + cc0, acc);
   }
   __threadfence();
@@ -1006,7 +1013,8 @@ __global__ void __launch_bounds__(512)
              typename Form<P>::TB *Unext, Slc S, const int64_t *__restrict__ crow0,
              const int32_t *__restrict__ crows, const int32_t *__restrict__ cgraph, int V, int R,
              int64_t ustride, int k, int s, const double *__restrict__ coef_all,
-             const int32_t *__restrict__ m_all, int nv) {
+             const int32_t *__restrict__ m_all, int nv, const typename Form<P>::TW *__restrict__ yscale,
+             typename Form<P>::TW *Ynext) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -1059,6 +1067,12 @@ __global__ void __launch_bounds__(512)
       if (!keep[v]) x[v] = TW(0);
     TW r[VE];
     stb(Unext + o, x, r);
+    if (Ynext) {  // pre-scaled copy for the next SpMM (MODE 3)
+      const TW sc = yscale[row];
+#pragma unroll
+      for (int v = 0; v < VE; ++v) r[v] *= sc;
+      stw<TW, VE>(Ynext + o, r);
+    }
   }
 }
 
@@ -1092,7 +1106,10 @@ Geometry geometry(int precision, int ld, int64_t n, int sms, const slaq_tuning &
   g.S.w = slice_width(precision, ld, t.slice_bytes);
   g.Vt = g.S.w / vec_elems(precision);
   g.Tw = g.Vt;
-  const bool align = t.spmm_align < 0 ? precision != SLAQ_FP32_BF16BASIS : t.spmm_align != 0;
+  // measured: whole-warp teams win for wide rows (R-MAT, nv = 100 FP32: 26 of
+  // 32 lanes), packed teams for narrow ones (BF16 nv = 100: 13 lanes; SBM
+  // batches, nv = 20 FP32: 6 lanes)
+  const bool align = t.spmm_align < 0 ? g.Vt > 16 : t.spmm_align != 0;
   if (align) {
     g.Tw = 1;
     while (g.Tw < g.Vt && g.Tw < 32) g.Tw *= 2;
@@ -1178,7 +1195,10 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
     diag = gr->x_diag32;
     scale = gr->x_scale32;
   }
-  const int mode = gr->weighted ? 2 : (gr->kind == SLAQ_NORMALIZED ? 0 : 1);
+  const int mode =
+      gr->weighted ? 2 : (gr->kind == SLAQ_NORMALIZED ? (K->ymode ? 3 : 0) : 1);
+  const TB *Yg = nullptr;
+  if constexpr (P == SLAQ_FP32) Yg = K->Y;
   const int ns = geo.S.nslices();
   const int64_t bps = ceil_div(n, geo.Rt);
   const unsigned blocks = (unsigned)(ns * bps);
@@ -1190,17 +1210,19 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
     ++tl_launches;                                                                              \
     k_spmm_heavy_warps<P, MODE><<<hwblocks, 32 * kHeavyWarps, 0, K->side>>>(                    \
         gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, static_cast<TW *>(K->P),          \
-        gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, geo.S, geo.Vt, gr->n_chunks); \
+        gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, Yg, geo.S, geo.Vt,           \
+        gr->n_chunks);                                                                          \
   } else if (gr->n_chunks > 0) {                                                                \
     ++tl_launches;                                                                              \
     k_spmm_heavy<P, MODE><<<hblocks, hthreads, 0, K->side>>>(                                   \
         gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, static_cast<TW *>(K->P),          \
-        gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, geo.S, geo.Vt, gr->n_chunks); \
+        gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, Yg, geo.S, geo.Vt,           \
+        gr->n_chunks);                                                                          \
   }                                                                                             \
   ++tl_launches;                                                                                \
   k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(gr->x_rowptr, gr->x_colidx, vals, diag, \
-                                                         scale, Uk, Z, geo.S, geo.Vt, geo.Tw,   \
-                                                         geo.Rt, bps, gr->heavy_degree);
+                                                         scale, Uk, Z, Yg, geo.S, geo.Vt,       \
+                                                         geo.Tw, geo.Rt, bps, gr->heavy_degree);
   // split rows on the side stream, concurrently with the light rows (the two
   // write disjoint rows of z)
   if (gr->n_chunks > 0) {
@@ -1211,8 +1233,10 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
     SLAQ_SPMM_CASE(0)
   } else if (mode == 1) {
     SLAQ_SPMM_CASE(1)
-  } else {
+  } else if (mode == 2) {
     SLAQ_SPMM_CASE(2)
+  } else {
+    if constexpr (P == SLAQ_FP32) { SLAQ_SPMM_CASE(3) }
   }
   if (gr->n_chunks > 0) {
     SLAQ_CHECK_CUDA(cudaEventRecord(K->ev_join, K->side));
@@ -1314,17 +1338,26 @@ int update(slaq_krylov K, const Geometry &geo, int64_t n, int k, bool second, cu
   const TB *U = static_cast<const TB *>(K->U);
   TB *Unext = static_cast<TB *>(K->U) + (int64_t)(k + 1) * n * K->ld;
   const int64_t ustride = n * K->ld;
+  // the FP32 form also writes y = s * u_{k+1} for the next SpMM (MODE 3)
+  const TW *yscale = nullptr;
+  TW *Ynext = nullptr;
+  if constexpr (P == SLAQ_FP32) {
+    if (K->ymode) {
+      yscale = K->yscale;
+      Ynext = K->Y;
+    }
+  }
   const size_t smem = (size_t)(k + 1) * K->ld * sizeof(TW);
   const TW *Z = static_cast<const TW *>(K->Z);
   ++tl_launches;
   if (second)
     k_update<P, true><<<K->n_uchunks, geo.threads, smem, st>>>(
         U, Z, Unext, geo.S, K->u_row0, K->u_rows, K->u_graph, geo.V, geo.R, ustride, k, K->s,
-        K->coef, K->m, K->nv);
+        K->coef, K->m, K->nv, yscale, Ynext);
   else
     k_update<P, false><<<K->n_uchunks, geo.threads, smem, st>>>(
         U, Z, Unext, geo.S, K->u_row0, K->u_rows, K->u_graph, geo.V, geo.R, ustride, k, K->s,
-        K->coef, K->m, K->nv);
+        K->coef, K->m, K->nv, yscale, Ynext);
   SLAQ_CHECK_LAUNCH("update");
   return SLAQ_OK;
 }
@@ -1333,6 +1366,8 @@ template <int P>
 int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   using TB = typename Form<P>::TB;
   const int64_t n = gr->n;
+  K->ymode = P == SLAQ_FP32 && !gr->weighted && gr->kind == SLAQ_NORMALIZED && K->Y;
+  K->yscale = gr->x_scale32;
   const Geometry geo = geometry(P, K->ld, n, num_sms(), K->tune);
   static bool attr_set = false;
   if (!attr_set) {
@@ -1396,7 +1431,8 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
     ++tl_launches;
     k_probe_init<P><<<(unsigned)std::min<int64_t>(ceil_div(n * K->ld, 256), 152LL * 64), 256, 0,
                       st>>>(static_cast<TB *>(K->U), gr->x_old_id, gr->x_graph, geo.S, K->nv,
-                            K->seed, (uint64_t)K->graph_id);
+                            K->seed, (uint64_t)K->graph_id, K->ymode ? K->yscale : nullptr,
+                            K->ymode ? K->Y : nullptr);
   }
   SLAQ_CHECK_LAUNCH("probe_init");
   for (int k = 0; k < K->s; ++k) {
@@ -1455,7 +1491,7 @@ int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaS
 
 void krylov_free(slaq_krylov k) {
   if (!k) return;
-  void *ptrs[] = {k->U, k->Z, k->P, k->part, k->dsum, k->coef, k->gram, k->proj, k->rscratch,
+  void *ptrs[] = {k->U, k->Z, k->Y, k->P, k->part, k->dsum, k->coef, k->gram, k->proj, k->rscratch,
                   k->alpha, k->beta,
                   k->m, k->theta, k->tau2, k->status, k->hcount, k->gn, k->gtrace, k->gbound,
                   k->d_row0, k->d_rows, k->d_goff, k->u_row0, k->u_rows, k->u_graph};
@@ -1513,6 +1549,7 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   if (n > K->n_cap) {
     SLAQ_TRY(grow(reinterpret_cast<unsigned char **>(&K->U), (size_t)s * n * ld * basis_bytes(precision)));
     SLAQ_TRY(grow(reinterpret_cast<unsigned char **>(&K->Z), (size_t)n * ld * work_bytes(precision)));
+    if (precision == SLAQ_FP32) SLAQ_TRY(grow(&K->Y, (size_t)n * ld));
     K->n_cap = n;
   }
   if (g->n_chunks > K->chunk_cap || !K->P) {
