@@ -222,11 +222,15 @@ def algorithmic_bytes(n, nnz, prec, nv=NV, s=S):
     bq = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
     bw = 8 if prec == "fp64" else 4
     vec = n * nv
-    spmm = s * (8 * (n + 1) + 4 * nnz + vec * (bq + bw) + n * 2 * bw)
+    # the FP32 form gathers y = s * u (written by the update) and reads u_k
+    # for the diagonal term: one more vector read per SpMM and one more
+    # vector written per update
+    yb = bw if prec == "fp32" else 0
+    spmm = s * (8 * (n + 1) + 4 * nnz + vec * (bq + bw + yb) + n * 2 * bw)
     # the FP64 form reads only u_{s-1} on the last step; the reduced forms
     # read the whole basis there (the last column of the projected matrix)
     dots = sum(((k + 1 if (k < s - 1 or prec != "fp64") else 1) * bq + bw) * vec for k in range(s))
-    update = sum(((k + 1) * bq + bw + bq) * vec for k in range(s - 1))
+    update = sum(((k + 1) * bq + bw + bq + yb) * vec for k in range(s - 1))
     return {"spmm": spmm, "dots": dots, "update": update}
 
 
