@@ -131,7 +131,12 @@ void slaq_graph_destroy(slaq_graph g);
 /* Run s-step Lanczos (Sec. 3.1, Algorithm 1 `lanczos`) of the graph's
  * Laplacian from nv Rademacher probes at once, then the Gauss rule of every
  * probe's tridiagonal T (Eq. quadratic: nodes = eigenvalues of T, weights =
- * squared first eigenvector components).
+ * squared first eigenvector components).  SLAQ_FP64 takes T from the
+ * recurrence (alpha, beta below).  The FP32 and BF16-basis forms take the
+ * Rayleigh-Ritz matrix of their stored, rounded basis, A = C^-1 M C^-T with
+ * M = U^T L U, U^T U = C C^T, reduced to tridiagonal form by Householder
+ * reflections that fix the first unit vector: in exact arithmetic A = T,
+ * and it removes the first-order effect of the basis rounding on the rule.
  *   Probe p's entry at node i is the sign of SplitMix64 applied to
  *   seed + 0x9E3779B97F4A7C15 * (c + 1), c = graph_id<<48 | p<<32 | orig_id(i)
  *   (-1 where bit 63 is set); the starting vector is that sign vector / sqrt(n').
@@ -177,7 +182,10 @@ int slaq_lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_
 int slaq_probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, void *stream);
 
 /* Device copies of alpha float64[nv*s] (row p holds alpha_0..alpha_{m_p-1}),
- * beta float64[nv*s] (beta_0..beta_{m_p-2}) and m int32[nv].  NULL skips. */
+ * beta float64[nv*s] (beta_0..beta_{m_p-2}) and m int32[nv].  NULL skips.
+ * For the FP32 and BF16-basis forms alpha and beta are the diagonal and
+ * off-diagonal of the tridiagonal form of the Rayleigh-Ritz matrix (the T
+ * whose Gauss rule the traces use). */
 int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, void *stream);
 
 /* Device copies of the Gauss nodes theta float64[nv*s] (ascending within a

@@ -313,11 +313,13 @@ __device__ __forceinline__ void finish_row(int64_t row, const typename Form<P>::
 
 // Probe slice sl = blockIdx.x / bps, rows (blockIdx.x % bps) * R + team:
 // a team of Tw threads per row, Vt = w / VE of them active, each owning VE
-// probe columns.  Tw is Vt rounded up to a power of two (or to whole warps),
-// so a row is never split between two warps: a split row costs an extra L1
-// wavefront for the 128-byte line both warps touch, and the gathers are
-// bound by L1 wavefronts.  Blocks run slice-major, so one slice of u_k is
-// gathered at a time.
+// probe columns.  Tw is Vt, or Vt rounded up to a power of two (whole warps
+// above 32) so that no row is split between two warps, which saves the extra
+// L1 wavefront of the 128-byte line both warps would touch; the host picks
+// by row width (measured).  Blocks run slice-major, so one slice of u_k is
+// gathered at a time.  The FP32 form runs at 32 registers per thread: full
+// occupancy keeps more gathers in flight, and the kernel is bound by gather
+// latency (no memory unit near its peak, long-scoreboard stalls dominate).
 template <int P, int MODE>
 __global__ void __launch_bounds__(512, P == SLAQ_FP32 ? 4 : 1)  // FP32: 32 registers, full occupancy
     k_spmm_light(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
@@ -826,7 +828,7 @@ __global__ void k_dot_reduce_narrow(const double *__restrict__ part, const int32
 }
 
 // ---------------------------------------------------------------- solve
-// One block per probe (lane 0 computes).  With G the Gram matrix of the
+// One warp per (graph, probe) problem.  With G the Gram matrix of the
 // stored basis u_0..u_k and d_j = u_j^T z, the coefficients of the projection
 // of z on span(u_0..u_k) are x = G^{-1} d (Cholesky of the unit-diagonal
 // scaling of G).  With an exactly orthogonal basis x_j = d_j / ||u_j||^2,

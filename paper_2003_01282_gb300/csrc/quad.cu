@@ -1,7 +1,9 @@
 // Gauss rule per probe and the Hutchinson estimate of Eq. slq for the heat
 // trace (Eq. heat-trace), the wave trace and the VNGE (Definition 1,
 // Sec. 2.1); spectral distances between descriptors (Sec. 4.2).
-// All FP64.  Probe sums run in probe order, so results are deterministic.
+// Eigensolves and sums are FP64; the FP32 and BF16 forms evaluate exp, cos
+// and sin in FP32 (see fval).  Probe sums run in a fixed order, so results
+// are deterministic.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
