@@ -100,7 +100,9 @@ int slaq_build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges
  * edges.  kind and flags as for slaq_build_laplacian, applied per graph.
  * 1 <= G <= 65536; offsets are host arrays of G+1 entries starting at 0.
  * Graph g's results match a single-graph run of graph g with graph_id
- * (of slaq_lanczos) increased by g.  Synchronizes `stream`. */
+ * (of slaq_lanczos) increased by g.  A graph that keeps no nodes (all
+ * isolated and dropped) stays in the batch with an empty Krylov space:
+ * m = 0, zero traces, zero entropy.  Synchronizes `stream`. */
 int slaq_build_laplacian_batch(const int32_t *src, const int32_t *dst,
                                const int64_t *edge_off_host, const int64_t *node_off_host,
                                int n_graphs, const double *weights, int kind, int flags,

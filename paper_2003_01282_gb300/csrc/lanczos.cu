@@ -218,8 +218,11 @@ __global__ void k_probe_export(double *out, const int64_t *old_id, int64_t n, in
   }
 }
 
+// m = s for every (graph, probe), except m = 0 for a graph of a batch that
+// kept no nodes (all isolated and dropped): its Krylov space is empty, and
+// its traces and entropy come out 0.
 __global__ void k_init_scalars(double *alpha, double *beta, int32_t *m, int64_t nvs, int64_t nvt,
-                               int s) {
+                               int s, int nv, const double *gn) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvs;
        i += (int64_t)gridDim.x * blockDim.x) {
     alpha[i] = 0.0;
@@ -227,7 +230,7 @@ __global__ void k_init_scalars(double *alpha, double *beta, int32_t *m, int64_t 
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvt;
        i += (int64_t)gridDim.x * blockDim.x)
-    m[i] = s;
+    m[i] = gn[i / nv] > 0.0 ? s : 0;
 }
 
 // ------------------------------------------------------------------ SpMM
@@ -1448,7 +1451,7 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
     const int64_t nvt = (int64_t)K->n_graphs * K->nv;
     ++tl_launches;
     k_init_scalars<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nvt * K->s, 256), 1024)),
-                     256, 0, st>>>(K->alpha, K->beta, K->m, nvt * K->s, nvt, K->s);
+                     256, 0, st>>>(K->alpha, K->beta, K->m, nvt * K->s, nvt, K->s, K->nv, K->gn);
     ++tl_launches;
     k_probe_init<P><<<(unsigned)std::min<int64_t>(ceil_div(n * K->ld, 256), 152LL * 64), 256, 0,
                       st>>>(static_cast<TB *>(K->U), gr->x_old_id, gr->x_graph, geo.S, K->nv,

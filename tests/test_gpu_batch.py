@@ -242,3 +242,30 @@ def test_lanczos_batched_rejects_mixed_kinds():
     assert ei.value.status == 1
     with pytest.raises(slaq.SlaqError):
         slaq.lanczos_batched([], 4, 5, 1)
+
+
+@pytest.mark.parametrize("prec", [slaq.FP64, slaq.FP32])
+def test_batch_graph_with_no_kept_nodes(prec):
+    """A graph of a batch whose nodes are all isolated and dropped has an empty
+    Krylov space: m = 0, zero traces and zero entropy, and the other graphs
+    are unaffected."""
+    empty = (np.zeros(0, np.int32), np.zeros(0, np.int32), 3)
+    graphs = [synth.path(5), empty, synth.cycle(4)]
+    nv, s, seed = 4, 6, 8
+    gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
+    info = slaq.graph_batch_info(gb)
+    assert list(np.diff(info["node_off"])) == [5, 0, 4]
+    K = slaq.lanczos(gb, nv, s, seed, precision=prec)
+    m = slaq.krylov_export(K)[2].cpu().numpy()
+    assert np.all(m[1] == 0) and np.all(m[0] > 0) and np.all(m[2] > 0)
+    t = _dev(synth.t_grid(32), torch.float64)
+    heat = slaq.trace_heat(K, t)[0].cpu().numpy()
+    vnge = slaq.trace_vnge(K)[0].cpu().numpy()
+    (wr, _), _ = slaq.trace_wave(K, t)
+    assert np.all(heat[1] == 0.0) and vnge[1] == 0.0 and np.all(wr[1].cpu().numpy() == 0.0)
+    for g in (0, 2):
+        src, dst, n = graphs[g]
+        gs = slaq.build_laplacian(_dev(src, torch.int32), _dev(dst, torch.int32), n,
+                                  flags=slaq.DROP_ISOLATED)
+        hs = slaq.trace_heat(slaq.lanczos(gs, nv, s, seed, graph_id=g, precision=prec), t)[0]
+        np.testing.assert_allclose(heat[g], hs.cpu().numpy(), rtol=1e-12 if prec == slaq.FP64 else 1e-5)
