@@ -145,9 +145,12 @@ void slaq_graph_destroy(slaq_graph g);
  *   Every step orthogonalizes the new vector against all previous Lanczos
  *   vectors of its probe by classical Gram-Schmidt (reorth_passes = 1) or
  *   twice (2).  A probe whose beta_k falls to tol * bound (tol 1e-10 FP64,
- *   1e-4 FP32, 3e-2 BF16 basis; bound 2 or 2 max d) stops with m = k+1.
+ *   1e-4 FP32 and BF16 basis; bound 2 or 2 max d) stops with m = k+1.
  *   1 <= nv <= 512, 1 <= s <= 64, precision one of SLAQ_FP64/FP32/
- *   FP32_BF16BASIS, graph_id + (graphs in g) - 1 < 65536.
+ *   FP32_BF16BASIS, graph_id + (graphs in g) - 1 < 65536; the projection
+ *   coefficients s * ld * (8 for FP64, else 4) bytes must fit 200 KiB (ld =
+ *   nv rounded up to a 32-byte row), else SLAQ_EUNSUPPORTED (FP64 with
+ *   nv = 512 allows s <= 50).
  * inout: if *inout is NULL a new handle is created; otherwise *inout must
  * come from an earlier call with the same nv, s and precision, and its
  * device workspace is reused (grown if the graph is larger).

@@ -29,7 +29,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-DEFAULT_TOL = {"fp64": 1e-10, "fp32": 1e-4, "bf16": 3e-2}
+DEFAULT_TOL = {"fp64": 1e-10, "fp32": 1e-4, "bf16": 1e-4}
 
 
 @dataclass

@@ -157,6 +157,10 @@ def _rel(a, b):
     ("k9", NORMALIZED, False, 6, 8),               # breakdown at m = 2
     ("star30", COMBINATORIAL, False, 5, 8),        # breakdown at m = 3
     ("k35", NORMALIZED, False, 4, 6),
+    ("ba2000", NORMALIZED, False, 1, 1),           # one probe, one step
+    ("ba2000", NORMALIZED, False, 2, 2),
+    ("ba2000", NORMALIZED, False, 512, 6),         # largest probe block
+    ("ba2000", NORMALIZED, False, 3, 64),          # largest step count
 ])
 def test_fp64_lanczos_and_descriptors(name, kind, drop, nv, s):
     src, dst, n = GRAPHS[name]()
@@ -257,6 +261,51 @@ def test_reduced_precision_forms_vs_fp64(precision, h_tol, v_tol):
     v64 = slaq.trace_vnge(K64)[0].item()
     v = slaq.trace_vnge(K)[0].item()
     assert abs(v - v64) / abs(v64) < v_tol
+
+
+@pytest.mark.parametrize("graph", ["star2600", "k9", "k35", "star30"])
+def test_reduced_forms_on_breakdown_graphs(graph):
+    """Graphs whose Krylov space closes after 2 or 3 steps, and a hub row of
+    2599 entries (split into chunks) whose sum against the null vector nearly
+    cancels: the reduced forms stop where the FP64 form stops and keep the
+    heat trace within 1e-4.  The BF16 basis may run a step past the closing:
+    its stored vectors' rounding leaves a residual of about 2^-9 there, and
+    the Rayleigh-Ritz step gives the extra direction its negligible weight."""
+    src, dst, n = synth.star(2600) if graph == "star2600" else GRAPHS[graph]()
+    g = gpu_graph(src, dst, n)
+    t = dev(synth.t_grid(), torch.float64)
+    K64 = slaq.lanczos(g, 16, 8, 21, precision=slaq.FP64)
+    m64 = slaq.krylov_export(K64)[2].cpu().numpy()
+    h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
+    for prec in (slaq.FP32, slaq.FP32_BF16BASIS):
+        K = slaq.lanczos(g, 16, 8, 21, precision=prec)
+        m = slaq.krylov_export(K)[2].cpu().numpy()
+        if prec == slaq.FP32:
+            assert np.array_equal(m, m64)
+        else:
+            assert np.all(m >= m64) and np.all(m <= m64 + 1)
+        assert _rel(slaq.trace_heat(K, t)[0].cpu().numpy(), h64) < 1e-4, prec
+
+
+def test_largest_sizes_reduced_forms_and_limits():
+    src, dst, n = GRAPHS["ba2000"]()
+    g = gpu_graph(src, dst, n)
+    t = dev(synth.t_grid(), torch.float64)
+    h64 = slaq.trace_heat(slaq.lanczos(g, 512, 40, 3, precision=slaq.FP64), t)[0].cpu().numpy()
+    for prec in (slaq.FP32, slaq.FP32_BF16BASIS):
+        h = slaq.trace_heat(slaq.lanczos(g, 512, 40, 3, precision=prec), t)[0].cpu().numpy()
+        assert _rel(h, h64) < 1e-4, prec
+        K = slaq.lanczos(g, 512, 64, 3, precision=prec)
+        assert np.all(np.isfinite(slaq.trace_heat(K, t)[0].cpu().numpy()))
+        h0 = slaq.trace_heat(K, dev([0.0], torch.float64))[0].item()
+        assert abs(h0 - n) < 1e-6 * n          # sum of the Gauss weights = 1
+    # the FP64 coefficient table holds s * ld * 8 <= 200 KiB
+    with pytest.raises(slaq.SlaqError) as ei:
+        slaq.lanczos(g, 512, 64, 3, precision=slaq.FP64)
+    assert ei.value.status == 6
+    for bad in ((0, 5), (513, 5), (4, 0), (4, 65)):
+        with pytest.raises(slaq.SlaqError):
+            slaq.lanczos(g, bad[0], bad[1], 3)
 
 
 def test_workspace_reuse_and_host_call():
