@@ -234,12 +234,14 @@ def algorithmic_bytes(n, nnz, prec, nv=NV, s=S):
     return {"spmm": spmm, "dots": dots, "update": update}
 
 
-def run_batched(args, dev, world=1, rank=0):
+def run_batched(args, dev, world=1, rank=0, tdist=None):
     """The SBM batch through one set of launches per step; graphs/s.  Also
-    times the same path graph by graph on a subset (per-graph launches)."""
+    times the same path graph by graph on a subset (per-graph launches).
+    Under torchrun every rank runs its own batch (seed + rank): weak scaling
+    over graphs, no exchange, the slowest rank's time."""
     import torch
     from paper_2003_01282_gb300 import slaq
-    graphs = synth.sbm_batch(SBM_GRAPHS, seed=SBM_SEED)
+    graphs = synth.sbm_batch(SBM_GRAPHS, seed=SBM_SEED + rank)
     srcs = np.concatenate([g[0] for g in graphs])
     dsts = np.concatenate([g[1] for g in graphs])
     edge_off = np.zeros(len(graphs) + 1, np.int64)
@@ -260,7 +262,7 @@ def run_batched(args, dev, world=1, rank=0):
             node_off.ctypes.data_as(C.c_void_p), len(graphs), None, slaq.NORMALIZED, slaq.DROP_ISOLATED,
             slaq._stream(None), C.byref(out)))
         g = slaq.Graph(out)
-        state["K"] = slaq.lanczos(g, SBM_NV, SBM_S, PROBE_SEED + 1000 * rank, precision=P,
+        state["K"] = slaq.lanczos(g, SBM_NV, SBM_S, rank_seed(rank), precision=P,
                                   reuse=state["K"])
         heat, _ = slaq.trace_heat(state["K"], t)
         nnz = g.info["nnz"]
@@ -281,6 +283,8 @@ def run_batched(args, dev, world=1, rank=0):
     prof = slaq.profile_read()
     slaq.profile_enable(False)
     ms = e0.elapsed_time(e1) / reps
+    if tdist is not None:
+        ms = max_over_ranks(ms, dev, tdist)
     # the same path graph by graph on a subset (every 25th graph)
     sub = graphs[::25]
     Ks = None
@@ -294,7 +298,8 @@ def run_batched(args, dev, world=1, rank=0):
     e1.record()
     torch.cuda.synchronize(dev)
     ms_sub = e0.elapsed_time(e1)
-    return {"workload": SBM_WORKLOAD, "metric": "graphs/s", "value": world * SBM_GRAPHS / (ms * 1e-3),
+    return {"workload": SBM_WORKLOAD, "metric": "graphs/s",
+            "value": whole_job_value(world, SBM_GRAPHS, ms),
             "ms_per_step": ms, "nnz": int(nnz),
             "probe_edges_per_s": world * nnz * SBM_NV * SBM_S / (ms * 1e-3),
             "kernels_ms_per_step": {k: round(v[0] / reps, 3) for k, v in prof.items()},
@@ -344,6 +349,34 @@ def kernel_capture(args):
     print(json.dumps({"kernel_capture": args.kernel_capture, "n_prime": g.info["n"], "nnz": g.info["nnz"]}))
 
 
+# ---- multi-rank host logic (probe sharding; no data-path collective)
+def rank_seed(rank: int) -> int:
+    """Probe seed of a rank: every rank draws its own nv probes."""
+    return PROBE_SEED + 1000 * rank
+
+
+def average_over_ranks(desc, world: int, tdist):
+    """The per-rank estimates of the same graph are Hutchinson means over
+    disjoint probe sets of equal size, so their mean is the estimate over
+    all world * nv probes: one all-reduce of the descriptor vector."""
+    tdist.all_reduce(desc)
+    desc /= world
+    return desc
+
+
+def max_over_ranks(ms: float, device, tdist) -> float:
+    """The job's step time: the slowest rank's."""
+    import torch
+    mt = torch.tensor([ms], device=device, dtype=torch.float64)
+    tdist.all_reduce(mt, op=tdist.ReduceOp.MAX)
+    return float(mt.item())
+
+
+def whole_job_value(world: int, units_per_step_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: every rank processes its own units each step."""
+    return world * units_per_step_per_rank / (ms * 1e-3)
+
+
 def run_ours(args):
     import torch
     from paper_2003_01282_gb300 import slaq
@@ -371,7 +404,7 @@ def run_ours(args):
     dst = dst_h.to(dev)
     t_np = synth.t_grid(NT)
     t = torch.as_tensor(t_np, device=dev)
-    seed = PROBE_SEED + 1000 * rank
+    seed = rank_seed(rank)
     prec = args.precision
     P = slaq.PRECISIONS[prec]
 
@@ -386,8 +419,7 @@ def run_ours(args):
         vn, _ = slaq.trace_vnge(K)
         desc = torch.cat([heat, wr, wi, vn])
         if dist:
-            tdist.all_reduce(desc)
-            desc /= world
+            average_over_ranks(desc, world, tdist)
         if state["ref"] is None:
             state["ref"] = desc[:NT].clone()
         d = slaq.distance(desc[:NT], state["ref"], slaq.DIST_HEAT)
@@ -429,11 +461,9 @@ def run_ours(args):
     clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
     if dist:
-        mt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        tdist.all_reduce(mt, op=tdist.ReduceOp.MAX)
-        ms = float(mt.item())
+        ms = max_over_ranks(ms, dev, tdist)
     pe_step = nnz * NV * S
-    value = world * pe_step / (ms * 1e-3)
+    value = whole_job_value(world, pe_step, ms)
 
     # roofline of the dominant Lanczos kernel class
     hbm, peak_src = peaks()
@@ -528,7 +558,7 @@ def run_ours(args):
                          "ms_per_step": e2e_s * 1e3}
 
     if not args.quick and not args.no_batched:
-        result["batched_sbm5000"] = run_batched(args, dev, world, rank)
+        result["batched_sbm5000"] = run_batched(args, dev, world, rank, tdist if dist else None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(src_np, dst_np, n_nodes)
     if rank == 0:
