@@ -302,10 +302,21 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
     TW x[4][VE];
 #pragma unroll
     for (int q = 0; q < 4; ++q) ldb(Ul + (int64_t)c[q] * stride, x[q]);
+    if (COMP) {
+      // the group's four products summed plainly, then one compensated add
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+      for (int v = 0; v < VE; ++v) {
+        TW g = w[0] * x[0][v];
 #pragma unroll
-      for (int v = 0; v < VE; ++v) acc_add<COMP>(acc[v], cmp[v], w[q], x[q][v]);
+        for (int q = 1; q < 4; ++q) g = fma(w[q], x[q][v], g);
+        acc_add<true>(acc[v], cmp[v], TW(1), g);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int v = 0; v < VE; ++v) acc_add<false>(acc[v], cmp[v], w[q], x[q][v]);
+    }
   }
   for (; j < e; ++j) {
     const int c = __ldcs(col + j);
@@ -1093,12 +1104,12 @@ __global__ void __launch_bounds__(512)
   const int gr = cgraph[blockIdx.x];
   const double *coef = coef_all + (int64_t)gr * s * ld;
   const int32_t *m = m_all + (int64_t)gr * nv;
-  // coefficients times the step's scale zs = 1/||u_k|| (row s-1 of coef;
-  // 1 in the second pass), then zs itself: u_{k+1} = zs (x - sum_j c_j u_j)
+  // coefficients, then the step's scale zs = 1/||u_k|| (row s-1 of coef;
+  // 1 in the second pass): u_{k+1} = zs (x - sum_j c_j u_j)
   TW *cf = reinterpret_cast<TW *>(dyn);  // [(k+2) * ld]
-  const double *zs = coef + (int64_t)(s - 1) * ld;
-  for (int i = threadIdx.x; i < (k + 1) * ld; i += blockDim.x) cf[i] = (TW)(coef[i] * zs[i % ld]);
-  for (int i = threadIdx.x; i < ld; i += blockDim.x) cf[(k + 1) * ld + i] = (TW)zs[i];
+  for (int i = threadIdx.x; i < (k + 1) * ld; i += blockDim.x) cf[i] = (TW)coef[i];
+  for (int i = threadIdx.x; i < ld; i += blockDim.x)
+    cf[(k + 1) * ld + i] = (TW)coef[(int64_t)(s - 1) * ld + i];
   __syncthreads();
   const int team = threadIdx.x / V, lane = threadIdx.x - team * V;
   if (team >= R) return;
@@ -1117,11 +1128,6 @@ __global__ void __launch_bounds__(512)
     TW x[VE];
     if (SECOND) ldb_rw(Unext + o, x);
     else ldw<TW, VE>(Z + o, x);
-    {
-      const TW *zv = cf + (k + 1) * ld + lane * VE;
-#pragma unroll
-      for (int v = 0; v < VE; ++v) x[v] *= zv[v];
-    }
     int j = 0;
     for (; j + 2 <= k + 1; j += 2) {
       TW u0[VE], u1[VE];
@@ -1142,9 +1148,11 @@ __global__ void __launch_bounds__(512)
 #pragma unroll
       for (int v = 0; v < VE; ++v) x[v] = fma(-c0[v], u0[v], x[v]);
     }
+    {
+      const TW *zv = cf + (k + 1) * ld + lane * VE;
 #pragma unroll
-    for (int v = 0; v < VE; ++v)
-      if (!keep[v]) x[v] = TW(0);
+      for (int v = 0; v < VE; ++v) x[v] = keep[v] ? x[v] * zv[v] : TW(0);
+    }
     TW r[VE];
     stb(Unext + o, x, r);
     if (Ynext) {  // pre-scaled copy for the next SpMM (MODE 3)
