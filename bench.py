@@ -199,13 +199,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ our arm
-# DRAM traffic of one SpMM (k_spmm_light + k_spmm_heavy, step 16) of the FP32
+# DRAM traffic of one SpMM (light-row + split-row kernels, step 16) of the FP32
 # R-MAT 2^20 workload, from the ncu capture summarised in
 # profiles/kernels_rmat20_fp32_k16.md; it describes the kernels only while
 # csrc/lanczos.cu is byte-identical to the source that was captured.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1739706000 + 236616192 + 573578000 + 8204032,
-    "source_sha256": "4b80d55696acc78c4ffe085c1a00017c92b5ee80dc679103384b86e76715c35c",
+    "bytes_per_spmm": 1954396000 + 351717376 + 561647000 + 8315136,
+    "source_sha256": "bd795d717c8297c7c1aec0ddd7b03a4d3e5f55acf8886fd35c02b2d840a4e2e0",
 }
 
 
