@@ -270,16 +270,17 @@ int radix_sort(uint64_t **keys, uint64_t **keys_alt, double **pay, double **pay_
   SLAQ_TRY(dalloc_t(&offsets, 256 * ntiles, st));
   SLAQ_TRY(dalloc_t(&total, 1, st));
   const bool with_pay = pay && *pay;
-  static bool attr_set = false;
-  if (!attr_set) {
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_radix_scatter<true>,
+  // once per process (a thread-safe static initialization)
+  static const cudaError_t attr = [] {
+    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rs_smem(true)));
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_radix_scatter<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rs_smem(false)));
-    attr_set = true;
-  }
+                                         (int)rs_smem(true));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_radix_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rs_smem(false));
+    return e;
+  }();
+  SLAQ_CHECK_CUDA(attr);
   for (int shift = 0; shift < bits; shift += 8) {
     ++tl_launches;
     k_radix_hist<<<(unsigned)ntiles, kRsHistThreads, 0, st>>>(*keys, n, shift, counts, ntiles);

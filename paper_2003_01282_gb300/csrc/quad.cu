@@ -466,13 +466,9 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   // the solver is latency-bound: few problems go one per block, over many SMs
   const int tpb = std::max(1, std::min(32, total / std::max(1, num_sms())));
   if (K->precision != SLAQ_FP64 && total < 4096) {
-    static bool attr_set = false;
-    if (!attr_set) {
-      SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_ritz_pencil_warp,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ritz_warp_smem(kMaxS)));
-      attr_set = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_ritz_pencil_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ritz_warp_smem(kMaxS));
+    SLAQ_CHECK_CUDA(attr);
     k_ritz_pencil_warp<<<(unsigned)total, 32, ritz_warp_smem(K->s), st>>>(
         K->gram, K->proj, K->m, K->nv, K->s, K->ld, K->alpha, K->beta, K->theta, K->tau2,
         K->status);

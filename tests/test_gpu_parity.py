@@ -263,6 +263,29 @@ def test_reduced_precision_forms_vs_fp64(precision, h_tol, v_tol):
     assert abs(v - v64) / abs(v64) < v_tol
 
 
+@pytest.mark.parametrize("kind,weighted", [(NORMALIZED, True), (COMBINATORIAL, False),
+                                           (COMBINATORIAL, True)])
+def test_reduced_forms_other_laplacians(kind, weighted):
+    """The values form (weighted) and the combinatorial pattern form in FP32
+    and with the BF16 basis, against the FP64 form: heat within 1e-4 where it
+    is above 1e-12 of its t = 0 value (the combinatorial spectrum reaches
+    2 max d, so exp(-t theta) underflows the comparison at large t), VNGE
+    within 1e-3."""
+    s, d, n = synth.barabasi_albert(3000, 5, seed=12)
+    w = np.random.default_rng(5).uniform(0.5, 2.0, s.size) if weighted else None
+    g = gpu_graph(s, d, n, kind, weights=w)
+    t = dev(synth.t_grid(), torch.float64)
+    K64 = slaq.lanczos(g, 24, 16, 6, precision=slaq.FP64)
+    h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
+    v64 = slaq.trace_vnge(K64)[0].item()
+    sel = h64 > 1e-12 * h64[0]
+    for prec in (slaq.FP32, slaq.FP32_BF16BASIS):
+        K = slaq.lanczos(g, 24, 16, 6, precision=prec)
+        h = slaq.trace_heat(K, t)[0].cpu().numpy()
+        assert _rel(h[sel], h64[sel]) < 1e-4, prec
+        assert abs(slaq.trace_vnge(K)[0].item() - v64) / abs(v64) < 1e-3, prec
+
+
 @pytest.mark.parametrize("graph", ["star2600", "k9", "k35", "star30"])
 def test_reduced_forms_on_breakdown_graphs(graph):
     """Graphs whose Krylov space closes after 2 or 3 steps, and a hub row of
