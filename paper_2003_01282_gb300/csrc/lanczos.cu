@@ -86,14 +86,16 @@ __device__ __forceinline__ void ldb(const float *p, float (&v)[4]) {
   v[2] = t.z;
   v[3] = t.w;
 }
-__device__ __forceinline__ void ldb(const __nv_bfloat16 *p, float (&v)[8]) {
-  uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
+__device__ __forceinline__ void unpack_bf16x8(const uint4 &t, float (&v)[8]) {
   const uint32_t w[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     v[2 * i] = __uint_as_float(w[i] << 16);
     v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
   }
+}
+__device__ __forceinline__ void ldb(const __nv_bfloat16 *p, float (&v)[8]) {
+  unpack_bf16x8(__ldg(reinterpret_cast<const uint4 *>(p)), v);
 }
 // coherent loads, for rows this kernel also writes (in-place second pass)
 __device__ __forceinline__ void ldb_rw(const double *p, double (&v)[2]) {
@@ -707,6 +709,30 @@ __global__ void __launch_bounds__(512, 2)
       }
       constexpr int UNR = VE >= 8 ? 2 : 4;  // rows in flight per thread (register budget)
       int r = rz;
+      if constexpr (P == SLAQ_FP32_BF16BASIS) {
+        // BF16: four rows in flight as packed 16-byte words, unpacked one at
+        // a time (eight floats per row would not fit the register budget)
+        for (; r + 3 * RZ < nr; r += 4 * RZ) {
+          uint4 raw[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            raw[q] = __ldg(reinterpret_cast<const uint4 *>(Uj + (row0 + r + q * RZ) * stride));
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            TW u[VE], x[VE];
+            unpack_bf16x8(raw[q], u);
+            lds(xt + (r + q * RZ) * ld, x);
+#pragma unroll
+            for (int v = 0; v < VE; ++v) dc[v] = fma(u[v], x[v], dc[v]);
+            if (WITH_G) {
+              TW w[VE];
+              lds(ut + (r + q * RZ) * ld, w);
+#pragma unroll
+              for (int v = 0; v < VE; ++v) gc[v] = fma(u[v], w[v], gc[v]);
+            }
+          }
+        }
+      }
       for (; r + (UNR - 1) * RZ < nr; r += UNR * RZ) {
         TW u[UNR][VE];
 #pragma unroll
@@ -1458,26 +1484,25 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   K->ymode = P == SLAQ_FP32 && !gr->weighted && gr->kind == SLAQ_NORMALIZED && K->Y;
   K->yscale = gr->x_scale32;
   const Geometry geo = geometry(P, K->ld, n, num_sms(), K->tune);
-  static bool attr_set = false;
-  if (!attr_set) {
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_update<P, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_update<P, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_dots<P, false, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_dots<P, false, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_dots<P, true, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_solve_lanes<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSolveLanesSmemMax));
-    SLAQ_CHECK_CUDA(cudaFuncSetAttribute(k_solve_lanes<float>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSolveLanesSmemMax));
-    attr_set = true;
-  }
+  // once per process and form (a thread-safe static initialization)
+  static const cudaError_t attr = [] {
+    const void *fs[] = {(const void *)k_update<P, false>, (const void *)k_update<P, true>,
+                        (const void *)k_dots<P, false, true>, (const void *)k_dots<P, false, false>,
+                        (const void *)k_dots<P, true, false>};
+    for (const void *f : fs) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDotsSmemMax);
+      if (e != cudaSuccess) return e;
+    }
+    const void *gs[] = {(const void *)k_solve_lanes<double>, (const void *)k_solve_lanes<float>};
+    for (const void *f : gs) {
+      const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSolveLanesSmemMax);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }();
+  SLAQ_CHECK_CUDA(attr);
   // chunk tables: dots chunks fill one wave; update chunks are smaller
   {
     const int Jb = std::min(K->s, geo.Jb);
@@ -1609,7 +1634,7 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   if (g->n < 1) return set_error(SLAQ_EINVAL, "graph has no nodes");
   if (g->n > (1LL << 31)) return set_error(SLAQ_EUNSUPPORTED, "too many nodes");
   const int ld = row_ld(nv, precision);
-  if ((size_t)s * ld * work_bytes(precision) > 200 * 1024)
+  if ((size_t)s * ld * work_bytes(precision) > kDotsSmemMax)
     return set_error(SLAQ_EUNSUPPORTED, "s * nv too large for the update kernel's coefficient table");
   slaq_krylov K = *inout;
   const bool fresh = (K == nullptr);
