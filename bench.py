@@ -204,8 +204,8 @@ class ClockSampler:
 # profiles/kernels_rmat20_fp32_k16.md; it describes the kernels only while
 # csrc/lanczos.cu is byte-identical to the source that was captured.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1954396000 + 351717376 + 561647000 + 8315136,
-    "source_sha256": "bd795d717c8297c7c1aec0ddd7b03a4d3e5f55acf8886fd35c02b2d840a4e2e0",
+    "bytes_per_spmm": 1955673000 + 351422720 + 562093000 + 8338688,
+    "source_sha256": "315eab6af78f98e929b6bed21057a7f43477ad0155745faffbb070c1dadbfa7e",
 }
 
 
