@@ -638,7 +638,7 @@ __global__ void k_perm_entries(const uint64_t *ukey, const int64_t *newid, int d
     const int64_t i = drop ? newid[r_old] : r_old;
     const int64_t x = xrowptr[inv[i]] + (e - rowptr[i]);
     xcol[x] = (int32_t)inv[colidx[e]];
-    xvals[x] = vals[e];
+    if (xvals) xvals[x] = vals[e];
     if (xvals32) xvals32[x] = vals32[e];
   }
 }
@@ -1030,7 +1030,9 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   // 5. execution copy: graph-major, then descending degree, then id
   SLAQ_TRY(persistent(&g->x_rowptr, n_out + 1));
   SLAQ_TRY(persistent(&g->x_colidx, nnz));
-  SLAQ_TRY(persistent(&g->x_vals, nnz));
+  // the SpMM reads values only in the weighted form; unweighted graphs run the
+  // pattern form from the scales, so their execution copy keeps no values
+  if (weighted) SLAQ_TRY(persistent(&g->x_vals, nnz));
   if (weighted) SLAQ_TRY(persistent(&g->x_vals32, nnz));
   SLAQ_TRY(persistent(&g->x_diag, n_out));
   SLAQ_TRY(persistent(&g->x_scale, n_out));
@@ -1204,7 +1206,7 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   SLAQ_TRY(persistent(&g->old_id, n));
   SLAQ_TRY(persistent(&g->x_rowptr, n + 1));
   SLAQ_TRY(persistent(&g->x_colidx, nnz));
-  SLAQ_TRY(persistent(&g->x_vals, nnz));
+  if (w) SLAQ_TRY(persistent(&g->x_vals, nnz));
   if (w) SLAQ_TRY(persistent(&g->x_vals32, nnz));
   SLAQ_TRY(persistent(&g->x_diag, n));
   SLAQ_TRY(persistent(&g->x_scale, n));
@@ -1227,7 +1229,7 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::colidx), nnz_of, col_add, g->colidx, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_colidx), nnz_of, col_add, g->x_colidx, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::vals), nnz_of, no_d, g->vals, st));
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_vals), nnz_of, no_d, g->x_vals, st));
+  if (w) SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_vals), nnz_of, no_d, g->x_vals, st));
   if (w) {
     SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::vals32), nnz_of, no_f, g->vals32, st));
     SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_vals32), nnz_of, no_f, g->x_vals32, st));

@@ -121,7 +121,7 @@ struct slaq_graph_s {
   // signs follow x_old_id, so they are those of the canonical order.
   int64_t *x_rowptr = nullptr;  // [n+1]
   int32_t *x_colidx = nullptr;  // [nnz]
-  double *x_vals = nullptr;     // [nnz]
+  double *x_vals = nullptr;     // [nnz] (weighted only: unweighted graphs run the pattern form)
   float *x_vals32 = nullptr;    // [nnz] (weighted only)
   double *x_diag = nullptr, *x_scale = nullptr;    // [n]
   float *x_diag32 = nullptr, *x_scale32 = nullptr; // [n]
