@@ -98,7 +98,7 @@ int slaq_build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges
  * edge_off_host[g+1]) with ids LOCAL to the graph, in [0, n_g), n_g =
  * node_off_host[g+1] - node_off_host[g] >= 1; weights (optional) follow the
  * edges.  kind and flags as for slaq_build_laplacian, applied per graph.
- * 1 <= G <= 65536; offsets are host arrays of G+1 entries starting at 0.
+ * 1 <= G <= 65535; offsets are host arrays of G+1 entries starting at 0.
  * Graph g's results match a single-graph run of graph g with graph_id
  * (of slaq_lanczos) increased by g.  A graph that keeps no nodes (all
  * isolated and dropped) stays in the batch with an empty Krylov space:
@@ -165,7 +165,7 @@ int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id,
  * (in order, sub-graphs of batch handles expanded) gets probe graph field
  * graph_id + g, so its results equal slaq_lanczos(gs[g], ..., graph_id + g)
  * up to rounding order.  All graphs must share the Laplacian kind and be all
- * weighted or all unweighted; at most 65536 graphs in total.
+ * weighted or all unweighted; at most 65535 graphs in total.
  * tune_cache: NULL runs the default launch shapes.  Otherwise it names a
  * text file: if it holds a line for this workload class (precision, nv, s,
  * reorth_passes, log2 of n', of nnz/n' and of the graph count, SM count) the

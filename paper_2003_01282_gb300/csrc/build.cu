@@ -765,8 +765,9 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   const bool batch = n_graphs > 1 || edge_off_host || node_off_host;
   std::vector<int64_t> node_off{0, n};
   if (batch) {
-    if (n_graphs < 1 || n_graphs > 65536 || !edge_off_host || !node_off_host)
-      return set_error(SLAQ_EINVAL, "a batch needs 1..65536 graphs and both offset arrays");
+    // 65535: per-graph launches put the graph on a grid's y or z axis
+    if (n_graphs < 1 || n_graphs > 65535 || !edge_off_host || !node_off_host)
+      return set_error(SLAQ_EINVAL, "a batch needs 1..65535 graphs and both offset arrays");
     if (edge_off_host[0] != 0 || node_off_host[0] != 0)
       return set_error(SLAQ_EINVAL, "offsets must start at 0");
     for (int g = 0; g < n_graphs; ++g) {
@@ -1148,7 +1149,7 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
                        "none weighted", h);
     G += a->n_graphs;
   }
-  if (G > 65536) return set_error(SLAQ_EINVAL, "a batch holds at most 65536 graphs");
+  if (G > 65535) return set_error(SLAQ_EINVAL, "a batch holds at most 65535 graphs");
   Temps tmp(st);
   slaq_graph g = new slaq_graph_s();
   struct Guard {
