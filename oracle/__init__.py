@@ -26,9 +26,11 @@ Modules and the passages they follow
 ``exact``      the plain definitions through a dense eigendecomposition
                (the ground truth the paper compares against, Sec. 4.1).
 ``distance``   spectral distances between descriptors (Sec. 4.2).
+``variance``   the polynomial control variate of Sec. 3.1 ("2-term
+               polynomial" variance reduction) and tr L^2.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants and the worked example of Fig. 1; nothing here is unpinned.
 """
 
-from . import laplacian, probes, lanczos, quadrature, descriptors, exact, distance  # noqa: F401
+from . import laplacian, probes, lanczos, quadrature, descriptors, exact, distance, variance  # noqa: F401
