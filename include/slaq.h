@@ -214,6 +214,21 @@ int slaq_krylov_info(slaq_krylov k, int *nv_host, int *s_host, int *precision_ho
 int slaq_trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *stderr_,
                     double *per_probe, void *stream);
 
+/* The heat trace with a polynomial control variate (Sec. 3.1, the "2-term
+ * polynomial" variance reduction, whose polynomial the paper does not give).
+ * Reading: p_t is the Chebyshev interpolant of degree `degree` (1: c0 + c1 x,
+ * 2: + c2 x^2) of exp(-t x) on [0, bound] (bound 2 normalized, 2 max d
+ * combinatorial), at the nodes (bound/2)(1 + cos(pi (j + 1/2)/(degree + 1))).
+ *   out[i] = (n'/nv) sum_p sum_k tau2 (exp(-t_i theta) - p_t(theta))
+ *            + c0 n' + c1 tr L + c2 tr L^2,
+ * with tr L^2 = sum_ij L_ij^2 computed by the builder.  Each probe's Gauss
+ * rule is exact for p_t, so the estimate stays unbiased; stderr_ is the
+ * sample std of the corrected per-probe values / sqrt(nv) (smaller where
+ * p_t follows exp(-t x) on the spectrum: small t).  per_probe (or NULL) as
+ * for slaq_trace_heat, corrected.  degree other than 1 or 2: SLAQ_EINVAL. */
+int slaq_trace_heat_cv(slaq_krylov k, const double *t, int nt, int degree, double *out,
+                       double *stderr_, double *per_probe, void *stream);
+
 /* Wave trace tr exp(-i t L): re[i] = sum cos(t lambda), im[i] = -sum sin(t lambda),
  * estimated as above; stderr arrays may be NULL. */
 int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im,

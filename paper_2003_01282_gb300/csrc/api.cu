@@ -332,6 +332,13 @@ int slaq_trace_heat(slaq_krylov k, const double *t, int nt, double *out, double 
   return trace_heat(k, t, nt, out, stderr_, per_probe, as_stream(stream));
 }
 
+int slaq_trace_heat_cv(slaq_krylov k, const double *t, int nt, int degree, double *out,
+                       double *stderr_, double *per_probe, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  return trace_heat_cv(k, t, nt, degree, out, stderr_, per_probe, as_stream(stream));
+}
+
 int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im,
                     double *stderr_re, double *stderr_im, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");

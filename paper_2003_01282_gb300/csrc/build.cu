@@ -540,6 +540,39 @@ __global__ void k_scale(const double *deg, int64_t n, int kind, double *scale, d
 }
 
 // One thread per stored entry; its row and column come from the sorted key.
+// tr(L_g^2) = sum_ij (L_g)_ij^2 of every graph: one block per graph, rows
+// strided over the threads (each row summed in column order), the threads'
+// compensated sums combined in a fixed tree order (deterministic).
+constexpr int kSqThreads = 256;
+__global__ void __launch_bounds__(kSqThreads)
+    k_graph_sq(const int64_t *rowptr, const double *vals, const double *diag,
+               const int64_t *goff, double *out) {
+  __shared__ double ssum[kSqThreads], scmp[kSqThreads];
+  const int gr = blockIdx.x;
+  double sm = 0.0, cp = 0.0;  // Neumaier
+  auto add = [&](double x) {
+    const double t = sm + x;
+    cp += fabs(sm) >= fabs(x) ? (sm - t) + x : (x - t) + sm;
+    sm = t;
+  };
+  for (int64_t i = goff[gr] + threadIdx.x; i < goff[gr + 1]; i += kSqThreads) {
+    double r = diag[i] * diag[i];
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) r += vals[e] * vals[e];
+    add(r);
+  }
+  ssum[threadIdx.x] = sm;
+  scmp[threadIdx.x] = cp;
+  __syncthreads();
+  for (int w = kSqThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      ssum[threadIdx.x] += ssum[threadIdx.x + w];
+      scmp[threadIdx.x] += scmp[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[gr] = ssum[0] + scmp[0];
+}
+
 // Batches: first union id of the graph of every input node (keys carry
 // graph-local column ids).
 __global__ void k_row_base(const int64_t *node_off, int G, int64_t n, int64_t *rowbase) {
@@ -685,7 +718,7 @@ void graph_free(slaq_graph g) {
                   g->scale32, g->old_id, g->heavy_row, g->heavy_first, g->chunk_slot,
                   g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32, g->x_diag, g->x_scale,
                   g->x_diag32, g->x_scale32, g->x_old_id, g->goff_dev, g->gn_dev,
-                  g->gtrace_dev, g->gbound_dev, g->x_graph};
+                  g->gtrace_dev, g->gbound_dev, g->x_graph, g->gtrace2_dev};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -1026,6 +1059,14 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
                                cudaMemcpyHostToDevice));
     SLAQ_CHECK_CUDA(cudaMemcpy(g->gbound_dev, g->gbound.data(), G * sizeof(double),
                                cudaMemcpyHostToDevice));
+    // tr(L_g^2) for the polynomial control variate of the heat trace
+    SLAQ_TRY(persistent(&g->gtrace2_dev, G));
+    ++tl_launches;
+    k_graph_sq<<<(unsigned)G, kSqThreads, 0, st>>>(g->rowptr, g->vals, g->diag, g->goff_dev,
+                                                   g->gtrace2_dev);
+    SLAQ_CHECK_LAUNCH("graph_sq");
+    g->gtrace2.assign(G, 0.0);
+    SLAQ_TRY(to_host(g->gtrace2.data(), g->gtrace2_dev, G, st));
   }
 
   // 5. execution copy: graph-major, then descending degree, then id
@@ -1182,6 +1223,7 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
     for (int q = 0; q < a->n_graphs; ++q) {
       g->goff.push_back(n + a->goff[q + 1]);
       g->gtrace.push_back(a->gtrace[q]);
+      g->gtrace2.push_back(a->gtrace2[q]);
       g->gbound.push_back(a->gbound[q]);
     }
     n += a->n;
@@ -1261,6 +1303,9 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
     SLAQ_CHECK_CUDA(cudaMemcpy(g->gtrace_dev, g->gtrace.data(), G * sizeof(double),
                                cudaMemcpyHostToDevice));
     SLAQ_CHECK_CUDA(cudaMemcpy(g->gbound_dev, g->gbound.data(), G * sizeof(double),
+                               cudaMemcpyHostToDevice));
+    SLAQ_TRY(persistent(&g->gtrace2_dev, G));
+    SLAQ_CHECK_CUDA(cudaMemcpy(g->gtrace2_dev, g->gtrace2.data(), G * sizeof(double),
                                cudaMemcpyHostToDevice));
   }
   SLAQ_TRY(heavy_schedule(g, tmp, st));

@@ -99,10 +99,12 @@ struct slaq_graph_s {
   int n_graphs = 1;
   std::vector<int64_t> goff;        // [G+1] host copy
   std::vector<double> gtrace;       // [G] tr(L_g)
+  std::vector<double> gtrace2;      // [G] tr(L_g^2) = sum_ij (L_g)_ij^2
   std::vector<double> gbound;       // [G] bound of the spectrum of L_g
   int64_t *goff_dev = nullptr;      // [G+1]
   double *gn_dev = nullptr;         // [G] node counts as double
   double *gtrace_dev = nullptr;     // [G]
+  double *gtrace2_dev = nullptr;    // [G]
   double *gbound_dev = nullptr;     // [G]
   int32_t *x_graph = nullptr;       // [n] graph of each execution row
   int64_t *rowptr = nullptr;   // [n+1]
@@ -187,6 +189,7 @@ struct slaq_krylov_s {
   int n_graphs = 1;
   double *gn = nullptr;      // [G] node counts
   double *gtrace = nullptr;  // [G] tr(L_g)
+  double *gtrace2 = nullptr; // [G] tr(L_g^2)
   double *gbound = nullptr;  // [G] spectral bounds (breakdown tolerance)
   int64_t gcap = 0;          // graphs the per-graph arrays hold
   // row chunks inside one graph: dots (d*) and update (u*) kernels
@@ -223,6 +226,8 @@ int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaS
 int run_ritz(slaq_krylov k, cudaStream_t st);
 int trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *se,
                double *per_probe, cudaStream_t st);
+int trace_heat_cv(slaq_krylov k, const double *t, int nt, int degree, double *out, double *se,
+                  double *per_probe, cudaStream_t st);
 int trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im, double *se_re,
                double *se_im, cudaStream_t st);
 int trace_vnge(slaq_krylov k, double *out, double *se, double *per_probe, cudaStream_t st);

@@ -1611,7 +1611,8 @@ void krylov_free(slaq_krylov k) {
   if (!k) return;
   void *ptrs[] = {k->U, k->Z, k->Y, k->P, k->part, k->dsum, k->coef, k->gram, k->proj, k->rscratch,
                   k->alpha, k->beta,
-                  k->m, k->theta, k->tau2, k->status, k->hcount, k->gn, k->gtrace, k->gbound,
+                  k->m, k->theta, k->tau2, k->status, k->hcount, k->gn, k->gtrace, k->gtrace2,
+                  k->gbound,
                   k->d_row0, k->d_rows, k->d_goff, k->u_row0, k->u_rows, k->u_graph};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -1698,11 +1699,14 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     SLAQ_TRY(grow(&K->tau2, ns));
     SLAQ_TRY(grow(&K->gn, (size_t)G));
     SLAQ_TRY(grow(&K->gtrace, (size_t)G));
+    SLAQ_TRY(grow(&K->gtrace2, (size_t)G));
     SLAQ_TRY(grow(&K->gbound, (size_t)G));
     K->gcap = G;
   }
   if (!K->status) SLAQ_TRY(grow(&K->status, 1));
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gn, g->gn_dev, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gtrace2, g->gtrace2_dev, G * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, st));
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gtrace, g->gtrace_dev, G * sizeof(double),
                                   cudaMemcpyDeviceToDevice, st));
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gbound, g->gbound_dev, G * sizeof(double),

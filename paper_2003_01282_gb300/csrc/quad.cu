@@ -405,6 +405,86 @@ __global__ void __launch_bounds__(kTT * kPG)
   }
 }
 
+// Heat trace with the polynomial control variate (Sec. 3.1, "2-term
+// polynomial" variance reduction; reading: Chebyshev interpolant of degree
+// DEG of f_t(x) = exp(-t x) on [0, bound_g]).  The Gauss rule of every probe
+// is exact for p_t, so subtracting sum_k tau2 p_t(theta_k) from each probe's
+// estimate and adding the exact c0 n + c1 tr L + c2 tr L^2 leaves the mean
+// unbiased and removes the part of its variance p_t explains.  Same block
+// layout and fixed-order Welford/Chan combination as k_trace_t.
+template <bool F32>
+__global__ void __launch_bounds__(kTT * kPG)
+    k_trace_cv(const double *__restrict__ theta, const double *__restrict__ tau2,
+               const int32_t *__restrict__ mm, int nv, int s, const double *__restrict__ gn,
+               const double *__restrict__ gtrace, const double *__restrict__ gtrace2,
+               const double *__restrict__ gbound, int degree, const double *__restrict__ t,
+               int nt, double *out, double *se, double *per_probe) {
+  __shared__ double sh_mean[kPG][kTT], sh_m2[kPG][kTT];
+  __shared__ int sh_cnt[kPG][kTT];
+  const int tt = threadIdx.x % kTT, pg = threadIdx.x / kTT;
+  const int ti = blockIdx.x * kTT + tt;
+  const int gr = blockIdx.y;
+  double mean = 0.0, m2 = 0.0, exact_part = 0.0;
+  int cnt = 0;
+  if (ti < nt) {
+    const double tv = t[ti];
+    const double n = gn[gr], b = gbound[gr];
+    // Chebyshev nodes of [0, b] and Newton divided differences of f there
+    const double pi = 3.141592653589793;
+    double c0, c1, c2 = 0.0;
+    if (degree == 1) {
+      const double x0 = 0.5 * b * (1.0 + cos(0.25 * pi)), x1 = 0.5 * b * (1.0 + cos(0.75 * pi));
+      const double f0 = exp(-tv * x0), f1 = exp(-tv * x1);
+      c1 = (f1 - f0) / (x1 - x0);
+      c0 = f0 - c1 * x0;
+    } else {
+      const double x0 = 0.5 * b * (1.0 + cos(pi / 6.0)), x1 = 0.5 * b,
+                   x2 = 0.5 * b * (1.0 + cos(5.0 * pi / 6.0));
+      const double f0 = exp(-tv * x0), f1 = exp(-tv * x1), f2 = exp(-tv * x2);
+      const double d01 = (f1 - f0) / (x1 - x0), d12 = (f2 - f1) / (x2 - x1);
+      const double d012 = (d12 - d01) / (x2 - x0);
+      c2 = d012;
+      c1 = d01 - d012 * (x0 + x1);
+      c0 = f0 - d01 * x0 + d012 * x0 * x1;
+    }
+    exact_part = c0 * n + c1 * gtrace[gr] + c2 * gtrace2[gr];
+    for (int p = pg; p < nv; p += kPG) {
+      const int64_t q = (int64_t)gr * nv + p;
+      double acc = 0.0;
+      const int m = mm[q];
+      for (int k = 0; k < m; ++k) {
+        const double th = theta[q * s + k];
+        acc += tau2[q * s + k] * (fval<0, F32>(tv, th) - (c0 + th * (c1 + th * c2)));
+      }
+      const double x = n * acc;
+      if (per_probe) per_probe[q * nt + ti] = x + exact_part;
+      ++cnt;
+      const double d = x - mean;
+      mean += d / cnt;
+      m2 += d * (x - mean);
+    }
+  }
+  sh_mean[pg][tt] = mean;
+  sh_m2[pg][tt] = m2;
+  sh_cnt[pg][tt] = cnt;
+  __syncthreads();
+  if (pg == 0 && ti < nt) {
+    double M = sh_mean[0][tt], S2 = sh_m2[0][tt];
+    int N = sh_cnt[0][tt];
+    for (int h = 1; h < kPG; ++h) {
+      const int nb = sh_cnt[h][tt];
+      if (nb == 0) continue;
+      const double delta = sh_mean[h][tt] - M;
+      const int nn = N + nb;
+      M += delta * nb / nn;
+      S2 += sh_m2[h][tt] + delta * delta * ((double)N * nb / nn);
+      N = nn;
+    }
+    out[(int64_t)gr * nt + ti] = M + exact_part;
+    if (se) se[(int64_t)gr * nt + ti] = nv > 1 ? sqrt(S2 / (nv - 1) / nv) : nan("");
+  }
+}
+
 // VNGE of graph blockIdx.x: f(theta) = -(theta/c) ln(theta/c) for theta > 0,
 // else 0, with c = tr(L_g).
 __global__ void k_vnge(const double *__restrict__ theta, const double *__restrict__ tau2,
@@ -505,6 +585,25 @@ int trace_heat(slaq_krylov K, const double *t, int nt, double *out, double *se, 
     k_trace_t<0, true><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
                                                     t, nt, out, se, per_probe);
   SLAQ_CHECK_LAUNCH("trace_heat");
+  return SLAQ_OK;
+}
+
+int trace_heat_cv(slaq_krylov K, const double *t, int nt, int degree, double *out, double *se,
+                  double *per_probe, cudaStream_t st) {
+  if (nt < 1 || !t || !out) return set_error(SLAQ_EINVAL, "heat trace needs t, nt >= 1 and out");
+  if (degree != 1 && degree != 2) return set_error(SLAQ_EINVAL, "control-variate degree must be 1 or 2");
+  ProfScope prof(SLAQ_PROF_TRACE, st);
+  ++tl_launches;
+  const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
+  if (K->precision == SLAQ_FP64)
+    k_trace_cv<false><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn,
+                                                   K->gtrace, K->gtrace2, K->gbound, degree, t, nt,
+                                                   out, se, per_probe);
+  else
+    k_trace_cv<true><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn,
+                                                  K->gtrace, K->gtrace2, K->gbound, degree, t, nt,
+                                                  out, se, per_probe);
+  SLAQ_CHECK_LAUNCH("trace_heat_cv");
   return SLAQ_OK;
 }
 

@@ -54,6 +54,7 @@ _SIGNATURES = {
     "slaq_ritz_export": (_I, [_VP, _VP, _VP, _VP]),
     "slaq_krylov_info": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_trace_heat": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
+    "slaq_trace_heat_cv": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP, _VP]),
     "slaq_trace_wave": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _VP]),
     "slaq_trace_vnge": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_krylov_destroy": (None, [_VP]),
@@ -317,6 +318,19 @@ def trace_heat(k, t, per_probe: bool = False, stream=None):
     pp = torch.empty(*lead, krylov_info(k)["nv"], nt, dtype=torch.float64, device="cuda") if per_probe else None
     _check(lib().slaq_trace_heat(_handle(k), _dev(t, torch.float64, "t"), nt, _dev(out), _dev(se),
                                  _dev(pp), _stream(stream)))
+    return (out, se, pp) if per_probe else (out, se)
+
+
+def trace_heat_cv(k, t, degree: int = 2, per_probe: bool = False, stream=None):
+    """slaq_trace_heat_cv: the heat trace with the polynomial control variate."""
+    torch = _torch()
+    nt = int(t.numel())
+    lead = _lead(k)
+    out = torch.empty(*lead, nt, dtype=torch.float64, device="cuda")
+    se = torch.empty_like(out)
+    pp = torch.empty(*lead, krylov_info(k)["nv"], nt, dtype=torch.float64, device="cuda") if per_probe else None
+    _check(lib().slaq_trace_heat_cv(_handle(k), _dev(t, torch.float64, "t"), nt, int(degree), _dev(out),
+                                    _dev(se), _dev(pp) if per_probe else None, _stream(stream)))
     return (out, se, pp) if per_probe else (out, se)
 
 
