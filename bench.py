@@ -204,8 +204,8 @@ class ClockSampler:
 # profiles/kernels_rmat20_fp32_k16.md; it describes the kernels only while
 # csrc/lanczos.cu is byte-identical to the source that was captured.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1955673000 + 351422720 + 562093000 + 8338688,
-    "source_sha256": "315eab6af78f98e929b6bed21057a7f43477ad0155745faffbb070c1dadbfa7e",
+    "bytes_per_spmm": 1952708000 + 349582848 + 561009000 + 8092416,
+    "source_sha256": "61787838c1a6d2e9b636444909c73e8f98f54f9baede8d33ded55e2b9905d172",
 }
 
 
@@ -508,6 +508,28 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks.summary(tw0, tw1),
     }
+
+    # the polynomial control variate on the last step's Lanczos run: standard
+    # errors against the plain estimate at a few t, and the kernel's time
+    if not args.quick:
+        K = state["K"]
+        tcv = torch.as_tensor([0.01, 0.1, 1.0, 10.0], device=dev, dtype=torch.float64)
+        _, se_plain = slaq.trace_heat(K, tcv)
+        out = {}
+        for degree in (1, 2):
+            slaq.trace_heat_cv(K, t, degree)
+            torch.cuda.synchronize(dev)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            slaq.trace_heat_cv(K, t, degree)
+            c1.record(stream)
+            torch.cuda.synchronize(dev)
+            _, se_cv = slaq.trace_heat_cv(K, tcv, degree)
+            out[f"degree_{degree}"] = {
+                "stderr_ratio_plain_over_cv": dict(zip(["t=0.01", "t=0.1", "t=1", "t=10"],
+                                                       (se_plain / se_cv).cpu().tolist())),
+                "ms_256_t": c0.elapsed_time(c1)}
+        result["variance_reduction"] = out
 
     # FP64 form beside it: time and error of the headline form against it
     if prec != "fp64" and not args.quick:

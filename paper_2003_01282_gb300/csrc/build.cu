@@ -360,14 +360,15 @@ __global__ void k_union_ids(const int32_t *src, const int32_t *dst, const double
 // per-graph statistics: kept nodes, non-isolated nodes, integer degree sum,
 // largest degree (non-negative doubles order like their bit patterns).  One
 // thread per node; a warp whose nodes share one graph adds its sums once.
-__global__ void k_node_graph(const int64_t *old_id, const double *deg, int64_t n,
-                             const int64_t *node_off, int G, int32_t *gid, int64_t *local,
-                             unsigned long long *kept, unsigned long long *nonisol,
-                             unsigned long long *degsum, unsigned long long *maxdeg) {
+__global__ void k_node_graph(const int64_t *old_id, const double *deg, const int64_t *rowptr,
+                             int64_t n, const int64_t *node_off, int G, int32_t *gid,
+                             int64_t *local, unsigned long long *kept,
+                             unsigned long long *nonisol, unsigned long long *degsum,
+                             unsigned long long *maxdeg, unsigned long long *entries) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool valid = i < n;
   int g = -1;
-  unsigned long long c_kept = 0, c_non = 0, c_sum = 0, c_max = 0;
+  unsigned long long c_kept = 0, c_non = 0, c_sum = 0, c_max = 0, c_ent = 0;
   if (valid) {
     g = find_segment(node_off, G, old_id[i]);
     gid[i] = g;
@@ -377,6 +378,7 @@ __global__ void k_node_graph(const int64_t *old_id, const double *deg, int64_t n
     c_non = d > 0.0 ? 1 : 0;
     c_sum = (unsigned long long)d;
     c_max = (unsigned long long)__double_as_longlong(d);
+    c_ent = (unsigned long long)(rowptr[i + 1] - rowptr[i]);
   }
   const int g0 = __shfl_sync(0xffffffffu, g, 0);
   const bool uniform = __all_sync(0xffffffffu, !valid || g == g0) && g0 >= 0;
@@ -386,6 +388,7 @@ __global__ void k_node_graph(const int64_t *old_id, const double *deg, int64_t n
       c_kept += __shfl_down_sync(0xffffffffu, c_kept, o);
       c_non += __shfl_down_sync(0xffffffffu, c_non, o);
       c_sum += __shfl_down_sync(0xffffffffu, c_sum, o);
+      c_ent += __shfl_down_sync(0xffffffffu, c_ent, o);
       const unsigned long long other = __shfl_down_sync(0xffffffffu, c_max, o);
       c_max = other > c_max ? other : c_max;
     }
@@ -394,12 +397,14 @@ __global__ void k_node_graph(const int64_t *old_id, const double *deg, int64_t n
       if (c_non) atomicAdd(nonisol + g0, c_non);
       atomicAdd(degsum + g0, c_sum);
       atomicMax(maxdeg + g0, c_max);
+      atomicAdd(entries + g0, c_ent);
     }
   } else if (valid) {
     atomicAdd(kept + g, c_kept);
     if (c_non) atomicAdd(nonisol + g, c_non);
     atomicAdd(degsum + g, c_sum);
     atomicMax(maxdeg + g, c_max);
+    atomicAdd(entries + g, c_ent);
   }
 }
 
@@ -539,29 +544,30 @@ __global__ void k_scale(const double *deg, int64_t n, int kind, double *scale, d
   }
 }
 
-// One thread per stored entry; its row and column come from the sorted key.
-// tr(L_g^2) = sum_ij (L_g)_ij^2 of every graph: one block per graph, rows
-// strided over the threads (each row summed in column order), the threads'
-// compensated sums combined in a fixed tree order (deterministic).
+// tr(L_g^2) = sum_ij (L_g)_ij^2 of every graph, in two deterministic levels.
+// A graph's rows are contiguous, so its diagonal (n_g values) and its stored
+// off-diagonal entries (E_g values) are two contiguous ranges.  Level 1 cuts
+// both ranges into chunks of kSqChunk values, one block per chunk: each
+// thread sums the squares of a fixed strided subset of 32 values with FP64
+// FMAs (relative error <= 32 eps; a compensated add per value would make the
+// kernel FP64-ALU-bound) and the threads combine in a fixed tree order.
+// Level 2: one block per graph adds its chunks' partials, Neumaier-compensated
+// per thread, in a fixed tree.  The result depends on neither the scheduling
+// nor the number of SMs, and chunks of equal size balance graphs with a few
+// very long rows.
 constexpr int kSqThreads = 256;
-__global__ void __launch_bounds__(kSqThreads)
-    k_graph_sq(const int64_t *rowptr, const double *vals, const double *diag,
-               const int64_t *goff, double *out) {
-  __shared__ double ssum[kSqThreads], scmp[kSqThreads];
-  const int gr = blockIdx.x;
-  double sm = 0.0, cp = 0.0;  // Neumaier
-  auto add = [&](double x) {
+constexpr int kSqChunk = 8192;
+struct Neumaier {
+  double sm = 0.0, cp = 0.0;
+  __device__ void add(double x) {
     const double t = sm + x;
     cp += fabs(sm) >= fabs(x) ? (sm - t) + x : (x - t) + sm;
     sm = t;
-  };
-  for (int64_t i = goff[gr] + threadIdx.x; i < goff[gr + 1]; i += kSqThreads) {
-    double r = diag[i] * diag[i];
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) r += vals[e] * vals[e];
-    add(r);
   }
-  ssum[threadIdx.x] = sm;
-  scmp[threadIdx.x] = cp;
+};
+__device__ double block_tree_sum(Neumaier acc, double *ssum, double *scmp) {
+  ssum[threadIdx.x] = acc.sm;
+  scmp[threadIdx.x] = acc.cp;
   __syncthreads();
   for (int w = kSqThreads / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
@@ -570,7 +576,54 @@ __global__ void __launch_bounds__(kSqThreads)
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[gr] = ssum[0] + scmp[0];
+  return ssum[0] + scmp[0];
+}
+// Graph q owns blocks coff[q] .. coff[q+1]-1: first its diagonal chunks, then
+// its entry chunks (graphs without rows own none).  goff / eoff: first row /
+// first stored entry of every graph.
+__global__ void __launch_bounds__(kSqThreads)
+    k_graph_sq_chunks(const double *vals, const double *diag, const int64_t *goff,
+                      const int64_t *eoff, const int64_t *coff, int G, double *partial) {
+  __shared__ double ssum[kSqThreads], scmp[kSqThreads];
+  const int64_t b = blockIdx.x;
+  const int q = find_segment(coff, G, b);
+  const int64_t j = b - coff[q];
+  const int64_t n_diag = (goff[q + 1] - goff[q] + kSqChunk - 1) / kSqChunk;
+  const double *x;
+  int64_t lo, hi;
+  if (j < n_diag) {
+    x = diag;
+    lo = goff[q] + j * kSqChunk;
+    hi = min(lo + kSqChunk, goff[q + 1]);
+  } else {
+    x = vals;
+    lo = eoff[q] + (j - n_diag) * kSqChunk;
+    hi = min(lo + kSqChunk, eoff[q + 1]);
+  }
+  double sq = 0.0;
+  for (int64_t i0 = lo + threadIdx.x; i0 < hi; i0 += 4 * kSqThreads) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + (int64_t)u * kSqThreads;
+      v[u] = i < hi ? x[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sq = fma(v[u], v[u], sq);
+  }
+  Neumaier acc;
+  acc.sm = sq;
+  const double v = block_tree_sum(acc, ssum, scmp);
+  if (threadIdx.x == 0) partial[b] = v;
+}
+__global__ void __launch_bounds__(kSqThreads)
+    k_graph_sq_sum(const double *partial, const int64_t *coff, double *out) {
+  __shared__ double ssum[kSqThreads], scmp[kSqThreads];
+  const int q = blockIdx.x;
+  Neumaier acc;
+  for (int64_t c = coff[q] + threadIdx.x; c < coff[q + 1]; c += kSqThreads) acc.add(partial[c]);
+  const double v = block_tree_sum(acc, ssum, scmp);
+  if (threadIdx.x == 0) out[q] = v;
 }
 
 // Batches: first union id of the graph of every input node (keys carry
@@ -999,20 +1052,21 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   // per-graph bookkeeping: graph of each kept node, kept counts, traces, bounds
   int32_t *gid = nullptr;
   int64_t *local = nullptr;
-  unsigned long long *stats = nullptr;  // [4][G]: kept, non-isolated, degree sum, max degree
+  // [5][G]: kept, non-isolated, degree sum, max degree, stored entries
+  unsigned long long *stats = nullptr;
   SLAQ_TRY(tmp.get(&gid, n_out));
   SLAQ_TRY(tmp.get(&local, n_out));
-  SLAQ_TRY(tmp.get(&stats, 4 * (size_t)G));
-  SLAQ_CHECK_CUDA(cudaMemsetAsync(stats, 0, 4 * (size_t)G * sizeof(unsigned long long), st));
+  SLAQ_TRY(tmp.get(&stats, 5 * (size_t)G));
+  SLAQ_CHECK_CUDA(cudaMemsetAsync(stats, 0, 5 * (size_t)G * sizeof(unsigned long long), st));
   if (n_out > 0) {
     ++tl_launches;
-    k_node_graph<<<(unsigned)ceil_div(n_out, 256), 256, 0, st>>>(g->old_id, deg, n_out, d_node_off, G, gid,
-                                                       local, stats, stats + G, stats + 2 * G,
-                                                       stats + 3 * G);
+    k_node_graph<<<(unsigned)ceil_div(n_out, 256), 256, 0, st>>>(
+        g->old_id, deg, g->rowptr, n_out, d_node_off, G, gid, local, stats, stats + G,
+        stats + 2 * G, stats + 3 * G, stats + 4 * G);
     SLAQ_CHECK_LAUNCH("node_graph");
   }
-  std::vector<unsigned long long> hst(4 * (size_t)G);
-  SLAQ_TRY(to_host(hst.data(), stats, 4 * (size_t)G, st));
+  std::vector<unsigned long long> hst(5 * (size_t)G);
+  SLAQ_TRY(to_host(hst.data(), stats, 5 * (size_t)G, st));
   g->n_graphs = G;
   g->goff.assign(G + 1, 0);
   g->gtrace.assign(G, 0.0);
@@ -1061,10 +1115,33 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
                                cudaMemcpyHostToDevice));
     // tr(L_g^2) for the polynomial control variate of the heat trace
     SLAQ_TRY(persistent(&g->gtrace2_dev, G));
+    // offs = [coff | eoff]: first chunk and first stored entry of every graph
+    std::vector<int64_t> offs(2 * ((size_t)G + 1), 0);
+    int64_t *coff = offs.data(), *eoff = coff + G + 1;
+    for (int q = 0; q < G; ++q) {
+      const int64_t e = (int64_t)hst[4 * (size_t)G + q];
+      eoff[q + 1] = eoff[q] + e;
+      coff[q + 1] = coff[q] + ceil_div(g->goff[q + 1] - g->goff[q], kSqChunk) + ceil_div(e, kSqChunk);
+    }
+    if (eoff[G] != nnz)
+      return set_error(SLAQ_EINVAL, "internal: stored entries per graph sum to %lld, not %lld",
+                       (long long)eoff[G], (long long)nnz);
+    const int64_t n_chunks = coff[G];
+    int64_t *d_offs = nullptr;
+    double *partial = nullptr;
+    SLAQ_TRY(tmp.get(&d_offs, offs.size()));
+    SLAQ_TRY(tmp.get(&partial, std::max<int64_t>(n_chunks, 1)));
+    SLAQ_CHECK_CUDA(cudaMemcpy(d_offs, offs.data(), offs.size() * sizeof(int64_t),
+                               cudaMemcpyHostToDevice));
+    if (n_chunks > 0) {
+      ++tl_launches;
+      k_graph_sq_chunks<<<(unsigned)n_chunks, kSqThreads, 0, st>>>(
+          g->vals, g->diag, g->goff_dev, d_offs + G + 1, d_offs, G, partial);
+      SLAQ_CHECK_LAUNCH("graph_sq_chunks");
+    }
     ++tl_launches;
-    k_graph_sq<<<(unsigned)G, kSqThreads, 0, st>>>(g->rowptr, g->vals, g->diag, g->goff_dev,
-                                                   g->gtrace2_dev);
-    SLAQ_CHECK_LAUNCH("graph_sq");
+    k_graph_sq_sum<<<(unsigned)G, kSqThreads, 0, st>>>(partial, d_offs, g->gtrace2_dev);
+    SLAQ_CHECK_LAUNCH("graph_sq_sum");
     g->gtrace2.assign(G, 0.0);
     SLAQ_TRY(to_host(g->gtrace2.data(), g->gtrace2_dev, G, st));
   }

@@ -38,6 +38,9 @@ CASES = {
     "islands": (lambda: synth.disjoint_union(synth.erdos_renyi(300, 0.03, 1), synth.cycle(17),
                                               extra_isolated=9), NORMALIZED, False, None),
     "ba_comb_w": (lambda: synth.barabasi_albert(800, 3, seed=5), COMBINATORIAL, False, 7),
+    # tr L^2 is summed in chunks of 8192 values: three diagonal chunks (the
+    # last ragged) and several entry chunks
+    "ba20000": (lambda: synth.barabasi_albert(20000, 2, seed=8), NORMALIZED, False, None),
 }
 
 
@@ -65,15 +68,20 @@ def test_cv_matches_oracle(name, degree):
 
 
 def test_cv_batch_per_graph():
+    empty = (np.zeros(0, np.int32), np.zeros(0, np.int32), 4)  # all nodes dropped
     graphs = [synth.barabasi_albert(300, 3, seed=1), synth.sbm([40, 40, 41], 0.3, 0.02, seed=2),
-              synth.cycle(17), synth.rmat(11, 8 << 11, seed=4)]
+              empty, synth.cycle(17), synth.rmat(11, 8 << 11, seed=4),
+              synth.barabasi_albert(9000, 3, seed=7)]  # 2 diagonal chunks of tr L^2
     gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
     nv, steps, seed = 6, 10, 5
     K = slaq.lanczos(gb, nv, steps, seed, precision=slaq.FP64)
     t = synth.t_grid(32)
     h = slaq.trace_heat_cv(K, _dev(t, torch.float64), 2)[0].cpu().numpy()
     assert h.shape == (len(graphs), t.size)
+    assert np.all(h[2] == 0.0)
     for gi, (s, d, n) in enumerate(graphs):
+        if gi == 2:
+            continue
         lap = build_laplacian(s, d, n, drop_isolated=True)
         runs = odesc.slq_runs(lap, steps, nv, seed, graph=gi)
         oh, _ = ovar.heat_trace_cv(runs, lap.n, t, 2, lap.norm_bound(), lap.trace,
