@@ -17,7 +17,10 @@ Modules and the passages they follow
                Rademacher signs from a SplitMix64 counter-based generator.
 ``lanczos``    Sec. 3.1: s-step Lanczos giving the tridiagonal T = Q^T L Q,
                with one classical Gram-Schmidt pass against all previous
-               Lanczos vectors after the three-term update.
+               Lanczos vectors after the three-term update; and Lanczos with
+               partial reorthogonalization (Simon's omega-recurrence; not in
+               the paper), which reorthogonalizes only when the estimated
+               loss of orthogonality passes sqrt(eps).
 ``quadrature`` Eq. quadratic and Eq. slq, Algorithm 1: eigh(T) gives nodes
                theta and weights tau^2 (first eigenvector components);
                Hutchinson mean over probes.

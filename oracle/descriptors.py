@@ -34,14 +34,20 @@ class ProbeResult:
 
 
 def slq_runs(lap, s: int, n_v: int, seed: int, graph: int = 0, reorth_passes: int = 1,
-             tol: float = _lz.DEFAULT_TOL["fp64"], probes=None) -> list[ProbeResult]:
-    """Lanczos + Gauss rule for probes ``probes`` (default: 0..n_v-1)."""
+             tol: float = _lz.DEFAULT_TOL["fp64"], probes=None,
+             partial: bool = False) -> list[ProbeResult]:
+    """Lanczos + Gauss rule for probes ``probes`` (default: 0..n_v-1);
+    ``partial`` runs Lanczos with partial reorthogonalization instead of
+    ``reorth_passes`` Gram-Schmidt passes per step."""
     L = lap.matrix()
     bound = lap.norm_bound()
     out = []
     for p in (range(n_v) if probes is None else probes):
         v = _pr.rademacher(seed, graph, p, lap.old_id)
-        run = _lz.lanczos(L, v, s, bound, reorth_passes=reorth_passes, tol=tol)
+        if partial:
+            run = _lz.lanczos_partial(L, v, s, bound, tol=tol)
+        else:
+            run = _lz.lanczos(L, v, s, bound, reorth_passes=reorth_passes, tol=tol)
         theta, tau2 = _qd.ritz(run.alpha, run.beta)
         out.append(ProbeResult(run.alpha, run.beta, run.m, theta, tau2))
     return out
