@@ -11,7 +11,10 @@ One step = the whole path on device-resident edges: Laplacian build, Lanczos
 the distance of the heat trace to a stored signature.  The metric is
 probe-edges per second: nnz * nv * s per step.  The headline form computes
 the Lanczos iteration in FP32 (alpha/beta reductions, eigensolve and
-quadrature in FP64); the FP64 form is timed beside it.
+quadrature in FP64).  Timed beside it, each with its error against the FP64
+form: the FP64 form, the BF16-basis form, and both FP32 and FP64 with
+partial reorthogonalization; the heat-trace control variate's standard
+errors; the 5000-graph SBM batch (graphs/s); the host-memory entry point.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -204,8 +207,8 @@ class ClockSampler:
 # profiles/kernels_rmat20_fp32_k16.md; it describes the kernels only while
 # csrc/lanczos.cu is byte-identical to the source that was captured.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1952708000 + 349582848 + 561009000 + 8092416,
-    "source_sha256": "61787838c1a6d2e9b636444909c73e8f98f54f9baede8d33ded55e2b9905d172",
+    "bytes_per_spmm": 1954789000 + 350599680 + 561229000 + 8384256,
+    "source_sha256": "c1aee8fdb04d0917beec216305a9c01e682b372fa1321ea92cfff723002525e2",
 }
 
 
@@ -410,9 +413,10 @@ def run_ours(args):
 
     state = {"K": None, "ref": None}
 
-    def step(precision=P, key="K"):
+    def step(precision=P, key="K", reorth=1):
         g = slaq.build_laplacian(src, dst, n_nodes, kind=slaq.NORMALIZED, flags=slaq.DROP_ISOLATED)
-        state[key] = slaq.lanczos(g, NV, S, seed, precision=precision, reuse=state.get(key))
+        state[key] = slaq.lanczos(g, NV, S, seed, precision=precision, reorth_passes=reorth,
+                                  reuse=state.get(key))
         K = state[key]
         heat, _ = slaq.trace_heat(K, t)
         (wr, _), (wi, _) = slaq.trace_wave(K, t)
@@ -560,6 +564,31 @@ def run_ours(args):
             result["bf16_form"] = {"ms_per_step": msbf, "value": world * pe_step / (msbf * 1e-3),
                                    "speedup_over_fp64_form": ms64 / msbf,
                                    "rel_err_vs_fp64": rel_errors(dbf.cpu().numpy(), b, t_np)}
+        # partial reorthogonalization (FP32 and FP64 forms): time, the
+        # Lanczos kernels' time, how many steps projected against the whole
+        # basis, and the error against the FP64 form with full reorthogonalization
+        pr = {}
+        for name, pp, ms_full in (("fp32", slaq.FP32, ms if prec == "fp32" else None),
+                                  ("fp64", slaq.FP64, ms64)):
+            key = "Kp" + name
+            step(pp, key, slaq.REORTH_PARTIAL)
+            torch.cuda.synchronize(dev)
+            slaq.profile_enable(True)
+            e0.record(stream)
+            for _ in range(2):
+                dp, _, _ = step(pp, key, slaq.REORTH_PARTIAL)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            kp = slaq.profile_read()
+            slaq.profile_enable(False)
+            msp = e0.elapsed_time(e1) / 2
+            fs = slaq.krylov_full_steps(state[key]).cpu().numpy()
+            pr[name] = {"ms_per_step": msp, "value": world * pe_step / (msp * 1e-3),
+                        "speedup_over_full_reorth": (ms_full / msp) if ms_full else None,
+                        "dots_update_ms_per_step": (kp["dots"][0] + kp["update"][0]) / 2,
+                        "full_projection_steps": int(fs.sum()), "of_steps": S - 1,
+                        "rel_err_vs_fp64": rel_errors(dp.double().cpu().numpy(), b, t_np)}
+        result["partial_reorth"] = pr
 
     # end to end through the host-memory entry point (pinned buffers)
     if not args.quick:

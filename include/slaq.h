@@ -54,6 +54,8 @@ enum { SLAQ_DROP_ISOLATED = 1 };
  *   SLAQ_FP32           basis, SpMM and reorthogonalization in FP32;
  *   SLAQ_FP32_BF16BASIS basis stored in BF16, SpMM and updates in FP32.   */
 enum { SLAQ_FP64 = 0, SLAQ_FP32 = 1, SLAQ_FP32_BF16BASIS = 2 };
+/* reorth_passes value for partial reorthogonalization (slaq_lanczos). */
+enum { SLAQ_REORTH_PARTIAL = 0 };
 /* Distance kinds. */
 enum { SLAQ_DIST_HEAT = 0, SLAQ_DIST_WAVE = 1, SLAQ_DIST_VNGE = 2 };
 
@@ -144,7 +146,19 @@ void slaq_graph_destroy(slaq_graph g);
  *   (-1 where bit 63 is set); the starting vector is that sign vector / sqrt(n').
  *   Every step orthogonalizes the new vector against all previous Lanczos
  *   vectors of its probe by classical Gram-Schmidt (reorth_passes = 1) or
- *   twice (2).  A probe whose beta_k falls to tol * bound (tol 1e-10 FP64,
+ *   twice (2).  reorth_passes = SLAQ_REORTH_PARTIAL (0) is partial
+ *   reorthogonalization (not in the paper; Simon, Math. Comp. 42, 1984):
+ *   a step projects the new vector on the previous two only, and every probe
+ *   estimates the loss of orthogonality omega_{k,j} ~ q_k^T q_j of its basis
+ *   by the recurrence that the symmetry of L imposes on it (measured from
+ *   the Gram column on steps that project on all vectors).  When a probe's
+ *   max_j |omega_{k,j}| passes sqrt(eps) (eps = 2^-53 FP64, 2^-24 FP32), the
+ *   next two steps of its graph project against all previous vectors.  The
+ *   Gauss rule then comes from the recurrence's T in both forms.  It needs a
+ *   host read of one flag per step (the call does not return before the
+ *   last step is enqueued); SLAQ_FP32_BF16BASIS with it: SLAQ_EUNSUPPORTED
+ *   (BF16 storage rounds at 2^-9, above the FP32 semi-orthogonality level).
+ *   A probe whose beta_k falls to tol * bound (tol 1e-10 FP64,
  *   1e-4 FP32 and BF16 basis; bound 2 or 2 max d) stops with m = k+1.
  *   1 <= nv <= 512, 1 <= s <= 64, precision one of SLAQ_FP64/FP32/
  *   FP32_BF16BASIS, graph_id + (graphs in g) - 1 < 65536; the projection
@@ -188,10 +202,18 @@ int slaq_probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, 
 
 /* Device copies of alpha float64[nv*s] (row p holds alpha_0..alpha_{m_p-1}),
  * beta float64[nv*s] (beta_0..beta_{m_p-2}) and m int32[nv].  NULL skips.
- * For the FP32 and BF16-basis forms alpha and beta are the diagonal and
- * off-diagonal of the tridiagonal form of the Rayleigh-Ritz matrix (the T
- * whose Gauss rule the traces use). */
+ * For the FP32 and BF16-basis forms with full reorthogonalization alpha and
+ * beta are the diagonal and off-diagonal of the tridiagonal form of the
+ * Rayleigh-Ritz matrix (the T whose Gauss rule the traces use); with partial
+ * reorthogonalization they are the recurrence's, as in SLAQ_FP64. */
 int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, void *stream);
+
+/* Which Lanczos steps projected against all previous vectors: full_steps
+ * int32[G][s] on the device, 1 where step k of graph g did (every step with
+ * reorth_passes 1 or 2, and steps 0 and 1, whose previous vectors are the
+ * local pair), else 0 (partial reorthogonalization only).  Steps after a
+ * graph's last probe stopped read 0. */
+int slaq_krylov_full_steps(slaq_krylov k, int32_t *full_steps, void *stream);
 
 /* Device copies of the Gauss nodes theta float64[nv*s] (ascending within a
  * probe's first m_p entries) and weights tau2 float64[nv*s]. */

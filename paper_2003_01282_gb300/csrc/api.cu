@@ -293,6 +293,13 @@ int slaq_probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, 
   return probes(g, nv, seed, graph_id, out, as_stream(stream));
 }
 
+int slaq_krylov_full_steps(slaq_krylov k, int32_t *full_steps, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  SLAQ_TRY(slaq::full_steps(k, full_steps, as_stream(stream)));
+  return SLAQ_OK;
+}
+
 int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());

@@ -153,7 +153,7 @@ struct slaq_tuning {
 
 struct slaq_krylov_s {
   int device = -1;
-  int nv = 0, s = 0, ld = 0, precision = 0, reorth = 1;
+  int nv = 0, s = 0, ld = 0, precision = 0, reorth = 1;  // reorth 0: partial
   int graph_id = 0;
   uint64_t seed = 0;
   int64_t n = 0;          // n' of the last run
@@ -200,6 +200,16 @@ struct slaq_krylov_s {
   int32_t *d_rows = nullptr, *u_rows = nullptr, *u_graph = nullptr, *d_goff = nullptr;
   int64_t dcap = 0, ucap = 0;
   int n_dchunks = 0, n_uchunks = 0;
+  // partial reorthogonalization (reorth = 0): step k of graph g projects
+  // against all previous vectors if pro_full[g][k] (else only u_{k-1}, u_k);
+  // pro_any[k] = any graph's flag, read on the host through pro_any_host;
+  // omega[g][p][3][s] holds the estimates omega_{i,j} of the last three steps
+  int32_t *pro_full = nullptr;      // [G][s+2]
+  int32_t *pro_any = nullptr;       // [s+2]
+  int32_t *pro_any_host = nullptr;  // [s+2], pinned
+  double *omega = nullptr;          // [G][nv][3][s]
+  int64_t pro_gcap = 0;             // graphs the partial-reorthogonalization arrays hold
+  cudaEvent_t ev_flag = nullptr;    // after the copy of pro_any[k+1]
   // side stream on which the split-row SpMM runs beside the light rows
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -223,6 +233,7 @@ int lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t see
                     slaq_krylov *inout);
 void krylov_free(slaq_krylov k);
 int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st);
+int full_steps(slaq_krylov k, int32_t *out, cudaStream_t st);
 int run_ritz(slaq_krylov k, cudaStream_t st);
 int trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *se,
                double *per_probe, cudaStream_t st);

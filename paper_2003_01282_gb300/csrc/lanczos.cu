@@ -920,21 +920,83 @@ __global__ void k_dot_reduce_narrow(const double *__restrict__ part, const int32
 // writes the update's scale 1/||u_k|| to row s-1 of the coefficients (a row
 // no step's coefficients use: they fill rows 0..k <= s-2); 1 in the second
 // pass.  need_coef == 0 on the last step.
-__global__ void k_solve(const double *__restrict__ dsum_all, const double *__restrict__ gram_all,
+// Partial reorthogonalization (Simon, Math. Comp. 42, 1984; not in the
+// paper).  full == nullptr: every step projects against all previous vectors.
+// Otherwise step k of graph g projects against all of them if full[g][k]
+// (stride s + 2), else against u_{k-1} and u_k only; omega[g][p][k % 3][j]
+// holds the estimate omega_{k,j} ~ q_k^T q_j of the last three steps (with
+// omega_{k,k} = 1); eps is the unit roundoff of the basis arithmetic.
+struct ProArgs {
+  int32_t *full;
+  int32_t *any;
+  double *omega;
+  double eps;
+};
+
+// first basis vector step k of graph g projects against
+__device__ __forceinline__ int pro_first(const ProArgs &P, int g, int k, int s) {
+  return (P.full && !P.full[(int64_t)g * (s + 2) + k]) ? max(0, k - 1) : 0;
+}
+
+// Row k of the orthogonality estimates of problem (g, p), entries j = j_begin,
+// j_begin + j_step, ... < k; returns their largest |omega_{k,j}| over j <= k-2.
+// Steps whose Gram column covers every j (measured) take omega_{k,j} =
+// G_jk / sqrt(G_jj G_kk); the others take the recurrence that q_k^T L q_j =
+// q_j^T L q_k imposes,
+//   beta_{k-1} omega_{k,j} = beta_j omega_{k-1,j+1} + (alpha_j - alpha_{k-1}) omega_{k-1,j}
+//                            + beta_{j-1} omega_{k-1,j-1} - beta_{k-2} omega_{k-2,j}
+// plus eps (beta_{k-1} + beta_j) in the direction that grows |omega|, with
+// omega_{k,k-1} = eps (the local projection leaves u_k orthogonal to u_{k-1}
+// to rounding).  alpha, beta: this problem's rows (beta_{k-1} already set).
+__device__ double omega_row(const ProArgs &P, int64_t prob, int k, int s, bool measured,
+                            const double *alpha, const double *beta, const double *gram, int ld,
+                            int p, int j_begin, int j_step) {
+  double *om = P.omega + prob * 3 * s;
+  double *rk = om + (k % 3) * s;
+  const double *r1 = om + ((k + 2) % 3) * s;  // row k-1
+  const double *r2 = om + ((k + 1) % 3) * s;  // row k-2
+  const double bk1 = beta[k - 1];
+  double mx = 0.0;
+  for (int j = j_begin; j < k; j += j_step) {
+    double w;
+    if (measured) {
+      w = gram[((int64_t)j * s + k) * ld + p] *
+          rsqrt(gram[((int64_t)j * s + j) * ld + p] * gram[((int64_t)k * s + k) * ld + p]);
+    } else if (j == k - 1) {
+      w = P.eps;
+    } else {
+      double t = beta[j] * r1[j + 1] + (alpha[j] - alpha[k - 1]) * r1[j];
+      if (j > 0) t += beta[j - 1] * r1[j - 1];
+      if (k >= 2) t -= beta[k - 2] * r2[j];
+      t += copysign(P.eps * (bk1 + beta[j]), t);
+      w = t / bk1;
+    }
+    rk[j] = w;
+    if (j <= k - 2) mx = fmax(mx, fabs(w));
+  }
+  return mx;
+}
+
+// the next two steps of graph g project against all previous vectors
+__device__ __forceinline__ void pro_flag_next(const ProArgs &P, int g, int k, int s) {
+  int32_t *f = P.full + (int64_t)g * (s + 2);
+  f[k + 1] = 1;
+  f[k + 2] = 1;
+  P.any[k + 1] = 1;
+  P.any[k + 2] = 1;
+}
+
+__global__ void k_solve(const double *__restrict__ dsum_all, double *__restrict__ gram_all,
                         int k, int s, int ld, int nv, int first_pass, int need_coef, double tol,
                         const double *__restrict__ gbound, int32_t *__restrict__ m_all,
                         double *__restrict__ alpha_all, double *__restrict__ beta_all,
-                        double *__restrict__ coef_all) {
+                        double *__restrict__ coef_all, ProArgs P, int jl) {
   extern __shared__ double sol_smem[];  // A [K1*K1], y [K1], sc [K1]
   __shared__ int run_flag;
   const int p = blockIdx.x;
   const int gr = blockIdx.y;
-  const int K1 = k + 1;
-  double *A = sol_smem;
-  double *y = A + K1 * K1;
-  double *sc = y + K1;
   const int lane = threadIdx.x;
-  const double *gram = gram_all + (int64_t)gr * s * s * ld;
+  double *gram = gram_all + (int64_t)gr * s * s * ld;
   const double *dsum = dsum_all + (int64_t)gr * s * ld;
   double *coef = coef_all + (int64_t)gr * s * ld;
   int32_t *m = m_all + (int64_t)gr * nv;
@@ -959,19 +1021,41 @@ __global__ void k_solve(const double *__restrict__ dsum_all, const double *__res
     run_flag = running ? 1 : 0;
   }
   __syncthreads();
+  // partial reorthogonalization: this step projects on u_j, j >= j0, and
+  // knows the Gram entries (j, k) for j >= j1 (the rest are zeroed: unknown)
+  const int j0 = pro_first(P, gr, k, s);
+  const int j1 = max(j0, jl);
+  if (P.full && first_pass && p < nv) {
+    if (run_flag && k >= 1 && need_coef) {
+      double mx = omega_row(P, (int64_t)gr * nv + p, k, s, j1 == 0, alpha + (int64_t)p * s,
+                            beta + (int64_t)p * s, gram, ld, p, lane, 32);
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0 && mx > sqrt(P.eps)) pro_flag_next(P, gr, k, s);
+    }
+    if (run_flag && lane == 0) P.omega[(((int64_t)gr * nv + p) * 3 + k % 3) * s + k] = 1.0;
+    for (int j = lane; j < j1; j += 32) {
+      gram[((int64_t)j * s + k) * ld + p] = 0.0;
+      gram[((int64_t)k * s + j) * ld + p] = 0.0;
+    }
+  }
   if (!need_coef) return;
+  const int K1 = k + 1 - j0;  // the projection's basis vectors j0 .. k
+  double *A = sol_smem;
+  double *y = A + K1 * K1;
+  double *sc = y + K1;
   if (!run_flag) {
-    for (int j = lane; j < K1; j += blockDim.x) coef[j * ld + p] = 0.0;
+    for (int j = lane; j <= k; j += blockDim.x) coef[j * ld + p] = 0.0;
     return;
   }
+  for (int j = lane; j < j0; j += blockDim.x) coef[j * ld + p] = 0.0;
   for (int j = lane; j < K1; j += blockDim.x) {
-    sc[j] = rsqrt(gram[((int64_t)j * s + j) * ld + p]);
-    y[j] = dsum[j * ld + p];
+    sc[j] = rsqrt(gram[((int64_t)(j0 + j) * s + j0 + j) * ld + p]);
+    y[j] = dsum[(j0 + j) * ld + p];
   }
   __syncthreads();
   for (int e = lane; e < K1 * K1; e += blockDim.x) {
     const int i = e / K1, j = e - i * K1;
-    if (j <= i) A[i * K1 + j] = gram[((int64_t)i * s + j) * ld + p] * sc[i] * sc[j];
+    if (j <= i) A[i * K1 + j] = gram[((int64_t)(j0 + i) * s + j0 + j) * ld + p] * sc[i] * sc[j];
   }
   __syncthreads();
   // Cholesky of Ghat = D^-1/2 G D^-1/2 (unit diagonal), in place, right-looking:
@@ -1005,7 +1089,7 @@ __global__ void k_solve(const double *__restrict__ dsum_all, const double *__res
     for (int i = lane; i < c; i += 32) y[i] -= A[c * K1 + i] * y[c];
     __syncwarp();
   }
-  for (int j = lane; j < K1; j += blockDim.x) coef[j * ld + p] = y[j] * sc[j];
+  for (int j = lane; j < K1; j += blockDim.x) coef[(j0 + j) * ld + p] = y[j] * sc[j];
   // the update divides by ||u_k|| (first pass), so ||u_{k+1}|| = beta_k
   if (lane == 0)
     coef[(s - 1) * ld + p] = first_pass ? rsqrt(gram[((int64_t)k * s + k) * ld + p]) : 1.0;
@@ -1039,17 +1123,16 @@ __device__ __forceinline__ float rsq<float>(float x) {
 
 template <typename T>
 __global__ void __launch_bounds__(kSolveLanes)
-    k_solve_lanes(const double *__restrict__ dsum_all, const double *__restrict__ gram_all, int k,
+    k_solve_lanes(const double *__restrict__ dsum_all, double *__restrict__ gram_all, int k,
                   int s, int ld, int nv, int n_graphs, int first_pass, int need_coef, double tol,
                   const double *__restrict__ gbound, int32_t *__restrict__ m_all,
                   double *__restrict__ alpha_all, double *__restrict__ beta_all,
-                  double *__restrict__ coef_all) {
+                  double *__restrict__ coef_all, ProArgs P, int jl) {
   extern __shared__ __align__(16) unsigned char sl_dyn[];
   const int64_t t = (int64_t)blockIdx.x * kSolveLanes + threadIdx.x;
   if (t >= (int64_t)n_graphs * nv) return;  // no block-wide barrier below
   const int gr = (int)(t / nv), p = (int)(t - (int64_t)gr * nv);
-  const int K1 = k + 1;
-  const double *gram = gram_all + (int64_t)gr * s * s * ld;
+  double *gram = gram_all + (int64_t)gr * s * s * ld;
   const double *dsum = dsum_all + (int64_t)gr * s * ld;
   double *coef = coef_all + (int64_t)gr * s * ld;
   int32_t *m = m_all + (int64_t)gr * nv;
@@ -1067,23 +1150,40 @@ __global__ void __launch_bounds__(kSolveLanes)
     }
     if (running) alpha_all[((int64_t)gr * nv + p) * s + k] = dsum[k * ld + p] / nk;
   }
+  // partial reorthogonalization (see k_solve)
+  const int j0 = pro_first(P, gr, k, s);
+  const int j1 = max(j0, jl);
+  if (P.full && first_pass) {
+    const int64_t prob = (int64_t)gr * nv + p;
+    if (running && k >= 1 && need_coef &&
+        omega_row(P, prob, k, s, j1 == 0, alpha_all + prob * s, beta_all + prob * s, gram, ld, p,
+                  0, 1) > sqrt(P.eps))
+      pro_flag_next(P, gr, k, s);
+    if (running) P.omega[(prob * 3 + k % 3) * s + k] = 1.0;
+    for (int j = 0; j < j1; ++j) {
+      gram[((int64_t)j * s + k) * ld + p] = 0.0;
+      gram[((int64_t)k * s + j) * ld + p] = 0.0;
+    }
+  }
   if (!need_coef) return;
   if (!running) {
-    for (int j = 0; j < K1; ++j) coef[j * ld + p] = 0.0;
+    for (int j = 0; j <= k; ++j) coef[j * ld + p] = 0.0;
     return;
   }
+  for (int j = 0; j < j0; ++j) coef[j * ld + p] = 0.0;
+  const int K1 = k + 1 - j0;  // the projection's basis vectors j0 .. k
   T *A = reinterpret_cast<T *>(sl_dyn) + threadIdx.x;  // packed (i, j <= i)
   T *y = A + (size_t)kSolveLanes * (K1 * (K1 + 1) / 2);
   T *sc = y + (size_t)kSolveLanes * K1;
 #define SLAQ_A(i, j) A[(((i) * ((i) + 1)) / 2 + (j)) * kSolveLanes]
   for (int i = 0; i < K1; ++i) {
-    sc[i * kSolveLanes] = (T)rsqrt(gram[((int64_t)i * s + i) * ld + p]);
-    y[i * kSolveLanes] = (T)dsum[i * ld + p] * sc[i * kSolveLanes];
+    sc[i * kSolveLanes] = (T)rsqrt(gram[((int64_t)(j0 + i) * s + j0 + i) * ld + p]);
+    y[i * kSolveLanes] = (T)dsum[(j0 + i) * ld + p] * sc[i * kSolveLanes];
   }
   for (int i = 0; i < K1; ++i) {
     const T si = sc[i * kSolveLanes];
     for (int j = 0; j <= i; ++j)
-      SLAQ_A(i, j) = (T)gram[((int64_t)i * s + j) * ld + p] * si * sc[j * kSolveLanes];
+      SLAQ_A(i, j) = (T)gram[((int64_t)(j0 + i) * s + j0 + j) * ld + p] * si * sc[j * kSolveLanes];
   }
   // right-looking Cholesky, inverse pivots on the diagonal
   for (int c = 0; c < K1; ++c) {
@@ -1106,7 +1206,8 @@ __global__ void __launch_bounds__(kSolveLanes)
     for (int i = 0; i < c; ++i) y[i * kSolveLanes] -= SLAQ_A(c, i) * xc;
   }
 #undef SLAQ_A
-  for (int j = 0; j < K1; ++j) coef[j * ld + p] = (double)(y[j * kSolveLanes] * sc[j * kSolveLanes]);
+  for (int j = 0; j < K1; ++j)
+    coef[(j0 + j) * ld + p] = (double)(y[j * kSolveLanes] * sc[j * kSolveLanes]);
   coef[(s - 1) * ld + p] = first_pass ? rsqrt(gram[((int64_t)k * s + k) * ld + p]) : 1.0;
 }
 
@@ -1115,14 +1216,14 @@ __global__ void __launch_bounds__(kSolveLanes)
 // (first pass), or x = the stored u_{k+1} and zs = 1 (second pass, in
 // place), rounded to the basis type; stopped probes and padding columns get
 // 0.  A pure streaming pass over the basis.
-template <int P, bool SECOND>
+template <int P, bool SECOND, bool PARTIAL = false>
 __global__ void __launch_bounds__(512)
     k_update(const typename Form<P>::TB *__restrict__ U, const typename Form<P>::TW *__restrict__ Z,
              typename Form<P>::TB *Unext, Slc S, const int64_t *__restrict__ crow0,
              const int32_t *__restrict__ crows, const int32_t *__restrict__ cgraph, int V, int R,
              int64_t ustride, int k, int s, const double *__restrict__ coef_all,
              const int32_t *__restrict__ m_all, int nv, const typename Form<P>::TW *__restrict__ yscale,
-             typename Form<P>::TW *Ynext) {
+             typename Form<P>::TW *Ynext, const int32_t *__restrict__ pro_full) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -1147,6 +1248,9 @@ __global__ void __launch_bounds__(512)
   }
   const int64_t r0 = crow0[blockIdx.x];
   const int64_t r1 = r0 + crows[blockIdx.x];
+  // partial reorthogonalization: only u_{k-1} and u_k unless the graph's step is full
+  int j0 = 0;
+  if constexpr (PARTIAL) j0 = pro_full[(int64_t)gr * (s + 2) + k] ? 0 : max(0, k - 1);
   int stride;
   const int64_t off = S.base(lane * VE, stride);
   for (int64_t row = r0 + team; row < r1; row += R) {
@@ -1155,6 +1259,19 @@ __global__ void __launch_bounds__(512)
     if (SECOND) ldb_rw(Unext + o, x);
     else ldw<TW, VE>(Z + o, x);
     int j = 0;
+    if (PARTIAL && j0 > 0) {  // partial reorthogonalization step: u_{k-1} and u_k only
+      TW u0[VE], u1[VE];
+      ldb(U + (int64_t)(k - 1) * ustride + o, u0);
+      ldb(U + (int64_t)k * ustride + o, u1);
+      const TW *c0 = cf + (k - 1) * ld + lane * VE;
+      const TW *c1 = c0 + ld;
+#pragma unroll
+      for (int v = 0; v < VE; ++v) {
+        x[v] = fma(-c0[v], u0[v], x[v]);
+        x[v] = fma(-c1[v], u1[v], x[v]);
+      }
+      j = k + 1;
+    }
     for (; j + 2 <= k + 1; j += 2) {
       TW u0[VE], u1[VE];
       ldb(U + (int64_t)j * ustride + o, u0);
@@ -1402,10 +1519,24 @@ int dots(slaq_krylov K, const Geometry &geo, int64_t n, int k, int jfirst, int j
   return SLAQ_OK;
 }
 
+ProArgs pro_args(slaq_krylov K) {
+  ProArgs P{nullptr, nullptr, nullptr, 0.0};
+  if (K->reorth == 0) {
+    P.full = K->pro_full;
+    P.any = K->pro_any;
+    P.omega = K->omega;
+    P.eps = K->precision == SLAQ_FP64 ? 0x1p-53 : 0x1p-24;
+  }
+  return P;
+}
+
 int reduce_and_solve(slaq_krylov K, int k, int jfirst, int jcount, bool with_g, bool first_pass,
                      bool need_coef, cudaStream_t st) {
   ProfScope prof(SLAQ_PROF_REDUCE, st);
-  double *pj = with_g ? K->proj : nullptr;  // null for the FP64 form
+  // the projected matrix feeds the reduced forms' Rayleigh-Ritz step, which
+  // partial reorthogonalization does not use (null for the FP64 form too)
+  double *pj = (with_g && K->reorth != 0) ? K->proj : nullptr;
+  const ProArgs P = pro_args(K);
   ++tl_launches;
   if (K->max_chunks_per_graph * K->dsub >= 8) {
     const dim3 grid((unsigned)ceil_div((int64_t)jcount * K->ld, 32), with_g ? 2 : 1,
@@ -1429,17 +1560,17 @@ int reduce_and_solve(slaq_krylov K, int k, int jfirst, int jcount, bool with_g, 
     if (tbytes == 8)
       k_solve_lanes<double><<<blocks, kSolveLanes, smem, st>>>(
           K->dsum, K->gram, k, K->s, K->ld, K->nv, K->n_graphs, first_pass ? 1 : 0,
-          need_coef ? 1 : 0, K->tol, K->gbound, K->m, K->alpha, K->beta, K->coef);
+          need_coef ? 1 : 0, K->tol, K->gbound, K->m, K->alpha, K->beta, K->coef, P, jfirst);
     else
       k_solve_lanes<float><<<blocks, kSolveLanes, smem, st>>>(
           K->dsum, K->gram, k, K->s, K->ld, K->nv, K->n_graphs, first_pass ? 1 : 0,
-          need_coef ? 1 : 0, K->tol, K->gbound, K->m, K->alpha, K->beta, K->coef);
+          need_coef ? 1 : 0, K->tol, K->gbound, K->m, K->alpha, K->beta, K->coef, P, jfirst);
   } else {
     // few problems: a warp per problem spreads them over the SMs
     const size_t smem = (size_t)(K1 * K1 + 2 * K1) * sizeof(double);
     k_solve<<<dim3(K->nv, K->n_graphs), 32, smem, st>>>(
         K->dsum, K->gram, k, K->s, K->ld, K->nv, first_pass ? 1 : 0, need_coef ? 1 : 0, K->tol,
-        K->gbound, K->m, K->alpha, K->beta, K->coef);
+        K->gbound, K->m, K->alpha, K->beta, K->coef, P, jfirst);
   }
   SLAQ_CHECK_LAUNCH("reduce_and_solve");
   return SLAQ_OK;
@@ -1468,11 +1599,15 @@ int update(slaq_krylov K, const Geometry &geo, int64_t n, int k, bool second, cu
   if (second)
     k_update<P, true><<<K->n_uchunks, geo.threads, smem, st>>>(
         U, Z, Unext, geo.S, K->u_row0, K->u_rows, K->u_graph, geo.V, geo.R, ustride, k, K->s,
-        K->coef, K->m, K->nv, yscale, Ynext);
+        K->coef, K->m, K->nv, yscale, Ynext, nullptr);
+  else if (K->reorth == 0)
+    k_update<P, false, true><<<K->n_uchunks, geo.threads, smem, st>>>(
+        U, Z, Unext, geo.S, K->u_row0, K->u_rows, K->u_graph, geo.V, geo.R, ustride, k, K->s,
+        K->coef, K->m, K->nv, yscale, Ynext, K->pro_full);
   else
     k_update<P, false><<<K->n_uchunks, geo.threads, smem, st>>>(
         U, Z, Unext, geo.S, K->u_row0, K->u_rows, K->u_graph, geo.V, geo.R, ustride, k, K->s,
-        K->coef, K->m, K->nv, yscale, Ynext);
+        K->coef, K->m, K->nv, yscale, Ynext, nullptr);
   SLAQ_CHECK_LAUNCH("update");
   return SLAQ_OK;
 }
@@ -1487,6 +1622,7 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   // once per process and form (a thread-safe static initialization)
   static const cudaError_t attr = [] {
     const void *fs[] = {(const void *)k_update<P, false>, (const void *)k_update<P, true>,
+                        (const void *)k_update<P, false, true>,
                         (const void *)k_dots<P, false, true>, (const void *)k_dots<P, false, false>,
                         (const void *)k_dots<P, true, false>};
     for (const void *f : fs) {
@@ -1549,15 +1685,32 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
                             K->ymode ? K->Y : nullptr);
   }
   SLAQ_CHECK_LAUNCH("probe_init");
+  const bool pro = K->reorth == 0;
+  if (pro) {
+    SLAQ_CHECK_CUDA(cudaMemsetAsync(K->pro_full, 0, (size_t)K->n_graphs * (K->s + 2) * 4, st));
+    SLAQ_CHECK_CUDA(cudaMemsetAsync(K->pro_any, 0, (size_t)(K->s + 2) * 4, st));
+  }
   for (int k = 0; k < K->s; ++k) {
     SLAQ_TRY(spmm<P>(gr, K, geo, k, st));
     const bool last = (k == K->s - 1);
     // last step: only alpha_k = d_k / G_kk and the Gram diagonal entry, except
     // for the reduced forms, whose Rayleigh-Ritz step needs the whole column
     // of the projected matrix
-    const int jfirst = (last && P == SLAQ_FP64) ? k : 0;
+    int jfirst = (last && (P == SLAQ_FP64 || pro)) ? k : 0;
+    if (pro && !last && k >= 2) {
+      // partial reorthogonalization: project on all vectors only if some
+      // graph's flag for this step is set (decided by step k-1's solve; the
+      // update of step k-1 and this SpMM run on the device meanwhile)
+      SLAQ_CHECK_CUDA(cudaEventSynchronize(K->ev_flag));
+      if (!K->pro_any_host[k]) jfirst = k - 1;
+    }
     SLAQ_TRY(dots<P>(K, geo, n, k, jfirst, k, false, true, K->Z, st));
     SLAQ_TRY(reduce_and_solve(K, k, jfirst, k - jfirst + 1, true, true, !last, st));
+    if (pro && k >= 1 && k + 1 < K->s - 1) {
+      SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->pro_any_host + k + 1, K->pro_any + k + 1, sizeof(int32_t),
+                                      cudaMemcpyDeviceToHost, st));
+      SLAQ_CHECK_CUDA(cudaEventRecord(K->ev_flag, st));
+    }
     if (last) break;
     SLAQ_TRY(update<P>(K, geo, n, k, false, st));
     if (K->reorth == 2) {
@@ -1594,6 +1747,33 @@ int grow(T **p, size_t count) {
 
 }  // namespace
 
+namespace {
+// out[g][k] = 1 if step k of graph g formed u_{k+1} by projecting against
+// all previous vectors (k < min(max_p m_gp, s - 1); with partial
+// reorthogonalization only steps 0, 1 and the flagged ones)
+__global__ void k_full_steps(const int32_t *pro_full, const int32_t *m_all, int G, int nv, int s,
+                             int32_t *out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)G * s) return;
+  const int g = (int)(i / s), k = (int)(i - (int64_t)g * s);
+  int mx = 0;
+  for (int p = 0; p < nv; ++p) mx = max(mx, m_all[(int64_t)g * nv + p]);
+  const bool formed = k < min(mx, s - 1);
+  const bool full = !pro_full || k <= 1 || pro_full[(int64_t)g * (s + 2) + k];
+  out[i] = formed && full ? 1 : 0;
+}
+}  // namespace
+
+int full_steps(slaq_krylov K, int32_t *out, cudaStream_t st) {
+  if (!K || !out) return set_error(SLAQ_EINVAL, "NULL Krylov handle or output");
+  const int64_t total = (int64_t)K->n_graphs * K->s;
+  ++tl_launches;
+  k_full_steps<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(
+      K->reorth == 0 ? K->pro_full : nullptr, K->m, K->n_graphs, K->nv, K->s, out);
+  SLAQ_CHECK_LAUNCH("full_steps");
+  return SLAQ_OK;
+}
+
 int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st) {
   if (!g || !out) return set_error(SLAQ_EINVAL, "NULL graph or output");
   if (nv < 1 || graph_id < 0 || graph_id > 0xffff) return set_error(SLAQ_EINVAL, "bad nv or graph_id");
@@ -1613,9 +1793,12 @@ void krylov_free(slaq_krylov k) {
                   k->alpha, k->beta,
                   k->m, k->theta, k->tau2, k->status, k->hcount, k->gn, k->gtrace, k->gtrace2,
                   k->gbound,
-                  k->d_row0, k->d_rows, k->d_goff, k->u_row0, k->u_rows, k->u_graph};
+                  k->d_row0, k->d_rows, k->d_goff, k->u_row0, k->u_rows, k->u_graph,
+                  k->pro_full, k->pro_any, k->omega};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (k->pro_any_host) cudaFreeHost(k->pro_any_host);
+  if (k->ev_flag) cudaEventDestroy(k->ev_flag);
   if (k->ev_fork) cudaEventDestroy(k->ev_fork);
   if (k->ev_join) cudaEventDestroy(k->ev_join);
   if (k->side) cudaStreamDestroy(k->side);
@@ -1631,7 +1814,12 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   if (graph_id < 0 || graph_id > 0xffff) return set_error(SLAQ_EINVAL, "graph_id must be < 65536");
   if (precision != SLAQ_FP64 && precision != SLAQ_FP32 && precision != SLAQ_FP32_BF16BASIS)
     return set_error(SLAQ_EINVAL, "unknown precision %d", precision);
-  if (reorth != 1 && reorth != 2) return set_error(SLAQ_EINVAL, "reorth_passes must be 1 or 2");
+  if (reorth != 0 && reorth != 1 && reorth != 2)
+    return set_error(SLAQ_EINVAL, "reorth_passes must be 0 (partial), 1 or 2");
+  if (reorth == 0 && precision == SLAQ_FP32_BF16BASIS)
+    return set_error(SLAQ_EUNSUPPORTED,
+                     "partial reorthogonalization needs an FP64 or FP32 basis (BF16 storage "
+                     "rounds above the semi-orthogonality level)");
   if (g->n < 1) return set_error(SLAQ_EINVAL, "graph has no nodes");
   if (g->n > (1LL << 31)) return set_error(SLAQ_EUNSUPPORTED, "too many nodes");
   const int ld = row_ld(nv, precision);
@@ -1704,6 +1892,16 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     K->gcap = G;
   }
   if (!K->status) SLAQ_TRY(grow(&K->status, 1));
+  if (reorth == 0 && G > K->pro_gcap) {
+    SLAQ_TRY(grow(&K->pro_full, (size_t)G * (s + 2)));
+    SLAQ_TRY(grow(&K->omega, (size_t)G * nv * 3 * s));
+    K->pro_gcap = G;
+  }
+  if (reorth == 0 && !K->pro_any) {
+    SLAQ_TRY(grow(&K->pro_any, (size_t)s + 2));
+    SLAQ_CHECK_CUDA(cudaMallocHost(&K->pro_any_host, (size_t)(s + 2) * sizeof(int32_t)));
+    SLAQ_CHECK_CUDA(cudaEventCreateWithFlags(&K->ev_flag, cudaEventDisableTiming));
+  }
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gn, g->gn_dev, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gtrace2, g->gtrace2_dev, G * sizeof(double),
                                   cudaMemcpyDeviceToDevice, st));

@@ -545,14 +545,18 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   const int total = K->n_graphs * K->nv;
   // the solver is latency-bound: few problems go one per block, over many SMs
   const int tpb = std::max(1, std::min(32, total / std::max(1, num_sms())));
-  if (K->precision != SLAQ_FP64 && total < 4096) {
+  // partial reorthogonalization keeps the recurrence's T in every form (no
+  // projected matrix is formed); full reorthogonalization in the reduced
+  // forms takes the Rayleigh-Ritz matrix of the stored basis
+  const bool pencil = K->precision != SLAQ_FP64 && K->reorth != 0;
+  if (pencil && total < 4096) {
     static const cudaError_t attr = cudaFuncSetAttribute(
         k_ritz_pencil_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ritz_warp_smem(kMaxS));
     SLAQ_CHECK_CUDA(attr);
     k_ritz_pencil_warp<<<(unsigned)total, 32, ritz_warp_smem(K->s), st>>>(
         K->gram, K->proj, K->m, K->nv, K->s, K->ld, K->alpha, K->beta, K->theta, K->tau2,
         K->status);
-  } else if (K->precision != SLAQ_FP64) {
+  } else if (pencil) {
     const int64_t need = (int64_t)total * ((int64_t)K->s * K->s + K->s * (K->s + 1) / 2 + 2 * K->s);
     if (need > K->rscratch_cap) {
       if (K->rscratch) cudaFree(K->rscratch);

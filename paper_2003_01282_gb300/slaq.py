@@ -18,6 +18,7 @@ from .build import LIB
 NORMALIZED, COMBINATORIAL = 0, 1
 DROP_ISOLATED = 1
 FP64, FP32, FP32_BF16BASIS = 0, 1, 2
+REORTH_PARTIAL = 0  # reorth_passes value: partial reorthogonalization
 DIST_HEAT, DIST_WAVE, DIST_VNGE = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": FP32_BF16BASIS}
 KINDS = {"normalized": NORMALIZED, "combinatorial": COMBINATORIAL}
@@ -51,6 +52,7 @@ _SIGNATURES = {
     "slaq_lanczos_batched": (_I, [_VP, _I, _I, _I, _U64, _I, _I, _I, C.c_char_p, _VP, _PVP]),
     "slaq_probes": (_I, [_VP, _I, _U64, _I, _VP, _VP]),
     "slaq_krylov_export": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "slaq_krylov_full_steps": (_I, [_VP, _VP, _VP]),
     "slaq_ritz_export": (_I, [_VP, _VP, _VP, _VP]),
     "slaq_krylov_info": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_trace_heat": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
@@ -298,6 +300,16 @@ def krylov_export(k, stream=None):
     m = torch.empty(*lead, nv, dtype=torch.int32, device="cuda")
     _check(lib().slaq_krylov_export(_handle(k), _dev(alpha), _dev(beta), _dev(m), _stream(stream)))
     return alpha, beta, m
+
+
+def krylov_full_steps(k, stream=None):
+    """int32 [(G,) s] on the device: 1 where a Lanczos step projected its new
+    vector against all previous ones (slaq_krylov_full_steps)."""
+    torch = _torch()
+    s = krylov_info(k)["s"]
+    out = torch.empty(*_lead(k), s, dtype=torch.int32, device="cuda")
+    _check(lib().slaq_krylov_full_steps(_handle(k), _dev(out), _stream(stream)))
+    return out
 
 
 def ritz_export(k, stream=None):
