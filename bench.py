@@ -207,8 +207,8 @@ class ClockSampler:
 # profiles/kernels_rmat20_fp32_k16.md; it describes the kernels only while
 # csrc/lanczos.cu is byte-identical to the source that was captured.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1954789000 + 350599680 + 561229000 + 8384256,
-    "source_sha256": "c1aee8fdb04d0917beec216305a9c01e682b372fa1321ea92cfff723002525e2",
+    "bytes_per_spmm": 1957124000 + 351158016 + 561571000 + 8496640,
+    "source_sha256": "0b1646bd6d614afdf2109c627e560ee8f3dfc231a1c9538f94fc5c6abb2383c0",
 }
 
 
@@ -309,6 +309,40 @@ def run_batched(args, dev, world=1, rank=0, tdist=None):
             "per_graph_launches": {"graphs": len(sub), "value": len(sub) / (ms_sub * 1e-3),
                                    "unit": "graphs/s"},
             "speedup_over_per_graph": (SBM_GRAPHS / ms) / (len(sub) / ms_sub)}
+
+
+def small_graph_replay():
+    """The small single-graph workload (BA n = 2000, m = 4, seed 0, normalized
+    Laplacian, nv = 10, s = 15, full reorthogonalization): wall time of one
+    Lanczos run (probes, s steps, Gauss rules; synchronous calls) through
+    slaq_lanczos and through slaq_lanczos_rerun, which replays the run's
+    captured CUDA graph with a new seed."""
+    import torch
+    from paper_2003_01282_gb300 import slaq
+    s_, d_, n = synth.barabasi_albert(2000, 4, seed=0)
+    g = slaq.build_laplacian(torch.as_tensor(s_, device="cuda"), torch.as_tensor(d_, device="cuda"),
+                             n, kind=slaq.NORMALIZED)
+    out = {"workload": "BA n=2000 m=4 seed 0, normalized; nv=10, s=15, full reorthogonalization"}
+    reps = 50
+    for name, prec in (("fp64", slaq.FP64), ("fp32", slaq.FP32)):
+        K = slaq.lanczos(g, 10, 15, 1, precision=prec)
+        for i in range(5):
+            slaq.lanczos(g, 10, 15, 2 + i, precision=prec, reuse=K)
+            slaq.lanczos_rerun(K, 2 + i)
+        t0 = time.perf_counter()
+        for i in range(reps):
+            slaq.lanczos(g, 10, 15, 100 + i, precision=prec, reuse=K)
+        t1 = time.perf_counter()
+        slaq.lanczos_rerun(K, 99)                # capture again after the last call
+        t2 = time.perf_counter()
+        for i in range(reps):
+            slaq.lanczos_rerun(K, 100 + i)
+        t3 = time.perf_counter()
+        a, b_ = (t1 - t0) / reps * 1e3, (t3 - t2) / reps * 1e3
+        out[name] = {"ms_per_run_launches": a, "ms_per_run_replay": b_, "speedup": a / b_}
+        K.close()
+    g.close()
+    return out
 
 
 def rel_errors(a, b, t_np):
@@ -589,6 +623,7 @@ def run_ours(args):
                         "full_projection_steps": int(fs.sum()), "of_steps": S - 1,
                         "rel_err_vs_fp64": rel_errors(dp.double().cpu().numpy(), b, t_np)}
         result["partial_reorth"] = pr
+        result["graph_replay"] = small_graph_replay()
 
     # end to end through the host-memory entry point (pinned buffers)
     if not args.quick:

@@ -172,6 +172,20 @@ void slaq_graph_destroy(slaq_graph g);
 int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id,
                  int precision, int reorth_passes, void *stream, slaq_krylov *inout);
 
+/* slaq_lanczos again on the same graph, sizes, form and reorthogonalization
+ * as the handle's last slaq_lanczos / slaq_lanczos_batched call, with probes
+ * from a new seed: the results equal that call's with `seed` bit for bit.
+ * The first rerun captures the run's launches (probe generation, the s
+ * Lanczos steps, the Gauss rules) into a CUDA graph; every rerun then copies
+ * the seed to the device and launches that graph, so a run costs one launch
+ * on the host instead of about 5 s + 10.  The graph handle of the last call
+ * must still be alive (a batched call's concatenation is owned by k).  Any
+ * slaq_lanczos call on k discards the captured graph.  Not available with
+ * partial reorthogonalization (its steps are decided on the host):
+ * SLAQ_EUNSUPPORTED.  Synchronizes `stream`; SLAQ_ENUMERIC as for
+ * slaq_lanczos. */
+int slaq_lanczos_rerun(slaq_krylov k, uint64_t seed, void *stream);
+
 /* slaq_lanczos for a batch of separately built graphs gs[0..count): the
  * graphs (each a single graph or itself a batch) are concatenated on the
  * device into one block-diagonal Laplacian owned by the Krylov handle, and

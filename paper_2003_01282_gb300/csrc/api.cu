@@ -99,6 +99,7 @@ void dfree(void *p, cudaStream_t st) {
 // ---------------------------------------------------------------- profiler
 thread_local int64_t tl_launches = 0;
 namespace {
+thread_local bool tl_prof_paused = false;  // inside a stream capture
 struct ProfPair {
   int cat;
   cudaEvent_t a, b;
@@ -138,10 +139,13 @@ void prof_collect_locked() {
 }
 }  // namespace
 
+ProfPause::ProfPause() : saved(tl_prof_paused) { tl_prof_paused = true; }
+ProfPause::~ProfPause() { tl_prof_paused = saved; }
+
 void prof_begin(int cat, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_prof_mutex);
   cudaEvent_t e = nullptr;
-  if (g_prof_on) {
+  if (g_prof_on && !tl_prof_paused) {
     e = prof_event();
     if (e && cudaEventRecord(e, st) != cudaSuccess) {
       cudaGetLastError();
@@ -162,7 +166,7 @@ void prof_end(int cat, cudaStream_t st, int64_t launches) {
       break;
     }
   }
-  if (cat >= 0 && cat < SLAQ_PROF_NCAT) g_prof_launch[cat] += launches;
+  if (cat >= 0 && cat < SLAQ_PROF_NCAT && !tl_prof_paused) g_prof_launch[cat] += launches;
   if (!a) return;
   cudaEvent_t b = prof_event();
   if (!b || cudaEventRecord(b, st) != cudaSuccess) {
@@ -268,6 +272,18 @@ int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int p
   int32_t status = 0;
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, (*inout)->status, sizeof(int32_t),
                                   cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
+  return SLAQ_OK;
+}
+
+int slaq_lanczos_rerun(slaq_krylov k, uint64_t seed, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  cudaStream_t st = as_stream(stream);
+  SLAQ_TRY(lanczos_rerun(k, seed, st));
+  int32_t status = 0;
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, k->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
   if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
   return SLAQ_OK;

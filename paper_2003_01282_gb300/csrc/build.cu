@@ -18,7 +18,9 @@
 // any correct builder's bit for bit.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -765,8 +767,30 @@ int bits_for(int64_t n) {
 
 }  // namespace
 
+namespace {
+std::mutex g_live_mutex;
+std::unordered_map<slaq_graph, uint64_t> g_live;  // handles not yet freed -> uid
+uint64_t g_next_uid = 1;
+}  // namespace
+
+void graph_register(slaq_graph g) {
+  std::lock_guard<std::mutex> lk(g_live_mutex);
+  g->uid = g_next_uid++;
+  g_live[g] = g->uid;
+}
+
+bool graph_alive(slaq_graph g, uint64_t uid) {
+  std::lock_guard<std::mutex> lk(g_live_mutex);
+  const auto it = g_live.find(g);
+  return it != g_live.end() && it->second == uid;
+}
+
 void graph_free(slaq_graph g) {
   if (!g) return;
+  {
+    std::lock_guard<std::mutex> lk(g_live_mutex);
+    g_live.erase(g);
+  }
   void *ptrs[] = {g->rowptr, g->colidx, g->vals, g->vals32, g->diag, g->scale, g->diag32,
                   g->scale32, g->old_id, g->heavy_row, g->heavy_first, g->chunk_slot,
                   g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32, g->x_diag, g->x_scale,
@@ -1009,6 +1033,7 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   const int64_t n_out = drop ? n_nonisolated : n;
 
   slaq_graph g = new slaq_graph_s();
+  graph_register(g);
   struct Guard {
     slaq_graph *g;
     ~Guard() {
@@ -1270,6 +1295,7 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   if (G > 65535) return set_error(SLAQ_EINVAL, "a batch holds at most 65535 graphs");
   Temps tmp(st);
   slaq_graph g = new slaq_graph_s();
+  graph_register(g);
   struct Guard {
     slaq_graph *g;
     ~Guard() {

@@ -42,6 +42,12 @@ int device_check();        // SLAQ_OK on a compute-capability 10.3 device
 extern thread_local int64_t tl_launches;
 void prof_begin(int cat, cudaStream_t st);
 void prof_end(int cat, cudaStream_t st, int64_t launches);
+// Suspends the profiler's event records on this thread (inside a capture).
+struct ProfPause {
+  bool saved;
+  ProfPause();
+  ~ProfPause();
+};
 struct ProfScope {
   int cat;
   cudaStream_t st;
@@ -84,6 +90,7 @@ constexpr int kHeavyChunk = 512;   // nnz per work item of a split (heavy) row
 }  // namespace slaq
 
 struct slaq_graph_s {
+  uint64_t uid = 0;      // unique over the process (graph_alive)
   int device = -1;
   int64_t n_input = 0;   // n_nodes given at build time (sum over a batch)
   int64_t n = 0;         // kept nodes n' (sum over a batch)
@@ -210,6 +217,13 @@ struct slaq_krylov_s {
   double *omega = nullptr;          // [G][nv][3][s]
   int64_t pro_gcap = 0;             // graphs the partial-reorthogonalization arrays hold
   cudaEvent_t ev_flag = nullptr;    // after the copy of pro_any[k+1]
+  // replay of the last run as a CUDA graph (slaq_lanczos_rerun)
+  uint64_t *seed_dev = nullptr;     // [1] the probe seed the run reads
+  slaq_graph last_g = nullptr;      // graph of the last run (not owned, unless == owned)
+  uint64_t last_uid = 0;            // its uid
+  cudaGraphExec_t gexec = nullptr;  // captured launches of that run, or null
+  int64_t graph_nodes = 0;          // nodes of the captured graph (counted as launches)
+  cudaStream_t cap = nullptr;       // private stream the capture runs on
   // side stream on which the split-row SpMM runs beside the light rows
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -224,6 +238,8 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges, int
                     slaq_graph *out, int n_graphs = 1, const int64_t *edge_off_host = nullptr,
                     const int64_t *node_off_host = nullptr);
 void graph_free(slaq_graph g);
+void graph_register(slaq_graph g);             // gives g its uid and marks it alive
+bool graph_alive(slaq_graph g, uint64_t uid);  // g not freed since it got uid
 int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
                 int reorth, cudaStream_t st, slaq_krylov *inout,
                 const slaq_tuning *tune = nullptr);
@@ -234,6 +250,7 @@ int lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t see
 void krylov_free(slaq_krylov k);
 int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st);
 int full_steps(slaq_krylov k, int32_t *out, cudaStream_t st);
+int lanczos_rerun(slaq_krylov k, uint64_t seed, cudaStream_t st);
 int run_ritz(slaq_krylov k, cudaStream_t st);
 int trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *se,
                double *per_probe, cudaStream_t st);

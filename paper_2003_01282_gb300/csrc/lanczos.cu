@@ -185,9 +185,11 @@ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
 
 template <int P>
 __global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id,
-                             const int32_t *xgraph, Slc S, int nv, uint64_t seed,
+                             const int32_t *xgraph, Slc S, int nv, const uint64_t *seed_p,
                              uint64_t graph_id, const float *yscale, float *Y0) {
   using TB = typename Form<P>::TB;
+  const uint64_t seed = *seed_p;  // in device memory, so that a captured run can be replayed
+                                  // with another seed
   const int64_t n = S.n;
   const int ld = S.ld;
   const int64_t total = n * ld;
@@ -1612,8 +1614,10 @@ int update(slaq_krylov K, const Geometry &geo, int64_t n, int k, bool second, cu
   return SLAQ_OK;
 }
 
+// launch_only: the chunk tables and buffers of this graph are in place (a
+// replay capture); only the run's launches are issued.
 template <int P>
-int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
+int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st, bool launch_only) {
   using TB = typename Form<P>::TB;
   const int64_t n = gr->n;
   K->ymode = P == SLAQ_FP32 && !gr->weighted && gr->kind == SLAQ_NORMALIZED && K->Y;
@@ -1640,7 +1644,7 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
   }();
   SLAQ_CHECK_CUDA(attr);
   // chunk tables: dots chunks fill one wave; update chunks are smaller
-  {
+  if (!launch_only) {
     const int Jb = std::min(K->s, geo.Jb);
     const int RZ = dots_phases(geo.V, Jb, geo.dots_threads);
     const int per_sm = blocks_per_sm(k_dots<P, false, true>, geo.V * Jb * RZ,
@@ -1681,7 +1685,7 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st) {
     ++tl_launches;
     k_probe_init<P><<<(unsigned)std::min<int64_t>(ceil_div(n * K->ld, 256), 152LL * 64), 256, 0,
                       st>>>(static_cast<TB *>(K->U), gr->x_old_id, gr->x_graph, geo.S, K->nv,
-                            K->seed, (uint64_t)K->graph_id, K->ymode ? K->yscale : nullptr,
+                            K->seed_dev, (uint64_t)K->graph_id, K->ymode ? K->yscale : nullptr,
                             K->ymode ? K->Y : nullptr);
   }
   SLAQ_CHECK_LAUNCH("probe_init");
@@ -1799,6 +1803,9 @@ void krylov_free(slaq_krylov k) {
     if (p) cudaFree(p);
   if (k->pro_any_host) cudaFreeHost(k->pro_any_host);
   if (k->ev_flag) cudaEventDestroy(k->ev_flag);
+  if (k->seed_dev) cudaFree(k->seed_dev);
+  if (k->gexec) cudaGraphExecDestroy(k->gexec);
+  if (k->cap) cudaStreamDestroy(k->cap);
   if (k->ev_fork) cudaEventDestroy(k->ev_fork);
   if (k->ev_join) cudaEventDestroy(k->ev_join);
   if (k->side) cudaStreamDestroy(k->side);
@@ -1910,6 +1917,13 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gbound, g->gbound_dev, G * sizeof(double),
                                   cudaMemcpyDeviceToDevice, st));
   K->seed = seed;
+  if (!K->seed_dev) SLAQ_TRY(grow(&K->seed_dev, 1));
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->seed_dev, &K->seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  // a replay graph of an earlier run no longer matches
+  if (K->gexec) cudaGraphExecDestroy(K->gexec);
+  K->gexec = nullptr;
+  K->last_g = g;
+  K->last_uid = g->uid;
   K->graph_id = graph_id;
   K->reorth = reorth;
   K->n = n;
@@ -1919,13 +1933,62 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   K->bound = g->bound;
   K->tol = default_tol(precision);
   int r;
-  if (precision == SLAQ_FP64) r = lanczos_form<SLAQ_FP64>(g, K, st);
-  else if (precision == SLAQ_FP32) r = lanczos_form<SLAQ_FP32>(g, K, st);
-  else r = lanczos_form<SLAQ_FP32_BF16BASIS>(g, K, st);
+  if (precision == SLAQ_FP64) r = lanczos_form<SLAQ_FP64>(g, K, st, false);
+  else if (precision == SLAQ_FP32) r = lanczos_form<SLAQ_FP32>(g, K, st, false);
+  else r = lanczos_form<SLAQ_FP32_BF16BASIS>(g, K, st, false);
   if (r != SLAQ_OK) return r;
   SLAQ_TRY(run_ritz(K, st));
   *inout = K;
   guard.fresh = false;  // the caller owns it now
+  return SLAQ_OK;
+}
+
+// Replays the last run's launches (probe init, s Lanczos steps, Gauss rules)
+// with a new seed.  The first call captures them into a CUDA graph on a
+// private stream (capture needs a stream other than the legacy default one);
+// later calls only copy the seed and launch the graph.  Partial
+// reorthogonalization decides on the host between steps and is not replayed.
+int lanczos_rerun(slaq_krylov K, uint64_t seed, cudaStream_t st) {
+  if (!K || !K->last_g) return set_error(SLAQ_EINVAL, "Krylov handle has no run to replay");
+  if (!graph_alive(K->last_g, K->last_uid))
+    return set_error(SLAQ_EINVAL, "the graph of the run to replay has been destroyed");
+  if (K->reorth == 0)
+    return set_error(SLAQ_EUNSUPPORTED, "partial reorthogonalization is not replayed");
+  if (!K->gexec) {
+    if (!K->cap) SLAQ_CHECK_CUDA(cudaStreamCreateWithFlags(&K->cap, cudaStreamNonBlocking));
+    // the capture stream starts after the work already on st
+    SLAQ_CHECK_CUDA(cudaEventRecord(K->ev_fork, st));
+    SLAQ_CHECK_CUDA(cudaStreamWaitEvent(K->cap, K->ev_fork, 0));
+    SLAQ_CHECK_CUDA(cudaStreamBeginCapture(K->cap, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = tl_launches;
+    int r;
+    {
+      ProfPause pause;  // no profiling events inside the capture
+      if (K->precision == SLAQ_FP64) r = lanczos_form<SLAQ_FP64>(K->last_g, K, K->cap, true);
+      else if (K->precision == SLAQ_FP32) r = lanczos_form<SLAQ_FP32>(K->last_g, K, K->cap, true);
+      else r = lanczos_form<SLAQ_FP32_BF16BASIS>(K->last_g, K, K->cap, true);
+      if (r == SLAQ_OK) r = run_ritz(K, K->cap);
+    }
+    tl_launches = l0;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(K->cap, &graph);
+    if (r != SLAQ_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return r;
+    }
+    SLAQ_CHECK_CUDA(e);
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    const cudaError_t ei = cudaGraphInstantiate(&K->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) K->gexec = nullptr;
+    SLAQ_CHECK_CUDA(ei);
+    K->graph_nodes = (int64_t)nodes;
+  }
+  K->seed = seed;
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->seed_dev, &K->seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  SLAQ_CHECK_CUDA(cudaGraphLaunch(K->gexec, st));
+  tl_launches += K->graph_nodes;
   return SLAQ_OK;
 }
 

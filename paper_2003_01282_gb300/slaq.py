@@ -53,6 +53,7 @@ _SIGNATURES = {
     "slaq_probes": (_I, [_VP, _I, _U64, _I, _VP, _VP]),
     "slaq_krylov_export": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_krylov_full_steps": (_I, [_VP, _VP, _VP]),
+    "slaq_lanczos_rerun": (_I, [_VP, _U64, _VP]),
     "slaq_ritz_export": (_I, [_VP, _VP, _VP, _VP]),
     "slaq_krylov_info": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_trace_heat": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
@@ -248,6 +249,14 @@ def lanczos(g, nv: int, s: int, seed: int, graph_id: int = 0, precision=FP64, re
     if reuse is not None:
         return reuse
     return Krylov(h)
+
+
+def lanczos_rerun(k, seed: int, stream=None):
+    """slaq_lanczos_rerun: the handle's last run again with a new probe seed,
+    replayed from a captured CUDA graph."""
+    _check(lib().slaq_lanczos_rerun(_handle(k), C.c_uint64(int(seed) & (2**64 - 1)),
+                                    _stream(stream)))
+    return k
 
 
 def lanczos_batched(graphs, nv: int, s: int, seed: int, graph_id: int = 0, precision=FP64,
