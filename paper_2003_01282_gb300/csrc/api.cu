@@ -261,7 +261,7 @@ int slaq_graph_export(slaq_graph g, int64_t *rowptr, int32_t *colidx, double *va
 void slaq_graph_destroy(slaq_graph g) {
   if (!g) return;
   cudaDeviceSynchronize();
-  graph_free(g);
+  graph_free(g, 0);
 }
 
 int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
@@ -406,7 +406,7 @@ int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int6
       cudaStreamSynchronize(st);
       for (void *x : p) cudaFreeAsync(x, st);
       if (k) krylov_free(k);
-      if (g) graph_free(g);
+      if (g) graph_free(g, st);
       cudaStreamSynchronize(st);
     }
   } b{st, {}};

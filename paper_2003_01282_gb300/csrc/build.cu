@@ -785,7 +785,7 @@ bool graph_alive(slaq_graph g, uint64_t uid) {
   return it != g_live.end() && it->second == uid;
 }
 
-void graph_free(slaq_graph g) {
+void graph_free(slaq_graph g, cudaStream_t st) {
   if (!g) return;
   {
     std::lock_guard<std::mutex> lk(g_live_mutex);
@@ -797,7 +797,7 @@ void graph_free(slaq_graph g) {
                   g->x_diag32, g->x_scale32, g->x_old_id, g->goff_dev, g->gn_dev,
                   g->gtrace_dev, g->gbound_dev, g->x_graph, g->gtrace2_dev};
   for (void *p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, st);
   delete g;
 }
 
@@ -819,15 +819,11 @@ struct Temps {
 };
 
 template <typename T>
-int persistent(T **p, size_t count) {
-  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    return set_error(SLAQ_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
-                     cudaGetErrorString(e));
-  }
-  return SLAQ_OK;
+int persistent(T **p, size_t count, cudaStream_t st) {
+  // stream-ordered, from the device pool that keeps freed blocks cached: a
+  // build of the same size reuses the last build's memory without a driver
+  // allocation (graph_free returns it the same way)
+  return dalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T), st);
 }
 }  // namespace
 
@@ -853,9 +849,9 @@ static int heavy_schedule(slaq_graph g, Temps &tmp, cudaStream_t st) {
     SLAQ_TRY(exclusive_scan(nchunk, g->n, chunk_of, d_total, st));
     SLAQ_TRY(to_host(&g->n_chunks, d_total, 1, st));
     if (g->n_heavy > 0) {
-      SLAQ_TRY(persistent(&g->heavy_row, g->n_heavy));
-      SLAQ_TRY(persistent(&g->heavy_first, g->n_heavy + 1));
-      SLAQ_TRY(persistent(&g->chunk_slot, g->n_chunks));
+      SLAQ_TRY(persistent(&g->heavy_row, g->n_heavy, st));
+      SLAQ_TRY(persistent(&g->heavy_first, g->n_heavy + 1, st));
+      SLAQ_TRY(persistent(&g->chunk_slot, g->n_chunks, st));
       ++tl_launches;
       k_heavy_table<<<grid_for(g->n, 256), 256, 0, st>>>(is_heavy, slot_of, chunk_of, nchunk,
                                                           g->n, g->n_heavy, g->n_chunks,
@@ -1036,10 +1032,11 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   graph_register(g);
   struct Guard {
     slaq_graph *g;
+    cudaStream_t st;
     ~Guard() {
-      if (*g) graph_free(*g);
+      if (*g) graph_free(*g, st);
     }
-  } guard{&g};
+  } guard{&g, st};
   SLAQ_CHECK_CUDA(cudaGetDevice(&g->device));
   g->n_input = n;
   g->n = n_out;
@@ -1047,15 +1044,15 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   g->kind = kind;
   g->flags = flags;
   g->weighted = weighted;
-  SLAQ_TRY(persistent(&g->rowptr, n_out + 1));
-  SLAQ_TRY(persistent(&g->colidx, nnz));
-  SLAQ_TRY(persistent(&g->vals, nnz));
-  if (weighted) SLAQ_TRY(persistent(&g->vals32, nnz));
-  SLAQ_TRY(persistent(&g->diag, n_out));
-  SLAQ_TRY(persistent(&g->scale, n_out));
-  SLAQ_TRY(persistent(&g->diag32, n_out));
-  SLAQ_TRY(persistent(&g->scale32, n_out));
-  SLAQ_TRY(persistent(&g->old_id, n_out));
+  SLAQ_TRY(persistent(&g->rowptr, n_out + 1, st));
+  SLAQ_TRY(persistent(&g->colidx, nnz, st));
+  SLAQ_TRY(persistent(&g->vals, nnz, st));
+  if (weighted) SLAQ_TRY(persistent(&g->vals32, nnz, st));
+  SLAQ_TRY(persistent(&g->diag, n_out, st));
+  SLAQ_TRY(persistent(&g->scale, n_out, st));
+  SLAQ_TRY(persistent(&g->diag32, n_out, st));
+  SLAQ_TRY(persistent(&g->scale32, n_out, st));
+  SLAQ_TRY(persistent(&g->old_id, n_out, st));
   double *deg = nullptr;
   SLAQ_TRY(tmp.get(&deg, n_out));
   ++tl_launches;
@@ -1127,10 +1124,10 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   {
     std::vector<double> gn(G);
     for (int q = 0; q < G; ++q) gn[q] = (double)(g->goff[q + 1] - g->goff[q]);
-    SLAQ_TRY(persistent(&g->goff_dev, G + 1));
-    SLAQ_TRY(persistent(&g->gn_dev, G));
-    SLAQ_TRY(persistent(&g->gtrace_dev, G));
-    SLAQ_TRY(persistent(&g->gbound_dev, G));
+    SLAQ_TRY(persistent(&g->goff_dev, G + 1, st));
+    SLAQ_TRY(persistent(&g->gn_dev, G, st));
+    SLAQ_TRY(persistent(&g->gtrace_dev, G, st));
+    SLAQ_TRY(persistent(&g->gbound_dev, G, st));
     SLAQ_CHECK_CUDA(cudaMemcpy(g->goff_dev, g->goff.data(), (G + 1) * sizeof(int64_t),
                                cudaMemcpyHostToDevice));
     SLAQ_CHECK_CUDA(cudaMemcpy(g->gn_dev, gn.data(), G * sizeof(double), cudaMemcpyHostToDevice));
@@ -1139,7 +1136,7 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
     SLAQ_CHECK_CUDA(cudaMemcpy(g->gbound_dev, g->gbound.data(), G * sizeof(double),
                                cudaMemcpyHostToDevice));
     // tr(L_g^2) for the polynomial control variate of the heat trace
-    SLAQ_TRY(persistent(&g->gtrace2_dev, G));
+    SLAQ_TRY(persistent(&g->gtrace2_dev, G, st));
     // offs = [coff | eoff]: first chunk and first stored entry of every graph
     std::vector<int64_t> offs(2 * ((size_t)G + 1), 0);
     int64_t *coff = offs.data(), *eoff = coff + G + 1;
@@ -1172,18 +1169,18 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   }
 
   // 5. execution copy: graph-major, then descending degree, then id
-  SLAQ_TRY(persistent(&g->x_rowptr, n_out + 1));
-  SLAQ_TRY(persistent(&g->x_colidx, nnz));
+  SLAQ_TRY(persistent(&g->x_rowptr, n_out + 1, st));
+  SLAQ_TRY(persistent(&g->x_colidx, nnz, st));
   // the SpMM reads values only in the weighted form; unweighted graphs run the
   // pattern form from the scales, so their execution copy keeps no values
-  if (weighted) SLAQ_TRY(persistent(&g->x_vals, nnz));
-  if (weighted) SLAQ_TRY(persistent(&g->x_vals32, nnz));
-  SLAQ_TRY(persistent(&g->x_diag, n_out));
-  SLAQ_TRY(persistent(&g->x_scale, n_out));
-  SLAQ_TRY(persistent(&g->x_diag32, n_out));
-  SLAQ_TRY(persistent(&g->x_scale32, n_out));
-  SLAQ_TRY(persistent(&g->x_old_id, n_out));
-  SLAQ_TRY(persistent(&g->x_graph, n_out));
+  if (weighted) SLAQ_TRY(persistent(&g->x_vals, nnz, st));
+  if (weighted) SLAQ_TRY(persistent(&g->x_vals32, nnz, st));
+  SLAQ_TRY(persistent(&g->x_diag, n_out, st));
+  SLAQ_TRY(persistent(&g->x_scale, n_out, st));
+  SLAQ_TRY(persistent(&g->x_diag32, n_out, st));
+  SLAQ_TRY(persistent(&g->x_scale32, n_out, st));
+  SLAQ_TRY(persistent(&g->x_old_id, n_out, st));
+  SLAQ_TRY(persistent(&g->x_graph, n_out, st));
   if (n_out > 0) {
     const int pcb = bits_for(n_out);
     const int pdb = bits_for(n_out + 1);
@@ -1298,10 +1295,11 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   graph_register(g);
   struct Guard {
     slaq_graph *g;
+    cudaStream_t st;
     ~Guard() {
-      if (*g) graph_free(*g);
+      if (*g) graph_free(*g, st);
     }
-  } guard{&g};
+  } guard{&g, st};
   g->device = dev;
   g->kind = gs[0]->kind;
   g->flags = gs[0]->flags;
@@ -1341,25 +1339,25 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   g->trace = g->gtrace[0];
   g->bound = *std::max_element(g->gbound.begin(), g->gbound.end());
   const bool w = g->weighted;
-  SLAQ_TRY(persistent(&g->rowptr, n + 1));
-  SLAQ_TRY(persistent(&g->colidx, nnz));
-  SLAQ_TRY(persistent(&g->vals, nnz));
-  if (w) SLAQ_TRY(persistent(&g->vals32, nnz));
-  SLAQ_TRY(persistent(&g->diag, n));
-  SLAQ_TRY(persistent(&g->scale, n));
-  SLAQ_TRY(persistent(&g->diag32, n));
-  SLAQ_TRY(persistent(&g->scale32, n));
-  SLAQ_TRY(persistent(&g->old_id, n));
-  SLAQ_TRY(persistent(&g->x_rowptr, n + 1));
-  SLAQ_TRY(persistent(&g->x_colidx, nnz));
-  if (w) SLAQ_TRY(persistent(&g->x_vals, nnz));
-  if (w) SLAQ_TRY(persistent(&g->x_vals32, nnz));
-  SLAQ_TRY(persistent(&g->x_diag, n));
-  SLAQ_TRY(persistent(&g->x_scale, n));
-  SLAQ_TRY(persistent(&g->x_diag32, n));
-  SLAQ_TRY(persistent(&g->x_scale32, n));
-  SLAQ_TRY(persistent(&g->x_old_id, n));
-  SLAQ_TRY(persistent(&g->x_graph, n));
+  SLAQ_TRY(persistent(&g->rowptr, n + 1, st));
+  SLAQ_TRY(persistent(&g->colidx, nnz, st));
+  SLAQ_TRY(persistent(&g->vals, nnz, st));
+  if (w) SLAQ_TRY(persistent(&g->vals32, nnz, st));
+  SLAQ_TRY(persistent(&g->diag, n, st));
+  SLAQ_TRY(persistent(&g->scale, n, st));
+  SLAQ_TRY(persistent(&g->diag32, n, st));
+  SLAQ_TRY(persistent(&g->scale32, n, st));
+  SLAQ_TRY(persistent(&g->old_id, n, st));
+  SLAQ_TRY(persistent(&g->x_rowptr, n + 1, st));
+  SLAQ_TRY(persistent(&g->x_colidx, nnz, st));
+  if (w) SLAQ_TRY(persistent(&g->x_vals, nnz, st));
+  if (w) SLAQ_TRY(persistent(&g->x_vals32, nnz, st));
+  SLAQ_TRY(persistent(&g->x_diag, n, st));
+  SLAQ_TRY(persistent(&g->x_scale, n, st));
+  SLAQ_TRY(persistent(&g->x_diag32, n, st));
+  SLAQ_TRY(persistent(&g->x_scale32, n, st));
+  SLAQ_TRY(persistent(&g->x_old_id, n, st));
+  SLAQ_TRY(persistent(&g->x_graph, n, st));
   auto ptrs = [&](auto field) {
     using T = std::remove_pointer_t<std::remove_reference_t<decltype(gs[0]->*field)>>;
     std::vector<const T *> v(count);
@@ -1396,10 +1394,10 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   {
     std::vector<double> gn(G);
     for (int64_t q = 0; q < G; ++q) gn[q] = (double)(g->goff[q + 1] - g->goff[q]);
-    SLAQ_TRY(persistent(&g->goff_dev, G + 1));
-    SLAQ_TRY(persistent(&g->gn_dev, G));
-    SLAQ_TRY(persistent(&g->gtrace_dev, G));
-    SLAQ_TRY(persistent(&g->gbound_dev, G));
+    SLAQ_TRY(persistent(&g->goff_dev, G + 1, st));
+    SLAQ_TRY(persistent(&g->gn_dev, G, st));
+    SLAQ_TRY(persistent(&g->gtrace_dev, G, st));
+    SLAQ_TRY(persistent(&g->gbound_dev, G, st));
     SLAQ_CHECK_CUDA(cudaMemcpy(g->goff_dev, g->goff.data(), (G + 1) * sizeof(int64_t),
                                cudaMemcpyHostToDevice));
     SLAQ_CHECK_CUDA(cudaMemcpy(g->gn_dev, gn.data(), G * sizeof(double), cudaMemcpyHostToDevice));
@@ -1407,7 +1405,7 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
                                cudaMemcpyHostToDevice));
     SLAQ_CHECK_CUDA(cudaMemcpy(g->gbound_dev, g->gbound.data(), G * sizeof(double),
                                cudaMemcpyHostToDevice));
-    SLAQ_TRY(persistent(&g->gtrace2_dev, G));
+    SLAQ_TRY(persistent(&g->gtrace2_dev, G, st));
     SLAQ_CHECK_CUDA(cudaMemcpy(g->gtrace2_dev, g->gtrace2.data(), G * sizeof(double),
                                cudaMemcpyHostToDevice));
   }

@@ -237,7 +237,9 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t n_edges, int
                     const double *weights, int kind, int flags, cudaStream_t st,
                     slaq_graph *out, int n_graphs = 1, const int64_t *edge_off_host = nullptr,
                     const int64_t *node_off_host = nullptr);
-void graph_free(slaq_graph g);
+// frees g's device arrays in stream order on st (every use of g must be
+// ordered before that point on st)
+void graph_free(slaq_graph g, cudaStream_t st);
 void graph_register(slaq_graph g);             // gives g its uid and marks it alive
 bool graph_alive(slaq_graph g, uint64_t uid);  // g not freed since it got uid
 int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,

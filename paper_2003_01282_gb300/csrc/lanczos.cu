@@ -1809,7 +1809,7 @@ void krylov_free(slaq_krylov k) {
   if (k->ev_fork) cudaEventDestroy(k->ev_fork);
   if (k->ev_join) cudaEventDestroy(k->ev_join);
   if (k->side) cudaStreamDestroy(k->side);
-  graph_free(k->owned);
+  graph_free(k->owned, 0);  // callers have synchronized the device or k's stream
   delete k;
 }
 

@@ -149,10 +149,11 @@ int lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t see
   SLAQ_TRY(union_graphs(gs, count, st, &u));
   struct Own {
     slaq_graph *u;
+    cudaStream_t st;
     ~Own() {
-      if (*u) graph_free(*u);
+      if (*u) graph_free(*u, st);
     }
-  } own{&u};
+  } own{&u, st};
   slaq_tuning tune;
   if (tune_cache) {
     std::map<std::string, slaq_tuning> all;
@@ -169,7 +170,7 @@ int lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t see
   }
   SLAQ_TRY(run_lanczos(u, nv, s, seed, graph_id, precision, reorth, st, inout, &tune));
   // the Krylov handle keeps the union alive until it is destroyed or reused
-  graph_free((*inout)->owned);
+  graph_free((*inout)->owned, st);
   (*inout)->owned = u;
   u = nullptr;
   return SLAQ_OK;
