@@ -1060,10 +1060,19 @@ __global__ void k_solve(const double *__restrict__ dsum_all, double *__restrict_
     if (j <= i) A[i * K1 + j] = gram[((int64_t)(j0 + i) * s + j0 + j) * ld + p] * sc[i] * sc[j];
   }
   __syncthreads();
+  // partial reorthogonalization: the Gram entries no step measured are zero
+  // in the solve, which is accurate while the basis is semi-orthogonal (the
+  // scaled pivots stay near 1).  A pivot below 1/2 means a near-breakdown
+  // has left it too far from orthogonal for that: the probe's Krylov space is
+  // numerically exhausted, and it stops as at a breakdown.
+  const bool pro = P.full != nullptr;
+  bool degenerate = false;
   // Cholesky of Ghat = D^-1/2 G D^-1/2 (unit diagonal), in place, right-looking:
   // the diagonal keeps the inverse pivot 1/L_cc, column c is scaled by it,
   // then the trailing block is updated by all lanes of the warp.
   for (int c = 0; c < K1; ++c) {
+    degenerate = degenerate || (pro && A[c * K1 + c] < 0.5);
+    __syncwarp();
     if (lane == 0) A[c * K1 + c] = rsqrt(fmax(A[c * K1 + c], 1e-300));
     __syncwarp();
     const double ipiv = A[c * K1 + c];
@@ -1090,6 +1099,18 @@ __global__ void k_solve(const double *__restrict__ dsum_all, double *__restrict_
     __syncwarp();
     for (int i = lane; i < c; i += 32) y[i] -= A[c * K1 + i] * y[c];
     __syncwarp();
+  }
+  if (pro) {
+    bool finite = !degenerate;
+    for (int j = lane; j < K1; j += 32) finite = finite && isfinite(y[j] * sc[j]);
+    if (!__all_sync(0xffffffffu, finite)) {  // numerically exhausted: stop as at a breakdown
+      if (lane == 0) {
+        m[p] = k + 1;  // alpha_k stands; u_{k+1} is written as zero
+        coef[(s - 1) * ld + p] = 0.0;
+      }
+      for (int j = lane; j <= k; j += 32) coef[j * ld + p] = 0.0;
+      return;
+    }
   }
   for (int j = lane; j < K1; j += blockDim.x) coef[(j0 + j) * ld + p] = y[j] * sc[j];
   // the update divides by ||u_k|| (first pass), so ||u_{k+1}|| = beta_k
@@ -1187,8 +1208,12 @@ __global__ void __launch_bounds__(kSolveLanes)
     for (int j = 0; j <= i; ++j)
       SLAQ_A(i, j) = (T)gram[((int64_t)(j0 + i) * s + j0 + j) * ld + p] * si * sc[j * kSolveLanes];
   }
+  // partial reorthogonalization: a scaled pivot below 1/2 stops the probe (see k_solve)
+  const bool pro = P.full != nullptr;
+  bool degenerate = false;
   // right-looking Cholesky, inverse pivots on the diagonal
   for (int c = 0; c < K1; ++c) {
+    degenerate = degenerate || (pro && SLAQ_A(c, c) < T(0.5));
     const T ip = rsq<T>(fmax(SLAQ_A(c, c), std::numeric_limits<T>::min()));
     SLAQ_A(c, c) = ip;
     for (int i = c + 1; i < K1; ++i) SLAQ_A(i, c) *= ip;
@@ -1208,6 +1233,14 @@ __global__ void __launch_bounds__(kSolveLanes)
     for (int i = 0; i < c; ++i) y[i * kSolveLanes] -= SLAQ_A(c, i) * xc;
   }
 #undef SLAQ_A
+  bool finite = !degenerate;
+  for (int j = 0; j < K1; ++j) finite = finite && isfinite(y[j * kSolveLanes] * sc[j * kSolveLanes]);
+  if (pro && !finite) {  // numerically exhausted: stop the probe as at a breakdown
+    m[p] = k + 1;         // alpha_k stands; u_{k+1} is written as zero
+    for (int j = 0; j <= k; ++j) coef[j * ld + p] = 0.0;
+    coef[(s - 1) * ld + p] = 0.0;
+    return;
+  }
   for (int j = 0; j < K1; ++j)
     coef[(j0 + j) * ld + p] = (double)(y[j * kSolveLanes] * sc[j * kSolveLanes]);
   coef[(s - 1) * ld + p] = first_pass ? rsqrt(gram[((int64_t)k * s + k) * ld + p]) : 1.0;

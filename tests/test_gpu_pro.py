@@ -251,3 +251,27 @@ def test_partial_full_size_workload():
     K32p = slaq.lanczos(g, 100, 20, 1, precision=slaq.FP32, reorth_passes=PARTIAL)
     assert _rel(slaq.trace_heat(K32p, t)[0].cpu().numpy(), h64) < 1e-4
     assert abs(slaq.trace_vnge(K32p)[0].item() - v64) / v64 < 1e-3
+
+
+@pytest.mark.parametrize("prec,h_tol", [(slaq.FP64, 1e-10), (slaq.FP32, 1e-4)])
+def test_partial_near_breakdown_probes(prec, h_tol):
+    """SBM graphs 800..899 of the 5000-graph batch (probe seed 1, nv = 20,
+    s = 15; graph_id 800 gives each graph the probes it has in the full
+    batch).  Some probes of graphs 853 and 872 come within a factor 1.3 of the
+    breakdown tolerance (beta_8 = 2.6e-4 in FP32), which leaves their next
+    vector far from orthogonal before the one-step-late flag takes effect.
+    A full step must stay finite there; the descriptors hold the form's bar
+    against full reorthogonalization in FP64."""
+    graphs = synth.sbm_batch(5000, seed=3)[800:900]
+    gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
+    t = _dev(synth.t_grid(64), torch.float64)
+    Kp = slaq.lanczos(gb, 20, 15, 1, graph_id=800, precision=prec, reorth_passes=PARTIAL)
+    alpha, beta, m = (x.cpu().numpy() for x in slaq.krylov_export(Kp))
+    for g in range(len(graphs)):
+        for p in range(20):
+            assert np.all(np.isfinite(alpha[g, p, :m[g, p]])), (g, p)
+            assert np.all(np.isfinite(beta[g, p, :max(m[g, p] - 1, 0)])), (g, p)
+    K64 = slaq.lanczos(gb, 20, 15, 1, graph_id=800, precision=slaq.FP64)
+    h, h64 = (slaq.trace_heat(K, t)[0].cpu().numpy() for K in (Kp, K64))
+    keep = h64 > 0  # graphs with no kept nodes have a zero trace in both
+    assert np.max(np.abs(h - h64)[keep] / h64[keep]) < h_tol
