@@ -207,8 +207,8 @@ class ClockSampler:
 # profiles/kernels_rmat20_fp32_k16.md; it describes the kernels only while
 # csrc/lanczos.cu is byte-identical to the source that was captured.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1957124000 + 351158016 + 561571000 + 8496640,
-    "source_sha256": "0b1646bd6d614afdf2109c627e560ee8f3dfc231a1c9538f94fc5c6abb2383c0",
+    "bytes_per_spmm": 1955883000 + 350987008 + 561419000 + 8566272,
+    "source_sha256": "539318e1736260c06e3e5c38220af5c6f958ea6afc09843f63491855f31327bf",
 }
 
 
