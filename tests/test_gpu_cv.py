@@ -106,3 +106,24 @@ def test_cv_reduced_forms_and_variance_reduction():
     with pytest.raises(slaq.SlaqError) as ei:
         slaq.trace_heat_cv(K64, t, 3)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("nv,steps", [(512, 6), (3, 64), (1, 8)])
+def test_cv_largest_sizes_and_one_probe(nv, steps):
+    """The control variate at the largest probe block and step count the
+    library accepts, and with one probe (no standard error: NaN)."""
+    s, d, n = synth.barabasi_albert(2000, 4, seed=0)
+    lap = build_laplacian(s, d, n)
+    g = slaq.build_laplacian(_dev(s), _dev(d), n)
+    K = slaq.lanczos(g, nv, steps, 3, precision=slaq.FP64)
+    t = synth.t_grid(32)
+    h, se = (x.cpu().numpy() for x in slaq.trace_heat_cv(K, _dev(t, torch.float64), 2))
+    runs = odesc.slq_runs(lap, steps, nv, 3)
+    oh, ose = ovar.heat_trace_cv(runs, lap.n, t, 2, lap.norm_bound(), lap.trace,
+                                 ovar.frobenius_sq(lap))
+    rt = np.maximum(RTOL, t * lap.norm_bound() * 1e-14)
+    assert np.all(np.abs(h - oh) <= rt * np.abs(oh))
+    if nv == 1:
+        assert np.all(np.isnan(se))
+    else:
+        assert np.all(np.abs(se - ose) <= 1e-6 * ose + 1e-9 * lap.n)

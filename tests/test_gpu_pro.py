@@ -275,3 +275,19 @@ def test_partial_near_breakdown_probes(prec, h_tol):
     h, h64 = (slaq.trace_heat(K, t)[0].cpu().numpy() for K in (Kp, K64))
     keep = h64 > 0  # graphs with no kept nodes have a zero trace in both
     assert np.max(np.abs(h - h64)[keep] / h64[keep]) < h_tol
+
+
+@pytest.mark.parametrize("nv,s", [(512, 6), (3, 64)])
+def test_partial_largest_sizes(nv, s):
+    """Partial reorthogonalization at the largest probe block and step count:
+    the omega ring and the step flags span s + 2 entries."""
+    src, dst, n = synth.barabasi_albert(2000, 4, seed=0)
+    lap = build_laplacian(src, dst, n)
+    g = _graph(src, dst, n)
+    K = slaq.lanczos(g, nv, s, 11, precision=slaq.FP64, reorth_passes=PARTIAL)
+    m = slaq.krylov_export(K)[2].cpu().numpy()
+    runs = odesc.slq_runs(lap, s, nv, 11)
+    assert all(m[p] == r.m for p, r in enumerate(runs))
+    _descriptors_close(K, runs, lap, synth.t_grid(64))
+    full = slaq.krylov_full_steps(K).cpu().numpy()
+    assert full.shape == (s,) and full[:2].sum() == 2 and full[s - 1] == 0
