@@ -153,7 +153,10 @@ void slaq_graph_destroy(slaq_graph g);
  *   by the recurrence that the symmetry of L imposes on it (measured from
  *   the Gram column on steps that project on all vectors).  When a probe's
  *   max_j |omega_{k,j}| passes sqrt(eps) (eps = 2^-53 FP64, 2^-24 FP32), the
- *   next two steps of its graph project against all previous vectors.  The
+ *   next two steps of its graph project against all previous vectors (their
+ *   Gram system with the entries no step measured set to zero; a scaled
+ *   pivot below 1/2 there means the basis is too far from orthogonal, as
+ *   just after a near-breakdown, and the probe stops as at a breakdown).  The
  *   Gauss rule then comes from the recurrence's T in both forms.  It needs a
  *   host read of one flag per step (the call does not return before the
  *   last step is enqueued); SLAQ_FP32_BF16BASIS with it: SLAQ_EUNSUPPORTED
