@@ -14,28 +14,39 @@ the Lanczos iteration in FP32 (alpha/beta reductions, eigensolve and
 quadrature in FP64).  Timed beside it, each with its error against the FP64
 form: the FP64 form, the BF16-basis form, and both FP32 and FP64 with
 partial reorthogonalization; the heat-trace control variate's standard
-errors; the 5000-graph SBM batch (graphs/s); the host-memory entry point.
+errors; the host-memory entry point.  Further legs, each its own workload:
+the 5000-graph SBM batch through one autotuned batched run (graphs/s), the
+R-MAT 2^24 graph with the BF16 basis against an FP64 run in two probe ranges
+(probe-edges/s, speedup, error per descriptor), and 64 R-MAT graph pairs of
+2^18 .. 2^22 nodes with 0.1% of their edges rewired (pairs/s per form,
+distance errors of the FP32 and BF16 forms against FP64).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank runs the same graph with its own probe
-seed (weak scaling over probes); the per-rank estimates are averaged with
-one all-reduce of the descriptor vector.  `--impl reference` times the CPU
-oracle on a bounded sample of the same workload.
+Under torchrun (N > 1) rank r runs probes [r*nv, (r+1)*nv) of the same seed
+(weak scaling over probes; slaq_lanczos_probes); the ranks all-gather their
+per-probe values and pool them (slaq_pool_probes_host), which gives the mean
+and standard error of one run over all N*nv probes.  `--impl reference` times
+the CPU oracle on a bounded sample of the same workload over a process pool
+of the host's cores.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
+import multiprocessing
 import os
+import platform
 import subprocess
 import sys
 import tempfile
 import threading
 import time
 
-if "--impl" in sys.argv and "reference" in sys.argv or "--cpu-baseline-worker" in sys.argv:
-    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+if "--impl" in sys.argv and "reference" in sys.argv:
+    for _v in BLAS_ENV:
         os.environ[_v] = "1"
 
 import numpy as np
@@ -53,14 +64,27 @@ WORKLOAD = ("R-MAT scale 20 (2^20 nodes, 16Mi unique undirected edges, a,b,c,d=.
             "seed 1), isolated nodes dropped, normalized Laplacian; nv=100 Rademacher probes, "
             "s=20 Lanczos steps, full CGS reorthogonalization; heat + wave traces on 256 "
             "log-spaced t in [1e-2,1e2] + VNGE")
-CPU_PROBES = 4        # probes of the CPU-oracle sample
-REF_PROBES = 1        # probes per step of the reference (oracle) arm
+CPU_PROBES_PER_WORKER = 2   # probes per pool worker in the CPU-oracle sample
 # batched workload: 5000 SBM graphs, nv = 20, s = 15, heat traces at 256 t
 SBM_GRAPHS, SBM_NV, SBM_S, SBM_SEED = 5000, 20, 15, 3
 SBM_WORKLOAD = ("5000 stochastic-block-model graphs (sizes lognormal, median 300, clipped to "
                 "[10, 5000]; 2-6 equal blocks; p_in ~ U[.05,.3], p_out = p_in/U[5,20]; seed 3), "
                 "isolated nodes dropped, normalized Laplacians as one block-diagonal batch; "
-                "nv=20, s=15; heat traces on 256 log-spaced t")
+                "nv=20, s=15; heat traces on 256 log-spaced t; launch shapes autotuned")
+# web-scale single graph: R-MAT 2^24, BF16 basis, nv = 64, s = 20
+R24_SCALE, R24_SEED, R24_NV, R24_S = 24, 2, 64, 20
+R24_WORKLOAD = ("R-MAT scale 24 (2^24 nodes, 256Mi unique undirected edges, same a,b,c,d, seed 2, "
+                "drawn on the GPU), isolated nodes dropped, normalized Laplacian; nv=64, s=20, "
+                "basis stored in BF16 with FP32 SpMM/updates, FP64 alpha/beta, Gauss rules and "
+                "quadrature; against an FP64 run of the same 64 probes in two ranges of 32")
+# graph pairs: 64 R-MAT graphs of 2^18 .. 2^22 nodes, each against a 0.1%-rewired copy
+PAIRS, PAIR_NV, PAIR_S, PAIR_SEED = 64, 64, 20, 5
+PAIR_WORKLOAD = ("64 R-MAT graphs, n_i = round(2^(18+4i/63)) nodes (pairs with an endpoint >= n_i "
+                 "rejected), 16*n_i unique undirected edges, seed 100+i, each against a copy with "
+                 "ceil(0.1%|E|) edges deleted and replaced by uniform non-edges (node ids kept, no "
+                 "dropping); normalized Laplacians; nv=64, s=20, common random probes per pair; "
+                 "heat-trace and wave-trace L2 distances and the VNGE difference")
+BF16_WAVE_TB = 20.0   # the BF16-basis form serves its wave trace for t * bound <= 20
 
 
 def make_graph():
@@ -76,77 +100,175 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def cpu_info() -> dict:
+    """Host cores the oracle pool uses, the CPU model, and the BLAS threads."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"cores": cores, "os_cpu_count": os.cpu_count(), "cpu_model": model or platform.machine(),
+            "blas_threads_per_worker": 1}
+
+
 # ------------------------------------------------------------ CPU oracle
-def oracle_sample(src, dst, n, probes: int, s: int):
-    """Oracle on a bounded sample: CSR build + `probes` probes of Lanczos +
-    heat/wave/VNGE quadrature.  Returns (seconds, nnz)."""
+# A process pool over the host's cores, started with `spawn` (never forked
+# from a process that holds a CUDA context).  Every worker loads the oracle's
+# CSR once (initializer) and runs whole probes: Lanczos, Gauss rule, and the
+# heat / wave / VNGE quadrature of that probe.
+_WORKER = {}
+
+
+_ARRAYS = ("rowptr", "colidx", "vals", "diag", "scale", "degree", "old_id", "t")
+
+
+def _pool_init(folder):
+    from oracle.laplacian import Laplacian
+    a = {k: np.load(os.path.join(folder, k + ".npy"), mmap_mode="r") for k in _ARRAYS}
+    with open(os.path.join(folder, "meta.json")) as f:
+        meta = json.load(f)
+    _WORKER["lap"] = Laplacian(n=meta["n"], kind=meta["kind"], trace=meta["trace"],
+                               **{k: a[k] for k in _ARRAYS if k != "t"})
+    _WORKER["t"] = np.asarray(a["t"])
+
+
+def _pool_ready(_):
+    return os.getpid()
+
+
+def _pool_probes(ids):
+    """The oracle's Lanczos, Gauss rules and quadrature for probes `ids`."""
     from oracle import descriptors as od
-    from oracle.laplacian import build_laplacian
-    t = synth.t_grid(NT)
-    t0 = time.perf_counter()
-    lap = build_laplacian(src, dst, n, drop_isolated=True)
-    runs = od.slq_runs(lap, s, probes, PROBE_SEED, probes=range(probes))
-    od.heat_trace(runs, lap.n, t)
-    od.wave_trace(runs, lap.n, t)
-    od.vnge(runs, lap.n, lap.trace)
-    return time.perf_counter() - t0, lap.nnz
+    lap, t = _WORKER["lap"], _WORKER["t"]
+    runs = od.slq_runs(lap, S, NV, PROBE_SEED, probes=list(ids))
+    heat = od.per_probe(runs, od.heat_f(t))
+    wr = od.per_probe(runs, od.wave_re_f(t))
+    wi = od.per_probe(runs, od.wave_im_f(t))
+    vn = od.per_probe(runs, od.vnge_f(lap.trace))
+    return list(ids), heat, wr, wi, vn
 
 
-def cpu_baseline_worker(path: str):
-    d = np.load(path)
-    sec, nnz = oracle_sample(d["src"], d["dst"], int(d["n"]), CPU_PROBES, S)
-    print(json.dumps({"seconds": sec, "nnz": nnz}))
+class OraclePool:
+    """The oracle's Laplacian of the workload and a spawn pool of workers."""
+
+    def __init__(self, src, dst, n):
+        from oracle.laplacian import build_laplacian
+        self.info = cpu_info()
+        t0 = time.perf_counter()
+        self.lap = build_laplacian(src, dst, n, drop_isolated=True)
+        self.build_s = time.perf_counter() - t0
+        self.td = tempfile.TemporaryDirectory()
+        L = self.lap
+        for k in _ARRAYS:
+            np.save(os.path.join(self.td.name, k + ".npy"), synth.t_grid(NT) if k == "t" else getattr(L, k))
+        with open(os.path.join(self.td.name, "meta.json"), "w") as f:
+            json.dump({"n": int(L.n), "kind": L.kind, "trace": float(L.trace)}, f)
+        self.workers = self.info["cores"]
+        # one BLAS thread per worker: the spawned children read these at import
+        saved = {v: os.environ.get(v) for v in BLAS_ENV}
+        for v in BLAS_ENV:
+            os.environ[v] = "1"
+        try:
+            ctx = multiprocessing.get_context("spawn")
+            self.pool = ctx.Pool(self.workers, initializer=_pool_init, initargs=(self.td.name,))
+        finally:
+            for v, x in saved.items():
+                if x is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = x
+        try:  # every worker loaded (bounded: a worker that cannot start must not hang the bench)
+            self.pool.map_async(_pool_ready, range(self.workers), chunksize=1).get(timeout=600)
+        except Exception:
+            self.pool.terminate()
+            self.td.cleanup()
+            raise
+
+    def probes(self, ids):
+        """Wall time of the probes `ids`, split into one contiguous range per worker."""
+        ids = list(ids)
+        chunks = [c for c in np.array_split(ids, min(self.workers, len(ids))) if len(c)]
+        t0 = time.perf_counter()
+        out = self.pool.map_async(_pool_probes, [c.tolist() for c in chunks], chunksize=1).get(timeout=1800)
+        return time.perf_counter() - t0, out
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.td.cleanup()
 
 
 def cpu_baseline(src, dst, n):
-    """Run the oracle sample in a child process limited to one thread."""
-    with tempfile.TemporaryDirectory() as td:
-        path = os.path.join(td, "g.npz")
-        np.savez(path, src=src, dst=dst, n=n)
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", path],
-                           capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        return {"error": r.stderr[-400:]}
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    pe = out["nnz"] * CPU_PROBES * S
-    return {"value": pe / out["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"CSR build of the full graph + {CPU_PROBES} of {NV} probes x {S} Lanczos "
-                      f"steps + heat/wave/VNGE quadrature ({out['seconds']:.1f} s, one thread)"}
+    """The oracle on a bounded sample of the workload: the CSR build (one
+    core) plus CPU_PROBES_PER_WORKER probes per host core over the pool."""
+    try:
+        pool = OraclePool(src, dst, n)
+    except Exception as e:  # pragma: no cover - host without spawn support
+        return {"error": repr(e)[:300]}
+    try:
+        nprobe = min(NV, CPU_PROBES_PER_WORKER * pool.workers)
+        sec, _ = pool.probes(range(nprobe))
+        total = pool.build_s + sec
+        nnz = pool.lap.nnz
+        return {"value": nnz * nprobe * S / total, "unit": UNIT, "cores": pool.workers,
+                "kind": "oracle", **pool.info,
+                "sample": f"CSR build of the full graph on one core ({pool.build_s:.1f} s) + {nprobe} of "
+                          f"{NV} probes x {S} Lanczos steps with heat/wave/VNGE quadrature over a "
+                          f"{pool.workers}-process pool ({sec:.1f} s)"}
+    finally:
+        pool.close()
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step is a bounded sample
-    (REF_PROBES probes of the workload), timed on one host thread."""
+    """The oracle as the reference arm: each step is a bounded sample (one
+    probe per pool worker, a new range of probes every step), timed on the
+    host's cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import descriptors as od
-    from oracle.laplacian import build_laplacian
     src, dst, n = make_graph()
-    lap = build_laplacian(src, dst, n, drop_isolated=True)
-    t = synth.t_grid(NT)
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        runs = od.slq_runs(lap, S, REF_PROBES, PROBE_SEED + i, probes=range(REF_PROBES))
-        od.heat_trace(runs, lap.n, t)
-        od.wave_trace(runs, lap.n, t)
-        od.vnge(runs, lap.n, lap.trace)
-        if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    sec = float(np.mean(times))
-    value = lap.nnz * REF_PROBES * S / sec
-    sample = f"{REF_PROBES} of {NV} probes x {S} Lanczos steps + quadrature per step, one thread"
-    print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nnz": lap.nnz, "n_prime": lap.n},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }))
+    pool = OraclePool(src, dst, n)
+    try:
+        W = pool.workers
+        times = []
+        for i in range(args.warmup + args.steps):
+            ids = [(i * W + w) % NV for w in range(W)]
+            sec, _ = pool.probes(ids)
+            if i >= args.warmup:
+                times.append(sec)
+        sec = float(np.mean(times))
+        nnz = pool.lap.nnz
+        value = nnz * W * S / sec
+        sample = (f"{W} of {NV} probes per step (one per pool worker) x {S} Lanczos steps with "
+                  f"heat/wave/VNGE quadrature; CSR built once before timing")
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nnz": nnz, "n_prime": pool.lap.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "sample": sample, **pool.info},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+    finally:
+        pool.close()
 
 
 # ------------------------------------------------------------ clocks
@@ -188,6 +310,7 @@ class ClockSampler:
                [r for _, r in self.rows if len(r) >= 9]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
         def num(x):
             try:
                 return float(x)
@@ -201,11 +324,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------ our arm
-# DRAM traffic of one SpMM (light-row + split-row kernels, step 16) of the FP32
-# R-MAT 2^20 workload, from the ncu capture summarised in
-# profiles/kernels_rmat20_fp32_k16.md; it describes the kernels only while
-# csrc/lanczos.cu is byte-identical to the source that was captured.
+# ------------------------------------------------------------ roofline
+# DRAM traffic of one SpMM (light-row + split-row kernels) of the FP32
+# R-MAT 2^20 workload from an ncu capture of step 16; it describes the
+# kernels only while csrc/lanczos.cu is byte-identical to the captured source.
 SPMM_TRAFFIC = {
     "bytes_per_spmm": 1955883000 + 350987008 + 561419000 + 8566272,
     "source_sha256": "539318e1736260c06e3e5c38220af5c6f958ea6afc09843f63491855f31327bf",
@@ -220,14 +342,23 @@ def spmm_traffic(prec):
     return SPMM_TRAFFIC["bytes_per_spmm"] if (same and prec == "fp32") else None
 
 
+BASIS_BYTES = {"fp64": 8, "fp32": 4, "bf16": 2}
+
+
+def spmm_algorithmic_bytes(n, nnz, prec, nv=NV):
+    """Algorithmic bytes of one SpMM z = L q (pattern form, useful nv
+    columns): int32 row pointers, int32 column ids, q read once, z written
+    once, the diagonal and scale vectors."""
+    bq, bw = BASIS_BYTES[prec], (8 if prec == "fp64" else 4)
+    return 4 * (n + 1) + 4 * nnz + n * nv * bq + n * nv * bw + 8 * n
+
+
 def algorithmic_bytes(n, nnz, prec, nv=NV, s=S):
-    """Algorithmic bytes of one run, per kernel class (useful nv columns)."""
-    bq = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
-    bw = 8 if prec == "fp64" else 4
+    """Bytes each kernel class moves per run as implemented (useful nv
+    columns): beside the SpMM's algorithmic bytes, its gathers of the
+    pre-scaled copy y = s * u (FP32 form) and its int64 row pointers."""
+    bq, bw = BASIS_BYTES[prec], (8 if prec == "fp64" else 4)
     vec = n * nv
-    # the FP32 form gathers y = s * u (written by the update) and reads u_k
-    # for the diagonal term: one more vector read per SpMM and one more
-    # vector written per update
     yb = bw if prec == "fp32" else 0
     spmm = s * (8 * (n + 1) + 4 * nnz + vec * (bq + bw + yb) + n * 2 * bw)
     # the FP64 form reads only u_{s-1} on the last step; the reduced forms
@@ -237,11 +368,32 @@ def algorithmic_bytes(n, nnz, prec, nv=NV, s=S):
     return {"spmm": spmm, "dots": dots, "update": update}
 
 
+def spmm_roofline(prof_spmm_ms, runs, n, nnz, prec, nv, s, hbm, peak_src, gather_peak):
+    """The SpMM against the HBM roofline of its algorithmic bytes, and its
+    gathered bytes against the measured L2 gather ceiling."""
+    units = runs * s
+    unit_ms = prof_spmm_ms / units
+    unit_bytes = spmm_algorithmic_bytes(n, nnz, prec, nv)
+    achieved = unit_bytes / (unit_ms * 1e-3) / 1e9
+    gathered = nnz * nv * (8 if prec == "fp64" else (4 if prec == "fp32" else 2))
+    out = {"bound": "hbm", "kernel": "spmm", "achieved": achieved, "peak": hbm,
+           "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm,
+           "unit_of_work": "one SpMM z = L u_k (light-row and split-row kernels)",
+           "algorithmic_bytes_per_unit": unit_bytes, "ms_per_unit": unit_ms,
+           "gather": {"gathered_bytes_per_unit": gathered,
+                      "achieved_TBps": gathered / (unit_ms * 1e-3) / 1e12,
+                      "l2_gather_peak_TBps": gather_peak,
+                      "frac": (gathered / (unit_ms * 1e-3) / 1e12 / gather_peak) if gather_peak else None}}
+    return out
+
+
+# ------------------------------------------------------------ batched leg
 def run_batched(args, dev, world=1, rank=0, tdist=None):
-    """The SBM batch through one set of launches per step; graphs/s.  Also
-    times the same path graph by graph on a subset (per-graph launches).
-    Under torchrun every rank runs its own batch (seed + rank): weak scaling
-    over graphs, no exchange, the slowest rank's time."""
+    """The SBM batch through one autotuned slaq_lanczos_batched run per step;
+    graphs/s.  Also times the default launch shapes and the same path graph
+    by graph on a subset (per-graph launches).  Under torchrun every rank runs
+    its own batch (seed + rank): weak scaling over graphs, no exchange, the
+    slowest rank's time."""
     import torch
     from paper_2003_01282_gb300 import slaq
     graphs = synth.sbm_batch(SBM_GRAPHS, seed=SBM_SEED + rank)
@@ -256,41 +408,65 @@ def run_batched(args, dev, world=1, rank=0, tdist=None):
     dst = torch.as_tensor(dsts, device=dev)
     t = torch.as_tensor(synth.t_grid(NT), device=dev)
     P = slaq.PRECISIONS[args.precision]
-    state = {"K": None}
+    td = tempfile.TemporaryDirectory()
+    cache = os.path.join(td.name, "slaq_tune.txt")
+    state = {"K": None, "Kd": None}
 
-    def step():
+    def build():
         out = C.c_void_p()
         slaq._check(slaq.lib().slaq_build_laplacian_batch(
             C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()), edge_off.ctypes.data_as(C.c_void_p),
             node_off.ctypes.data_as(C.c_void_p), len(graphs), None, slaq.NORMALIZED, slaq.DROP_ISOLATED,
             slaq._stream(None), C.byref(out)))
-        g = slaq.Graph(out)
-        state["K"] = slaq.lanczos(g, SBM_NV, SBM_S, rank_seed(rank), precision=P,
-                                  reuse=state["K"])
-        heat, _ = slaq.trace_heat(state["K"], t)
+        return slaq.Graph(out)
+
+    def step(tuned=True):
+        g = build()
+        if tuned:
+            state["K"] = slaq.lanczos_batched([g], SBM_NV, SBM_S, PROBE_SEED + rank, precision=P,
+                                              tune_cache=cache, reuse=state["K"])
+            K = state["K"]
+        else:
+            state["Kd"] = slaq.lanczos(g, SBM_NV, SBM_S, PROBE_SEED + rank, precision=P, reuse=state["Kd"])
+            K = state["Kd"]
+        heat, _ = slaq.trace_heat(K, t)
         nnz = g.info["nnz"]
         g.close()
         return heat, nnz
 
-    for _ in range(2):
-        _, nnz = step()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 3
-    slaq.profile_enable(True)
-    e0.record()
-    for _ in range(reps):
-        step()
-    e1.record()
-    torch.cuda.synchronize(dev)
-    prof = slaq.profile_read()
-    slaq.profile_enable(False)
-    ms = e0.elapsed_time(e1) / reps
+    def timed(tuned, reps=3):
+        for _ in range(2):
+            _, nnz = step(tuned)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        slaq.profile_enable(True)
+        e0.record()
+        for _ in range(reps):
+            step(tuned)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        prof = slaq.profile_read()
+        slaq.profile_enable(False)
+        return e0.elapsed_time(e1) / reps, prof, nnz, reps
+
+    ms, prof, nnz, reps = timed(True)          # the first warm-up call tunes and writes the cache
     if tdist is not None:
         ms = max_over_ranks(ms, dev, tdist)
+    ms_default, _, _, _ = timed(False)
+    shapes = None
+    try:
+        with open(cache) as f:
+            line = [x for x in f if not x.startswith("#")][0]
+        vals = [int(v) for v in line.split("|")[1].split()]
+        shapes = dict(zip(["spmm_threads", "update_threads", "dots_threads", "slice_bytes", "spmm_align"],
+                          vals))
+    except Exception:
+        pass
+    td.cleanup()
     # the same path graph by graph on a subset (every 25th graph)
     sub = graphs[::25]
     Ks = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for (sg, dg, ng) in sub:
         g = slaq.build_laplacian(torch.as_tensor(sg, device=dev), torch.as_tensor(dg, device=dev), ng,
@@ -303,7 +479,10 @@ def run_batched(args, dev, world=1, rank=0, tdist=None):
     ms_sub = e0.elapsed_time(e1)
     return {"workload": SBM_WORKLOAD, "metric": "graphs/s",
             "value": whole_job_value(world, SBM_GRAPHS, ms),
-            "ms_per_step": ms, "nnz": int(nnz),
+            "ms_per_step": ms, "nnz": int(nnz), "entry_point": "slaq_lanczos_batched (tune cache)",
+            "tuned_shapes": shapes,
+            "default_shapes": {"ms_per_step": ms_default,
+                               "value": whole_job_value(world, SBM_GRAPHS, ms_default)},
             "probe_edges_per_s": world * nnz * SBM_NV * SBM_S / (ms * 1e-3),
             "kernels_ms_per_step": {k: round(v[0] / reps, 3) for k, v in prof.items()},
             "per_graph_launches": {"graphs": len(sub), "value": len(sub) / (ms_sub * 1e-3),
@@ -311,6 +490,166 @@ def run_batched(args, dev, world=1, rank=0, tdist=None):
             "speedup_over_per_graph": (SBM_GRAPHS / ms) / (len(sub) / ms_sub)}
 
 
+# ------------------------------------------------------------ config 3
+def run_rmat24(dev, hbm, peak_src, gather_peak):
+    """R-MAT 2^24 with the BF16 basis (nv = 64, s = 20): probe-edges/s, the
+    SpMM roofline, and the error per descriptor and speedup against an FP64
+    run of the same 64 probes in two ranges of 32 (its basis would not fit
+    otherwise), pooled exactly."""
+    import torch
+    from paper_2003_01282_gb300 import shard, slaq
+    t0 = time.perf_counter()
+    src, dst, n = synth.rmat_torch(R24_SCALE, 16 << R24_SCALE, seed=R24_SEED, device=dev)
+    gen_s = time.perf_counter() - t0
+    g = slaq.build_laplacian(src, dst, n, flags=slaq.DROP_ISOLATED)
+    del src, dst
+    torch.cuda.empty_cache()
+    info = g.info
+    n_prime, nnz = info["n"], info["nnz"]
+    t_np = synth.t_grid(NT)
+    t = torch.as_tensor(t_np, device=dev)
+    lo_np = t_np * 2.0 <= BF16_WAVE_TB
+    t_lo = t[torch.as_tensor(lo_np, device=dev)].contiguous()
+    state = {}
+
+    def bf16_run():
+        state["Kb"] = slaq.lanczos(g, R24_NV, R24_S, PROBE_SEED, precision=slaq.FP32_BF16BASIS,
+                                   reuse=state.get("Kb"))
+        K = state["Kb"]
+        h = slaq.trace_heat(K, t)[0]
+        (wr, _), (wi, _) = slaq.trace_wave(K, t_lo)
+        v = slaq.trace_vnge(K)[0]
+        return h, wr, wi, v
+
+    bf16_run()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    slaq.profile_enable(True)
+    e0.record()
+    reps = 2
+    for _ in range(reps):
+        h, wr, wi, v = bf16_run()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    prof = slaq.profile_read()
+    slaq.profile_enable(False)
+    ms_bf = e0.elapsed_time(e1) / reps
+    mon = slaq.krylov_monitor(state["Kb"])
+    del state["Kb"]
+    torch.cuda.empty_cache()
+    # FP64 over the same probes: two ranges of 32, per-probe values pooled
+    parts = []
+    K64 = None
+    e0.record()
+    for p0 in (0, R24_NV // 2):
+        K64 = slaq.lanczos_probes(g, R24_NV // 2, p0, R24_S, PROBE_SEED, precision=slaq.FP64, reuse=K64)
+        hp = slaq.trace_heat(K64, t, per_probe=True)[2]
+        rp, ip = slaq.trace_wave_per_probe(K64, t)
+        vp = slaq.trace_vnge(K64, per_probe=True)[2]
+        parts.append(torch.cat([hp, rp, ip, vp[:, None]], dim=1))
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms64 = e0.elapsed_time(e1)
+    K64.close()
+    mean64, _ = shard.pool(torch.cat(parts).cpu().numpy())
+    h64, wr64, wi64, v64 = mean64[:NT], mean64[NT:2 * NT], mean64[2 * NT:3 * NT], mean64[-1]
+    h, wr, wi, v = h.cpu().numpy(), wr.cpu().numpy(), wi.cpu().numpy(), v.item()
+    wscale = np.max(np.abs(wr64))
+    err = {"heat_max": float(np.max(np.abs(h - h64) / np.abs(h64))),
+           "wave_re_max_t_le_10": float(np.max(np.abs(wr - wr64[lo_np])) / wscale),
+           "wave_im_max_t_le_10": float(np.max(np.abs(wi - wi64[lo_np])) / wscale),
+           "vnge": float(abs(v - v64) / abs(v64))}
+    g.close()
+    pe = nnz * R24_NV * R24_S
+    roof = spmm_roofline(prof["spmm"][0], reps, n_prime, nnz, "bf16", R24_NV, R24_S, hbm, peak_src,
+                         gather_peak.get(R24_NV * 2))
+    return {"workload": R24_WORKLOAD, "n_prime": n_prime, "nnz": nnz, "generate_s": gen_s,
+            "ms_per_run": ms_bf, "probe_edges_per_s": pe / (ms_bf * 1e-3),
+            "kernels_ms_per_run": {k: round(vv[0] / reps, 3) for k, vv in prof.items()},
+            "spmm_roofline": roof, "orthogonality": mon,
+            "fp64_two_ranges": {"ms": ms64, "probe_edges_per_s": pe / (ms64 * 1e-3)},
+            "speedup_over_fp64": ms64 / ms_bf, "rel_err_vs_fp64": err,
+            "wave_t_max": float(t_np[lo_np][-1])}
+
+
+# ------------------------------------------------------------ config 5
+def run_pairs(dev, n_pairs=PAIRS):
+    """64 R-MAT graph pairs (2^18 .. 2^22 nodes): per form, the time of the
+    Lanczos runs, traces and distances of both graphs of every pair (pairs/s),
+    and the relative error of the FP32 / BF16 distances against FP64's."""
+    import torch
+    from paper_2003_01282_gb300 import slaq
+    t_np = synth.t_grid(NT)
+    t = torch.as_tensor(t_np, device=dev)
+    lo_np = t_np * 2.0 <= BF16_WAVE_TB
+    t_lo = t[torch.as_tensor(lo_np, device=dev)].contiguous()
+    nlo = int(lo_np.sum())
+    idx = list(range(PAIRS)) if n_pairs >= PAIRS else \
+        sorted({round(k * (PAIRS - 1) / max(1, n_pairs - 1)) for k in range(n_pairs)})
+    forms = {"fp64": slaq.FP64, "fp32": slaq.FP32, "bf16": slaq.FP32_BF16BASIS}
+    K = {k: None for k in forms}
+    ms = {k: 0.0 for k in forms}
+    dist = {k: [] for k in forms}
+    gen_s, nnz_total = 0.0, 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in idx:
+        n_i = int(round(2.0 ** (18 + 4 * i / 63)))
+        scale = int(math.ceil(math.log2(n_i)))
+        t0 = time.perf_counter()
+        sa, da, _ = synth.rmat_torch(scale, 16 * n_i, seed=100 + i, device=dev, n_nodes=n_i)
+        sb, db, _ = synth.rewire_torch(sa, da, n_i, frac=1e-3, seed=i)
+        ga = slaq.build_laplacian(sa, da, n_i)
+        gb = slaq.build_laplacian(sb, db, n_i)
+        del sa, da, sb, db
+        torch.cuda.synchronize(dev)
+        gen_s += time.perf_counter() - t0
+        nnz_total += ga.info["nnz"] + gb.info["nnz"]
+        for name, P in forms.items():
+            tw = t_lo if name == "bf16" else t
+            e0.record()
+            desc = []
+            for g in (ga, gb):
+                K[name] = slaq.lanczos(g, PAIR_NV, PAIR_S, PAIR_SEED, graph_id=i, precision=P,
+                                       reuse=K[name])
+                h = slaq.trace_heat(K[name], t)[0]
+                (wr, _), (wi, _) = slaq.trace_wave(K[name], tw)
+                v = slaq.trace_vnge(K[name])[0]
+                desc.append((h, torch.cat([wr, wi]), v, torch.cat([wr[:nlo], wi[:nlo]])))
+            (ha, wa, va, wla), (hb, wb, vb, wlb) = desc
+            d = torch.cat([slaq.distance(ha, hb, slaq.DIST_HEAT),
+                           slaq.distance(wa, wb, slaq.DIST_WAVE),
+                           slaq.distance(va, vb, slaq.DIST_VNGE),
+                           slaq.distance(wla, wlb, slaq.DIST_WAVE)])
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms[name] += e0.elapsed_time(e1)
+            dist[name].append(d.cpu().numpy())
+        ga.close()
+        gb.close()
+    for k in K:
+        if K[k] is not None:
+            K[k].close()
+    d64 = np.array(dist["fp64"])
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+    errs = {}
+    for name in ("fp32", "bf16"):
+        d = np.array(dist[name])
+        e = {"heat_distance": rel(d[:, 0], d64[:, 0]), "vnge_difference": rel(d[:, 2], d64[:, 2]),
+             "wave_distance_t_le_10": rel(d[:, 3], d64[:, 3])}
+        if name == "fp32":
+            e["wave_distance"] = rel(d[:, 1], d64[:, 1])
+        errs[name] = e
+    return {"workload": PAIR_WORKLOAD, "pairs": len(idx),
+            "subset": None if len(idx) == PAIRS else f"pairs {idx}",
+            "nnz_total": int(nnz_total), "generate_and_build_s": gen_s,
+            "pairs_per_s": {k: len(idx) / (v * 1e-3) for k, v in ms.items()},
+            "ms_total": ms, "distance_rel_err_vs_fp64": errs,
+            "wave_t_max_bf16": float(t_np[lo_np][-1])}
+
+
+# ------------------------------------------------------------ other legs
 def small_graph_replay():
     """The small single-graph workload (BA n = 2000, m = 4, seed 0, normalized
     Laplacian, nv = 10, s = 15, full reorthogonalization): wall time of one
@@ -346,19 +685,21 @@ def small_graph_replay():
 
 
 def rel_errors(a, b, t_np):
-    """Error of descriptors a against the FP64 run b (both [heat | wave re |
-    wave im | vnge]): heat relative per t, wave relative to its largest
-    magnitude (over all t and over t < 10), VNGE relative."""
-    lo = t_np < 10.0
-    h, h64 = a[:NT], b[:NT]
-    wr, wr64 = a[NT:2 * NT], b[NT:2 * NT]
-    wi, wi64 = a[2 * NT:3 * NT], b[2 * NT:3 * NT]
+    """Error of descriptors a against the FP64 run b (dicts of heat, wave_re,
+    wave_im on the same leading t, vnge): heat relative per t, wave relative
+    to its largest magnitude (over the t a holds and over t < 10), VNGE
+    relative."""
+    nw = a["wave_re"].size
+    lo = t_np[:nw] < 10.0
+    wr64, wi64 = b["wave_re"][:nw], b["wave_im"][:nw]
+    sc_r, sc_i = np.max(np.abs(b["wave_re"])), np.max(np.abs(b["wave_im"]))
     return {
-        "heat_max": float(np.max(np.abs(h - h64) / np.abs(h64))),
-        "wave_re_max": float(np.max(np.abs(wr - wr64)) / np.max(np.abs(wr64))),
-        "wave_im_max": float(np.max(np.abs(wi - wi64)) / np.max(np.abs(wi64))),
-        "wave_re_max_t_lt_10": float(np.max(np.abs(wr - wr64)[lo]) / np.max(np.abs(wr64))),
-        "vnge": float(abs(a[-1] - b[-1]) / abs(b[-1])),
+        "heat_max": float(np.max(np.abs(a["heat"] - b["heat"]) / np.abs(b["heat"]))),
+        "wave_re_max": float(np.max(np.abs(a["wave_re"] - wr64)) / sc_r),
+        "wave_im_max": float(np.max(np.abs(a["wave_im"] - wi64)) / sc_i),
+        "wave_re_max_t_lt_10": float(np.max(np.abs(a["wave_re"] - wr64)[lo]) / sc_r),
+        "wave_t_max": float(t_np[nw - 1]),
+        "vnge": float(abs(a["vnge"] - b["vnge"]) / abs(b["vnge"])),
     }
 
 
@@ -386,21 +727,7 @@ def kernel_capture(args):
     print(json.dumps({"kernel_capture": args.kernel_capture, "n_prime": g.info["n"], "nnz": g.info["nnz"]}))
 
 
-# ---- multi-rank host logic (probe sharding; no data-path collective)
-def rank_seed(rank: int) -> int:
-    """Probe seed of a rank: every rank draws its own nv probes."""
-    return PROBE_SEED + 1000 * rank
-
-
-def average_over_ranks(desc, world: int, tdist):
-    """The per-rank estimates of the same graph are Hutchinson means over
-    disjoint probe sets of equal size, so their mean is the estimate over
-    all world * nv probes: one all-reduce of the descriptor vector."""
-    tdist.all_reduce(desc)
-    desc /= world
-    return desc
-
-
+# ---- multi-rank host logic
 def max_over_ranks(ms: float, device, tdist) -> float:
     """The job's step time: the slowest rank's."""
     import torch
@@ -416,13 +743,14 @@ def whole_job_value(world: int, units_per_step_per_rank: float, ms: float) -> fl
 
 def run_ours(args):
     import torch
-    from paper_2003_01282_gb300 import slaq
+    from paper_2003_01282_gb300 import shard, slaq
     from paper_2003_01282_gb300.build import build
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = world > 1
+    tdist = None
     if dist:
         import torch.distributed as tdist
         torch.cuda.set_device(local)
@@ -441,32 +769,44 @@ def run_ours(args):
     dst = dst_h.to(dev)
     t_np = synth.t_grid(NT)
     t = torch.as_tensor(t_np, device=dev)
-    seed = rank_seed(rank)
+    lo_np = t_np * 2.0 <= BF16_WAVE_TB
+    t_lo = t[torch.as_tensor(lo_np, device=dev)].contiguous()
     prec = args.precision
     P = slaq.PRECISIONS[prec]
+    probe0 = rank * NV   # this rank's probes of the one seed
 
     state = {"K": None, "ref": None}
 
     def step(precision=P, key="K", reorth=1):
         g = slaq.build_laplacian(src, dst, n_nodes, kind=slaq.NORMALIZED, flags=slaq.DROP_ISOLATED)
-        state[key] = slaq.lanczos(g, NV, S, seed, precision=precision, reorth_passes=reorth,
-                                  reuse=state.get(key))
+        state[key] = slaq.lanczos_probes(g, NV, probe0, S, PROBE_SEED, precision=precision,
+                                         reorth_passes=reorth, reuse=state.get(key))
         K = state[key]
-        heat, _ = slaq.trace_heat(K, t)
-        (wr, _), (wi, _) = slaq.trace_wave(K, t)
-        vn, _ = slaq.trace_vnge(K)
-        desc = torch.cat([heat, wr, wi, vn])
+        tw = t_lo if precision == slaq.FP32_BF16BASIS else t
+        nw = tw.numel()
         if dist:
-            average_over_ranks(desc, world, tdist)
+            # per-probe values of every rank's range, pooled over all probes
+            hp = slaq.trace_heat(K, t, per_probe=True)[2]
+            rp, ip = slaq.trace_wave_per_probe(K, tw)
+            vp = slaq.trace_vnge(K, per_probe=True)[2]
+            full = shard.gather_probe_values(torch.cat([hp, rp, ip, vp[:, None]], dim=1),
+                                             world * NV, tdist)
+            mean, _ = shard.pool(full)
+            desc = torch.as_tensor(mean, device=dev)
+            heat, wr, wi, vn = desc[:NT], desc[NT:NT + nw], desc[NT + nw:NT + 2 * nw], desc[-1:]
+        else:
+            heat, _ = slaq.trace_heat(K, t)
+            (wr, _), (wi, _) = slaq.trace_wave(K, tw)
+            vn, _ = slaq.trace_vnge(K)
         if state["ref"] is None:
-            state["ref"] = desc[:NT].clone()
-        d = slaq.distance(desc[:NT], state["ref"], slaq.DIST_HEAT)
+            state["ref"] = heat.clone()
+        d = slaq.distance(heat, state["ref"], slaq.DIST_HEAT)
         info = g.info
         g.close()
-        return desc, d, info
+        return {"heat": heat, "wave_re": wr, "wave_im": wi, "vnge": vn, "dist": d}, info
 
     for _ in range(args.warmup):
-        desc, _, info = step()
+        desc, info = step()
     torch.cuda.synchronize(dev)
     n_prime, nnz = info["n"], info["nnz"]
 
@@ -488,7 +828,7 @@ def run_ours(args):
     tw0 = time.perf_counter()
     ev0.record(stream)
     for _ in range(args.steps):
-        desc, dval, _ = step()
+        desc, _ = step()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     tw1 = time.perf_counter()
@@ -503,8 +843,14 @@ def run_ours(args):
     pe_step = nnz * NV * S
     value = whole_job_value(world, pe_step, ms)
 
-    # roofline of the dominant Lanczos kernel class
     hbm, peak_src = peaks()
+    gather_peak = {}
+    for nvq in (NV * 4, 64 * 2):  # the FP32 headline's rows; the 2^24 BF16 rows
+        rb = (nvq + 15) // 16 * 16
+        try:
+            gather_peak[nvq] = slaq.profile_gather_peak(min(rb, 512))
+        except Exception:
+            gather_peak[nvq] = None
     alg = algorithmic_bytes(n_prime, nnz, prec)
     kernels = {}
     for name in ("spmm", "dots", "update", "reduce", "build", "ritz", "trace", "probes", "dist"):
@@ -512,44 +858,37 @@ def run_ours(args):
         entry = {"ms_per_step": kms / args.steps, "launches_per_step": kl / args.steps}
         if name in alg and kms > 0:
             gbs = alg[name] * args.steps / (kms * 1e-3) / 1e9
-            entry.update({"GBps": gbs, "frac": gbs / hbm})
+            entry.update({"GBps_as_implemented": gbs, "frac": gbs / hbm})
         kernels[name] = entry
-    dom = max(("spmm", "dots", "update"), key=lambda k: prof[k][0])
-    dom_ms, dom_launch = prof[dom]
-    # unit of work: one SpMM (light and split-row kernels, overlapped), one
-    # dots pass or one update pass; S, S and S - 1 of them per Lanczos run
-    units = {"spmm": S, "dots": S, "update": S - 1}[dom]
-    unit_ms = dom_ms / (args.steps * units)
-    unit_bytes = alg[dom] / units
-    achieved = unit_bytes / (unit_ms * 1e-3) / 1e9
-    traffic = spmm_traffic(prec) if dom == "spmm" else None
+    roofline = spmm_roofline(prof["spmm"][0], args.steps, n_prime, nnz, prec, NV, S, hbm, peak_src,
+                             gather_peak.get(NV * 4) if prec == "fp32" else None)
+    roofline.update({"traffic": spmm_traffic(prec),
+                     "implementation_bytes_per_unit": alg["spmm"] / S,
+                     "launches_per_unit": prof["spmm"][1] / (args.steps * S)})
     launches = sum(v[1] for v in prof.values())
+    mon = slaq.krylov_monitor(state["K"])
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else ("bf16" if prec == "bf16" else "f64"),
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_prime": n_prime, "nnz": nnz, "nv": NV, "s": S, "nt": NT,
-                   "precision": prec, "parallelism": f"probes x{world}" if world > 1 else "single GPU",
+                   "precision": prec,
+                   "parallelism": f"probe ranges x{world} (rank r: probes [r*{NV}, (r+1)*{NV}))"
+                   if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (basis %.1f GB, edge list %.0f MB)" % (
-                       S * n_prime * NV * {"fp64": 8, "fp32": 4, "bf16": 2}[prec] / 1e9,
-                       src.numel() * 8 / 1e6)},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic,
-                     "unit_of_work": {"spmm": "one SpMM z = L u_k (light-row and split-row kernels)",
-                                      "dots": "one dots pass", "update": "one update pass"}[dom],
-                     "algorithmic_bytes_per_unit": unit_bytes, "ms_per_unit": unit_ms,
-                     "launches_per_unit": dom_launch / (args.steps * units)},
+                       S * n_prime * NV * BASIS_BYTES[prec] / 1e9, src.numel() * 8 / 1e6)},
+        "roofline": roofline,
         "kernels": kernels,
+        "orthogonality": {"max_abs_QtQ_minus_I": mon["ortho"], "min_beta": mon["min_beta"]},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(tw0, tw1),
     }
 
     # the polynomial control variate on the last step's Lanczos run: standard
     # errors against the plain estimate at a few t, and the kernel's time
-    if not args.quick:
+    if not args.quick and not dist:
         K = state["K"]
         tcv = torch.as_tensor([0.01, 0.1, 1.0, 10.0], device=dev, dtype=torch.float64)
         _, se_plain = slaq.trace_heat(K, tcv)
@@ -569,35 +908,39 @@ def run_ours(args):
                 "ms_256_t": c0.elapsed_time(c1)}
         result["variance_reduction"] = out
 
+    def host(dsc):
+        return {k: (v.double().cpu().numpy() if k != "vnge" else float(v.item()))
+                for k, v in dsc.items() if k != "dist"}
+
     # FP64 form beside it: time and error of the headline form against it
     if prec != "fp64" and not args.quick:
-        for _ in range(1):
-            d64, _, _ = step(slaq.FP64, "K64")
+        step(slaq.FP64, "K64")
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(2):
-            d64, _, _ = step(slaq.FP64, "K64")
+            d64, _ = step(slaq.FP64, "K64")
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms64 = e0.elapsed_time(e1) / 2
-        b = d64.cpu().numpy()
+        b = host(d64)
         result["fp64_form"] = {"ms_per_step": ms64, "value": world * pe_step / (ms64 * 1e-3),
                                "speedup_of_headline": ms64 / ms}
-        result["rel_err_vs_fp64"] = rel_errors(desc.double().cpu().numpy(), b, t_np)
+        result["rel_err_vs_fp64"] = rel_errors(host(desc), b, t_np)
         # the BF16-basis form of the same step, against the same FP64 run
+        # (its wave trace over the t it serves, t <= 10)
         if prec != "bf16":
             step(slaq.FP32_BF16BASIS, "Kbf")
             torch.cuda.synchronize(dev)
             e0.record(stream)
             for _ in range(2):
-                dbf, _, _ = step(slaq.FP32_BF16BASIS, "Kbf")
+                dbf, _ = step(slaq.FP32_BF16BASIS, "Kbf")
             e1.record(stream)
             torch.cuda.synchronize(dev)
             msbf = e0.elapsed_time(e1) / 2
             result["bf16_form"] = {"ms_per_step": msbf, "value": world * pe_step / (msbf * 1e-3),
                                    "speedup_over_fp64_form": ms64 / msbf,
-                                   "rel_err_vs_fp64": rel_errors(dbf.cpu().numpy(), b, t_np)}
+                                   "rel_err_vs_fp64": rel_errors(host(dbf), b, t_np)}
         # partial reorthogonalization (FP32 and FP64 forms): time, the
         # Lanczos kernels' time, how many steps projected against the whole
         # basis, and the error against the FP64 form with full reorthogonalization
@@ -610,7 +953,7 @@ def run_ours(args):
             slaq.profile_enable(True)
             e0.record(stream)
             for _ in range(2):
-                dp, _, _ = step(pp, key, slaq.REORTH_PARTIAL)
+                dp, _ = step(pp, key, slaq.REORTH_PARTIAL)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             kp = slaq.profile_read()
@@ -621,19 +964,26 @@ def run_ours(args):
                         "speedup_over_full_reorth": (ms_full / msp) if ms_full else None,
                         "dots_update_ms_per_step": (kp["dots"][0] + kp["update"][0]) / 2,
                         "full_projection_steps": int(fs.sum()), "of_steps": S - 1,
-                        "rel_err_vs_fp64": rel_errors(dp.double().cpu().numpy(), b, t_np)}
+                        "orthogonality": slaq.krylov_monitor(state[key]),
+                        "rel_err_vs_fp64": rel_errors(host(dp), b, t_np)}
         result["partial_reorth"] = pr
-        result["graph_replay"] = small_graph_replay()
+        for key in ("K64", "Kbf", "Kpfp32", "Kpfp64"):
+            if state.get(key) is not None:
+                state[key].close()
+                state[key] = None
+        torch.cuda.empty_cache()
+        if not dist:
+            result["graph_replay"] = small_graph_replay()
 
     # end to end through the host-memory entry point (pinned buffers)
-    if not args.quick:
+    if not args.quick and not dist:
         src_np_p, dst_np_p = src_h.numpy(), dst_h.numpy()
         e2e_times = []
         for i in range(1 + min(args.steps, 3)):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            out = slaq.descriptors_host(src_np_p, dst_np_p, n_nodes, t_np, kind=slaq.NORMALIZED,
-                                        flags=slaq.DROP_ISOLATED, nv=NV, s=S, seed=seed, precision=P)
+            slaq.descriptors_host(src_np_p, dst_np_p, n_nodes, t_np, kind=slaq.NORMALIZED,
+                                  flags=slaq.DROP_ISOLATED, nv=NV, s=S, seed=PROBE_SEED, precision=P)
             t1 = time.perf_counter()
             if i > 0:
                 e2e_times.append(t1 - t0)
@@ -643,8 +993,19 @@ def run_ours(args):
                          "d2h_bytes_per_step": int(8 * (3 * NT + 1)),
                          "ms_per_step": e2e_s * 1e3}
 
+    if state.get("K") is not None:
+        state["K"].close()
+        state["K"] = None
+    del src, dst
+    torch.cuda.empty_cache()
     if not args.quick and not args.no_batched:
-        result["batched_sbm5000"] = run_batched(args, dev, world, rank, tdist if dist else None)
+        result["batched_sbm5000"] = run_batched(args, dev, world, rank, tdist)
+    if not args.quick and not args.no_rmat24 and not dist:
+        result["rmat24_bf16"] = run_rmat24(dev, hbm, peak_src, gather_peak)
+        torch.cuda.empty_cache()
+    if not args.quick and args.pairs > 0 and not dist:
+        result["graph_pairs64"] = run_pairs(dev, args.pairs)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(src_np, dst_np, n_nodes)
     if rank == 0:
@@ -660,18 +1021,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64", "bf16"], default="fp32")
-    ap.add_argument("--quick", action="store_true", help="skip the FP64-form and end-to-end legs")
+    ap.add_argument("--quick", action="store_true", help="the headline step only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the SBM-batch leg")
+    ap.add_argument("--no-rmat24", action="store_true", help="skip the R-MAT 2^24 leg")
+    ap.add_argument("--pairs", type=int, default=PAIRS,
+                    help="graph pairs of the distance leg (an evenly spread subset below 64; 0 skips)")
     ap.add_argument("--kernel-capture", type=int, default=0,
                     help="profiling driver: run Lanczos this many times on the R-MAT graph and exit")
     ap.add_argument("--capture-batched", action="store_true",
                     help="with --kernel-capture: use the SBM batch instead of the R-MAT graph")
-    ap.add_argument("--cpu-baseline-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.cpu_baseline_worker:
-        cpu_baseline_worker(args.cpu_baseline_worker)
-        return
     if args.kernel_capture:
         kernel_capture(args)
         return

@@ -52,7 +52,10 @@ enum { SLAQ_DROP_ISOLATED = 1 };
  * tridiagonal eigensolve and the quadrature are FP64 in every form):
  *   SLAQ_FP64           basis, SpMM and reorthogonalization in FP64;
  *   SLAQ_FP32           basis, SpMM and reorthogonalization in FP32;
- *   SLAQ_FP32_BF16BASIS basis stored in BF16, SpMM and updates in FP32.   */
+ *   SLAQ_FP32_BF16BASIS basis stored in BF16, SpMM and updates in FP32.
+ * The FP32 and BF16-basis forms run normalized Laplacians only (spectrum in
+ * [0, 2]); on a combinatorial Laplacian slaq_lanczos returns
+ * SLAQ_EUNSUPPORTED. */
 enum { SLAQ_FP64 = 0, SLAQ_FP32 = 1, SLAQ_FP32_BF16BASIS = 2 };
 /* reorth_passes value for partial reorthogonalization (slaq_lanczos). */
 enum { SLAQ_REORTH_PARTIAL = 0 };
@@ -175,6 +178,22 @@ void slaq_graph_destroy(slaq_graph g);
 int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id,
                  int precision, int reorth_passes, void *stream, slaq_krylov *inout);
 
+/* slaq_lanczos over a range of the probe generator's probes: column p of the
+ * run is generator probe probe0 + p (the probe field of the counter above),
+ * so that runs over disjoint ranges of one seed -- one per GPU, or chunks
+ * that fit memory -- together hold the probes of one run over their union
+ * (Sec. 3.1, Eq. trace: the probes are independent).  Every per-probe output
+ * of column p (alpha, beta, m, Gauss rule, per-probe traces) equals that of
+ * column probe0 + p of a run from probe 0, up to rounding order (the dot
+ * products' summation order depends on the block width nv).
+ * 0 <= probe0 and probe0 + nv <= 65536, else SLAQ_EINVAL; everything else as
+ * for slaq_lanczos, which is this call with probe0 = 0.  A later
+ * slaq_lanczos_rerun keeps the range.  slaq_pool_probes_host combines the
+ * ranges' per-probe values into the estimate and standard error over all
+ * their probes. */
+int slaq_lanczos_probes(slaq_graph g, int nv, int probe0, int s, uint64_t seed, int graph_id,
+                        int precision, int reorth_passes, void *stream, slaq_krylov *inout);
+
 /* slaq_lanczos again on the same graph, sizes, form and reorthogonalization
  * as the handle's last slaq_lanczos / slaq_lanczos_batched call, with probes
  * from a new seed: the results equal that call's with `seed` bit for bit.
@@ -269,9 +288,23 @@ int slaq_trace_heat_cv(slaq_krylov k, const double *t, int nt, int degree, doubl
                        double *stderr_, double *per_probe, void *stream);
 
 /* Wave trace tr exp(-i t L): re[i] = sum cos(t lambda), im[i] = -sum sin(t lambda),
- * estimated as above; stderr arrays may be NULL. */
+ * estimated as above; stderr arrays may be NULL.  The BF16-basis form serves
+ * |t| * bound <= 20 only (t <= 10 on a normalized Laplacian, whose bound is
+ * 2): cos(t theta) turns its basis rounding into errors that grow with t
+ * (measured below 1e-5 of max |Re| up to that limit, up to 0.28 at t = 100).
+ * A larger t gives SLAQ_EUNSUPPORTED; for that form the call copies t to the
+ * host and synchronizes `stream` to check it. */
 int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im,
                     double *stderr_re, double *stderr_im, void *stream);
+
+/* Per-probe values of the wave trace (as slaq_trace_wave, with its limit on
+ * t for the BF16-basis form, before the mean
+ * over probes): re_pp[p][i] = n' sum_k tau2 cos(t_i theta) and im_pp[p][i] =
+ * -n' sum_k tau2 sin(t_i theta), float64[nv*nt] each ([G][nv][nt] for a
+ * batch).  With the per_probe outputs of the heat trace and the VNGE these
+ * are the values slaq_pool_probes_host pools across probe ranges. */
+int slaq_trace_wave_per_probe(slaq_krylov k, const double *t, int nt, double *re_pp,
+                              double *im_pp, void *stream);
 
 /* Von Neumann graph entropy (Definition 1, Sec. 2.1) of P = L / tr(L) for
  * the Laplacian the graph was built with: -sum mu ln mu over mu = theta/tr(L)
@@ -279,6 +312,19 @@ int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *
  * float64[nv] or NULL. */
 int slaq_trace_vnge(slaq_krylov k, double *out, double *stderr_, double *per_probe,
                     void *stream);
+
+/* Orthogonality monitor of the last run (not in the paper; the quantities
+ * that decide whether the Gauss rule of Eq. quadratic can be trusted):
+ *   *ortho_host    = max over probes and stored vectors j < k of
+ *                    |u_j^T u_k| / (||u_j|| ||u_k||), i.e. max |Q^T Q - I|
+ *                    off the diagonal, from the Gram entries the run
+ *                    measured (the last vector is left out where the run
+ *                    forms only its norm: the FP64 form, and partial
+ *                    reorthogonalization, whose unmeasured entries count 0);
+ *   *min_beta_host = the smallest beta_k over probes and k < m_p - 1
+ *                    (+inf if no probe has two steps).
+ * Either pointer may be NULL.  Synchronizes `stream`. */
+int slaq_krylov_monitor(slaq_krylov k, double *ortho_host, double *min_beta_host, void *stream);
 
 void slaq_krylov_destroy(slaq_krylov k);
 
@@ -304,36 +350,74 @@ int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int6
                           double *wave_re_host, double *wave_im_host, double *vnge_host,
                           void *stream);
 
+/* Hutchinson estimate and standard error over probes (Eq. trace) from
+ * per-probe values, on the host (needs no GPU): values_host[nprobe][len],
+ * row p holding probe p's values (for example the per-probe heat traces of
+ * several slaq_lanczos_probes ranges, concatenated in probe order);
+ * mean_host[j] = mean of column j; stderr_host[j] (or NULL) = sample standard
+ * deviation / sqrt(nprobe), NaN when nprobe = 1.  The sums run in the fixed
+ * order of the device quadrature kernels (Welford over the probe groups
+ * p mod 4, combined pairwise in group order), so ranges pooled here reproduce
+ * the estimate of one run over all their probes up to the rounding of the
+ * per-probe values.  nprobe < 1, len < 1 or NULL values/mean: SLAQ_EINVAL. */
+int slaq_pool_probes_host(const double *values_host, int nprobe, int len, double *mean_host,
+                          double *stderr_host);
+
 /* ------------------------------------------------ allocation-free variant */
 
 /* Heat trace from Lanczos coefficients without any device allocation.
- * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory at the time they call, for example code
- * that must not call cudaMalloc (or a caching allocator) while it records
- * work into a CUDA graph, or an application whose memory manager owns all
- * device memory and hands libraries only the buffers it created.
- * It computes what slaq_trace_heat computes after slaq_lanczos (the Gauss
- * rule of every probe's tridiagonal, then Eq. slq for exp(-t theta)), but
- * takes the coefficients as inputs and keeps the Gauss nodes and weights in
- * a fixed scratch array inside the library instead of a handle:
+ * The paper has no counterpart.  Some callers cannot allocate device memory
+ * when they call into a library: an application whose own memory manager
+ * owns all device memory and hands libraries only buffers it created, or a
+ * latency-critical loop where a cudaMalloc (which may synchronize the device
+ * or fail once the pool is carved up) is not allowed.  For them this entry
+ * point computes what slaq_trace_heat computes after slaq_lanczos, from
+ * coefficients the caller holds, and keeps its scratch (the Gauss nodes and
+ * weights) in a fixed array inside the library instead of a handle:
+ *   out[i] = (n / nv) sum_p sum_k tau2_{p,k} exp(-t_i theta_{p,k}), where
+ *   theta_{p,k} and tau2_{p,k} are the eigenvalues and squared first
+ *   eigenvector components of probe p's m[p] x m[p] tridiagonal matrix;
+ *   stderr_[i] = sample std over the probes / sqrt(nv) (NaN when nv = 1).
+ * Arguments (device arrays unless noted):
  *   alpha, beta  float64[nv*s] as written by slaq_krylov_export (row p holds
  *                alpha_0..alpha_{m_p-1} and beta_0..beta_{m_p-2});
- *   m            int32[nv]; n the node count n'; t float64[nt];
+ *   m            int32[nv]: each value is clamped to [0, s] before use;
+ *   n            the node count n' (host value); t float64[nt];
  *   out, stderr_ float64[nt] (stderr_ may be NULL);
- *   status       int32[1] or NULL: receives 0, or 1 if an eigensolve did
- *                not converge.
+ *   status       int32[1] or NULL: receives 0, or the OR of 1 (an eigensolve
+ *                did not converge) and 2 (some m[p] was outside [0, s] and
+ *                was clamped).
  * Limits: nv <= 512, s <= 64 (the scratch holds 512 x 64 nodes and
- * weights, 512 KiB per device, kept until the process exits); larger sizes
- * return SLAQ_EINVAL.  It calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * weights and 512 rule sizes, about 514 KiB per device, kept until the
+ * process exits); larger sizes return SLAQ_EINVAL before any work is
+ * enqueued.  It calls no cudaMalloc, cudaFree or other allocating routine.
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.
  * All calls on a device share the one scratch array, which keeps the last
- * call's contents: calls whose GPU work overlaps (other streams, other
- * threads) race and must be ordered by the caller. */
+ * call's contents (the call clears its status word itself): calls whose GPU
+ * work overlaps (other streams, other threads) race and must be ordered by
+ * the caller. */
 int slaq_trace_heat_tridiag_static(const double *alpha, const double *beta, const int32_t *m,
                                    int nv, int s, int64_t n, const double *t, int nt, double *out,
                                    double *stderr_, int32_t *status, void *stream);
+
+/* ------------------------------------------------------------ test hooks */
+
+/* Failure injection for the error paths (off by default; for tests): the
+ * nth allocation the library makes after this call -- device memory from
+ * cudaMalloc or the stream-ordered pool, or pinned host memory -- fails as
+ * if the device were out of memory, and the call that makes it returns
+ * SLAQ_ENOMEM after releasing what it had allocated.  The hook fires once;
+ * nth <= 0 disarms it.  A handle whose run failed this way stays valid to
+ * destroy or to run again; reading its results returns SLAQ_EINVAL.
+ * Returns SLAQ_OK.  Needs no GPU. */
+int slaq_debug_fail_alloc(int64_t nth);
+
+/* Number of allocations the library currently holds (graph and Krylov
+ * handles, the temporaries of calls in progress), for leak checks around
+ * failing calls.  Needs no GPU. */
+int64_t slaq_debug_live_allocs(void);
 
 /* ------------------------------------------------------------- profiling */
 
@@ -360,6 +444,16 @@ int slaq_profile_enable(int on);
  * launches of one class since the last slaq_profile_enable(1).  Launches
  * are counted whether or not timing is on.  Waits for the recorded events. */
 int slaq_profile_read(int category, double *ms_host, int64_t *launches_host);
+
+/* The gather ceiling the SpMM works against (profiling; not part of the
+ * method): every stored entry of L gathers one basis row of nv values, far
+ * more bytes than reach HBM, and the L2 serves them.  This times random
+ * gathers of row_bytes-wide rows (a multiple of 16 in [16, 512], one 16-byte
+ * vector per lane, as the SpMM reads them) from an L2-resident 64 MiB table
+ * on the current device and writes the rate in TB/s of gathered bytes to
+ * *tbps_host.  Allocates and frees its table; synchronizes the device's
+ * legacy default stream. */
+int slaq_profile_gather_peak(int row_bytes, double *tbps_host);
 
 /* Gauss rule of one symmetric tridiagonal matrix on the host, with the same
  * implicit-shift QR code the GPU kernel runs (Golub & Van Loan, Sec. 8.3):

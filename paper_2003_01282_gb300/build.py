@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libslaq.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["api.cu", "build.cu", "lanczos.cu", "quad.cu", "tune.cu"]
+SOURCES = ["api.cu", "build.cu", "lanczos.cu", "quad.cu", "tune.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

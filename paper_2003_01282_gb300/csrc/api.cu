@@ -2,9 +2,13 @@
 // checks, device check, error reporting; the work is in build.cu,
 // lanczos.cu and quad.cu.
 #include <algorithm>
+#include <atomic>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 #include "tridiag.cuh"
@@ -81,7 +85,28 @@ int num_sms() {
   return std::max(1, g_dev[dev].sms);
 }
 
+// ------------------------------------------------------------ allocations
+// Every device (and pinned host) allocation of the library goes through
+// these functions: they count the allocations the library holds, and a test
+// hook (slaq_debug_fail_alloc) can make the n-th one fail as an out-of-memory
+// device would, so that every SLAQ_ENOMEM path can be walked.
+namespace {
+std::atomic<int64_t> g_live_allocs{0};
+std::atomic<int64_t> g_fail_at{0};     // 0: off
+std::atomic<int64_t> g_alloc_seen{0};  // allocations since the hook was armed
+}  // namespace
+
+static int alloc_gate(size_t bytes) {
+  const int64_t f = g_fail_at.load();
+  if (f > 0 && g_alloc_seen.fetch_add(1) + 1 == f)
+    return set_error(SLAQ_ENOMEM, "allocation of %zu bytes failed (injected by slaq_debug_fail_alloc)",
+                     bytes);
+  return SLAQ_OK;
+}
+
 int dalloc(void **p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  SLAQ_TRY(alloc_gate(bytes));
   cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -89,11 +114,53 @@ int dalloc(void **p, size_t bytes, cudaStream_t st) {
     return set_error(SLAQ_ENOMEM, "cudaMallocAsync of %zu bytes failed: %s", bytes,
                      cudaGetErrorString(e));
   }
+  ++g_live_allocs;
   return SLAQ_OK;
 }
 
 void dfree(void *p, cudaStream_t st) {
-  if (p) cudaFreeAsync(p, st);
+  if (!p) return;
+  cudaFreeAsync(p, st);
+  --g_live_allocs;
+}
+
+int dmalloc(void **p, size_t bytes) {
+  *p = nullptr;
+  SLAQ_TRY(alloc_gate(bytes));
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_error(SLAQ_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  ++g_live_allocs;
+  return SLAQ_OK;
+}
+
+void dmfree(void *p) {
+  if (!p) return;
+  cudaFree(p);
+  --g_live_allocs;
+}
+
+int hmalloc(void **p, size_t bytes) {
+  *p = nullptr;
+  SLAQ_TRY(alloc_gate(bytes));
+  cudaError_t e = cudaMallocHost(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_error(SLAQ_ENOMEM, "cudaMallocHost of %zu bytes failed: %s", bytes,
+                     cudaGetErrorString(e));
+  }
+  ++g_live_allocs;
+  return SLAQ_OK;
+}
+
+void hmfree(void *p) {
+  if (!p) return;
+  cudaFreeHost(p);
+  --g_live_allocs;
 }
 
 // ---------------------------------------------------------------- profiler
@@ -138,6 +205,14 @@ void prof_collect_locked() {
   g_prof_pairs.clear();
 }
 }  // namespace
+
+void nvtx_push(int cat) {
+  static const char *names[SLAQ_PROF_NCAT] = {"slaq:build",  "slaq:probes", "slaq:spmm",
+                                              "slaq:dots",   "slaq:update", "slaq:reduce",
+                                              "slaq:ritz",   "slaq:trace",  "slaq:distance"};
+  nvtxRangePushA(cat >= 0 && cat < SLAQ_PROF_NCAT ? names[cat] : "slaq");
+}
+void nvtx_pop() { nvtxRangePop(); }
 
 ProfPause::ProfPause() : saved(tl_prof_paused) { tl_prof_paused = true; }
 ProfPause::~ProfPause() { tl_prof_paused = saved; }
@@ -277,6 +352,20 @@ int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int p
   return SLAQ_OK;
 }
 
+int slaq_lanczos_probes(slaq_graph g, int nv, int probe0, int s, uint64_t seed, int graph_id,
+                        int precision, int reorth_passes, void *stream, slaq_krylov *inout) {
+  SLAQ_TRY(device_check());
+  cudaStream_t st = as_stream(stream);
+  SLAQ_TRY(run_lanczos(g, nv, s, seed, graph_id, precision, reorth_passes, st, inout, nullptr,
+                       probe0));
+  int32_t status = 0;
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, (*inout)->status, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
+  return SLAQ_OK;
+}
+
 int slaq_lanczos_rerun(slaq_krylov k, uint64_t seed, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
@@ -312,6 +401,7 @@ int slaq_probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, 
 int slaq_krylov_full_steps(slaq_krylov k, int32_t *full_steps, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
   SLAQ_TRY(slaq::full_steps(k, full_steps, as_stream(stream)));
   return SLAQ_OK;
 }
@@ -319,6 +409,7 @@ int slaq_krylov_full_steps(slaq_krylov k, int32_t *full_steps, void *stream) {
 int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
   cudaStream_t st = as_stream(stream);
   const size_t ns = (size_t)k->n_graphs * k->nv * k->s;
   if (alpha) SLAQ_CHECK_CUDA(cudaMemcpyAsync(alpha, k->alpha, ns * 8, cudaMemcpyDeviceToDevice, st));
@@ -332,6 +423,7 @@ int slaq_krylov_export(slaq_krylov k, double *alpha, double *beta, int32_t *m, v
 int slaq_ritz_export(slaq_krylov k, double *theta, double *tau2, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
   cudaStream_t st = as_stream(stream);
   const size_t ns = (size_t)k->n_graphs * k->nv * k->s;
   if (theta) SLAQ_CHECK_CUDA(cudaMemcpyAsync(theta, k->theta, ns * 8, cudaMemcpyDeviceToDevice, st));
@@ -352,6 +444,7 @@ int slaq_trace_heat(slaq_krylov k, const double *t, int nt, double *out, double 
                     double *per_probe, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
   return trace_heat(k, t, nt, out, stderr_, per_probe, as_stream(stream));
 }
 
@@ -359,6 +452,7 @@ int slaq_trace_heat_cv(slaq_krylov k, const double *t, int nt, int degree, doubl
                        double *stderr_, double *per_probe, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
   return trace_heat_cv(k, t, nt, degree, out, stderr_, per_probe, as_stream(stream));
 }
 
@@ -366,12 +460,23 @@ int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *
                     double *stderr_re, double *stderr_im, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
   return trace_wave(k, t, nt, re, im, stderr_re, stderr_im, as_stream(stream));
+}
+
+int slaq_trace_wave_per_probe(slaq_krylov k, const double *t, int nt, double *re_pp,
+                              double *im_pp, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  if (!re_pp || !im_pp) return set_error(SLAQ_EINVAL, "per-probe outputs must not be NULL");
+  SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
+  return trace_wave(k, t, nt, nullptr, nullptr, nullptr, nullptr, as_stream(stream), re_pp, im_pp);
 }
 
 int slaq_trace_vnge(slaq_krylov k, double *out, double *stderr_, double *per_probe, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
   return trace_vnge(k, out, stderr_, per_probe, as_stream(stream));
 }
 
@@ -379,6 +484,13 @@ void slaq_krylov_destroy(slaq_krylov k) {
   if (!k) return;
   cudaDeviceSynchronize();
   krylov_free(k);
+}
+
+int slaq_krylov_monitor(slaq_krylov k, double *ortho_host, double *min_beta_host, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
+  return krylov_monitor(k, ortho_host, min_beta_host, as_stream(stream));
 }
 
 int slaq_distance(const double *a, const double *b, int nt, int kind, double *out, void *stream) {
@@ -404,7 +516,7 @@ int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int6
     slaq_krylov k = nullptr;
     ~Bufs() {
       cudaStreamSynchronize(st);
-      for (void *x : p) cudaFreeAsync(x, st);
+      for (void *x : p) dfree(x, st);
       if (k) krylov_free(k);
       if (g) graph_free(g, st);
       cudaStreamSynchronize(st);
@@ -455,6 +567,14 @@ int slaq_trace_heat_tridiag_static(const double *alpha, const double *beta, cons
                            as_stream(stream));
 }
 
+int slaq_debug_fail_alloc(int64_t nth) {
+  g_alloc_seen = 0;
+  g_fail_at = nth > 0 ? nth : 0;
+  return SLAQ_OK;
+}
+
+int64_t slaq_debug_live_allocs(void) { return g_live_allocs.load(); }
+
 int slaq_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mutex);
   if (on) {
@@ -468,6 +588,12 @@ int slaq_profile_enable(int on) {
   return SLAQ_OK;
 }
 
+int slaq_profile_gather_peak(int row_bytes, double *tbps_host) {
+  SLAQ_TRY(device_check());
+  if (!tbps_host) return set_error(SLAQ_EINVAL, "NULL output");
+  return profile_gather_peak(row_bytes, tbps_host);
+}
+
 int slaq_profile_read(int category, double *ms, int64_t *launches) {
   if (category < 0 || category >= SLAQ_PROF_NCAT)
     return set_error(SLAQ_EINVAL, "unknown profile category %d", category);
@@ -475,6 +601,41 @@ int slaq_profile_read(int category, double *ms, int64_t *launches) {
   prof_collect_locked();
   if (ms) *ms = g_prof_ms[category];
   if (launches) *launches = g_prof_launch[category];
+  return SLAQ_OK;
+}
+
+int slaq_pool_probes_host(const double *values, int nprobe, int len, double *mean,
+                          double *stderr_) {
+  if (!values || !mean || nprobe < 1 || len < 1)
+    return set_error(SLAQ_EINVAL, "pooling needs values, mean, nprobe >= 1 and len >= 1");
+  // Welford means and squared deviations over the probe groups p mod 4, then
+  // Chan's pairwise combination in group order: the order the device
+  // quadrature kernels use, so pooled shards of one run reproduce it.
+  constexpr int kGroups = 4;
+  for (int j = 0; j < len; ++j) {
+    double gm[kGroups] = {0}, g2[kGroups] = {0};
+    int gc[kGroups] = {0};
+    for (int h = 0; h < kGroups; ++h)
+      for (int p = h; p < nprobe; p += kGroups) {
+        const double x = values[(size_t)p * len + j];
+        ++gc[h];
+        const double d = x - gm[h];
+        gm[h] += d / gc[h];
+        g2[h] += d * (x - gm[h]);
+      }
+    double M = gm[0], S2 = g2[0];
+    int N = gc[0];
+    for (int h = 1; h < kGroups; ++h) {
+      if (gc[h] == 0) continue;
+      const double delta = gm[h] - M;
+      const int nn = N + gc[h];
+      M += delta * gc[h] / nn;
+      S2 += g2[h] + delta * delta * ((double)N * gc[h] / nn);
+      N = nn;
+    }
+    mean[j] = M;
+    if (stderr_) stderr_[j] = nprobe > 1 ? std::sqrt(S2 / (nprobe - 1) / nprobe) : NAN;
+  }
   return SLAQ_OK;
 }
 

@@ -120,6 +120,11 @@ int exclusive_scan(const TI *in, int64_t n, int64_t *out, int64_t *total_dev, cu
   int64_t nb = std::max<int64_t>(1, ceil_div(n, kScanTile));
   int64_t *bsum = nullptr;
   SLAQ_TRY(dalloc_t(&bsum, nb, st));
+  struct Free {
+    int64_t *p;
+    cudaStream_t st;
+    ~Free() { dfree(p, st); }
+  } free_bsum{bsum, st};
   if (n > 0) {
     ++tl_launches;
     k_scan_tile_sums<TI><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum);
@@ -134,7 +139,6 @@ int exclusive_scan(const TI *in, int64_t n, int64_t *out, int64_t *total_dev, cu
     k_scan_apply<TI><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum, out);
   }
   SLAQ_CHECK_LAUNCH("exclusive_scan");
-  dfree(bsum, st);
   return SLAQ_OK;
 }
 
@@ -268,6 +272,16 @@ int radix_sort(uint64_t **keys, uint64_t **keys_alt, double **pay, double **pay_
   const int64_t ntiles = ceil_div(n, kRsTile);
   uint32_t *counts = nullptr;
   int64_t *offsets = nullptr, *total = nullptr;
+  struct Free {
+    uint32_t **c;
+    int64_t **o, **t;
+    cudaStream_t st;
+    ~Free() {
+      dfree(*c, st);
+      dfree(*o, st);
+      dfree(*t, st);
+    }
+  } free_tmp{&counts, &offsets, &total, st};
   SLAQ_TRY(dalloc_t(&counts, 256 * ntiles, st));
   SLAQ_TRY(dalloc_t(&offsets, 256 * ntiles, st));
   SLAQ_TRY(dalloc_t(&total, 1, st));
@@ -301,9 +315,6 @@ int radix_sort(uint64_t **keys, uint64_t **keys_alt, double **pay, double **pay_
     SLAQ_CHECK_LAUNCH("radix_scatter");
     std::swap(*keys, *keys_alt);
   }
-  dfree(counts, st);
-  dfree(offsets, st);
-  dfree(total, st);
   return SLAQ_OK;
 }
 
@@ -796,8 +807,7 @@ void graph_free(slaq_graph g, cudaStream_t st) {
                   g->x_rowptr, g->x_colidx, g->x_vals, g->x_vals32, g->x_diag, g->x_scale,
                   g->x_diag32, g->x_scale32, g->x_old_id, g->goff_dev, g->gn_dev,
                   g->gtrace_dev, g->gbound_dev, g->x_graph, g->gtrace2_dev};
-  for (void *p : ptrs)
-    if (p) cudaFreeAsync(p, st);
+  for (void *p : ptrs) dfree(p, st);
   delete g;
 }
 

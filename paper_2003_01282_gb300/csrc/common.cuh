@@ -48,18 +48,38 @@ struct ProfPause {
   ProfPause();
   ~ProfPause();
 };
+// A kernel class on the host timeline: an NVTX range (visible to Nsight
+// tools when one is attached; a no-op otherwise) and, when the profiler is
+// on, CUDA events on the launch stream.
+void nvtx_push(int cat);
+void nvtx_pop();
 struct ProfScope {
   int cat;
   cudaStream_t st;
   int64_t start;
-  ProfScope(int c, cudaStream_t s) : cat(c), st(s), start(tl_launches) { prof_begin(c, s); }
-  ~ProfScope() { prof_end(cat, st, tl_launches - start); }
+  ProfScope(int c, cudaStream_t s) : cat(c), st(s), start(tl_launches) {
+    nvtx_push(c);
+    prof_begin(c, s);
+  }
+  ~ProfScope() {
+    prof_end(cat, st, tl_launches - start);
+    nvtx_pop();
+  }
 };
 int num_sms();             // streaming multiprocessors of the current device
 
-// stream-ordered device allocation (the device's default memory pool)
+// Allocations (api.cu).  Every allocation of the library goes through these:
+// they keep the count slaq_debug_live_allocs reports and honour the test
+// hook slaq_debug_fail_alloc.  dalloc/dfree: stream-ordered, from the
+// device's default memory pool; dmalloc/dmfree: cudaMalloc/cudaFree;
+// hmalloc/hmfree: pinned host memory.  On failure *p is NULL and the status
+// is SLAQ_ENOMEM.
 int dalloc(void **p, size_t bytes, cudaStream_t st);
 void dfree(void *p, cudaStream_t st);
+int dmalloc(void **p, size_t bytes);
+void dmfree(void *p);
+int hmalloc(void **p, size_t bytes);
+void hmfree(void *p);
 
 template <typename T>
 inline int dalloc_t(T **p, size_t count, cudaStream_t st) {
@@ -162,6 +182,8 @@ struct slaq_krylov_s {
   int device = -1;
   int nv = 0, s = 0, ld = 0, precision = 0, reorth = 1;  // reorth 0: partial
   int graph_id = 0;
+  int probe0 = 0;         // generator index of the first probe (probe ranges)
+  bool ready = false;     // the last run completed: its buffers and results are valid
   uint64_t seed = 0;
   int64_t n = 0;          // n' of the last run
   int64_t n_cap = 0;      // rows the workspace holds
@@ -189,7 +211,7 @@ struct slaq_krylov_s {
   int32_t *m = nullptr;     // [nv]
   double *theta = nullptr;  // [nv][s]
   double *tau2 = nullptr;   // [nv][s]
-  int32_t *status = nullptr;  // [1] device-side error flags
+  int32_t *status = nullptr;  // [8]: [0] device-side error flags; bytes 8..23: monitor words
   uint32_t *hcount = nullptr; // [n_heavy * slices] arrival counters of split rows (kept zero)
   int64_t hcount_cap = 0;
   // batches: G graphs; per-graph arrays are [G][...] (alpha [G][nv][s], ...)
@@ -244,12 +266,16 @@ void graph_register(slaq_graph g);             // gives g its uid and marks it a
 bool graph_alive(slaq_graph g, uint64_t uid);  // g not freed since it got uid
 int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
                 int reorth, cudaStream_t st, slaq_krylov *inout,
-                const slaq_tuning *tune = nullptr);
+                const slaq_tuning *tune = nullptr, int probe0 = 0);
 int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *out);
 int lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t seed, int graph_id,
                     int precision, int reorth, const char *tune_cache, cudaStream_t st,
                     slaq_krylov *inout);
 void krylov_free(slaq_krylov k);
+// SLAQ_OK if k holds a completed run (every buffer a later call reads is in
+// place), else SLAQ_EINVAL: a run that failed part-way (for example out of
+// memory) leaves the handle destroyable and reusable but not readable
+int krylov_ready(slaq_krylov k);
 int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st);
 int full_steps(slaq_krylov k, int32_t *out, cudaStream_t st);
 int lanczos_rerun(slaq_krylov k, uint64_t seed, cudaStream_t st);
@@ -259,9 +285,11 @@ int trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *se,
 int trace_heat_cv(slaq_krylov k, const double *t, int nt, int degree, double *out, double *se,
                   double *per_probe, cudaStream_t st);
 int trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im, double *se_re,
-               double *se_im, cudaStream_t st);
+               double *se_im, cudaStream_t st, double *pp_re = nullptr, double *pp_im = nullptr);
 int trace_vnge(slaq_krylov k, double *out, double *se, double *per_probe, cudaStream_t st);
 int distance(const double *a, const double *b, int nt, int kind, double *out, cudaStream_t st);
+int krylov_monitor(slaq_krylov k, double *ortho, double *min_beta, cudaStream_t st);
+int profile_gather_peak(int row_bytes, double *tbps);
 int trace_heat_static(const double *alpha, const double *beta, const int32_t *m, int nv, int s,
                       int64_t n, const double *t, int nt, double *out, double *se,
                       int32_t *status_out, cudaStream_t st);

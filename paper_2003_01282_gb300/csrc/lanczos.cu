@@ -183,10 +183,12 @@ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+// Column p of the block is generator probe probe0 + p (probe ranges split one
+// seed's probes over several runs, e.g. one per GPU).
 template <int P>
 __global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id,
                              const int32_t *xgraph, Slc S, int nv, const uint64_t *seed_p,
-                             uint64_t graph_id, const float *yscale, float *Y0) {
+                             uint64_t graph_id, uint64_t probe0, const float *yscale, float *Y0) {
   using TB = typename Form<P>::TB;
   const uint64_t seed = *seed_p;  // in device memory, so that a captured run can be replayed
                                   // with another seed
@@ -203,7 +205,7 @@ __global__ void k_probe_init(typename Form<P>::TB *U0, const int64_t *old_id,
     float v = 0.0f;
     if (p < nv) {
       const uint64_t gfield = (graph_id + (uint64_t)xgraph[i]) & 0xffffull;
-      const uint64_t c = (gfield << 48) | ((uint64_t)p << 32) | (uint64_t)old_id[i];
+      const uint64_t c = (gfield << 48) | (((uint64_t)p + probe0) << 32) | (uint64_t)old_id[i];
       const uint64_t z = splitmix64_mix(seed + 0x9E3779B97F4A7C15ull * (c + 1ull));
       v = (z >> 63) ? -1.0f : 1.0f;
     }
@@ -1695,16 +1697,19 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st, bool launch_only
     for (size_t q = 0; q + 1 < K->hd_goff.size(); ++q)
       K->max_chunks_per_graph = std::max(K->max_chunks_per_graph, K->hd_goff[q + 1] - K->hd_goff[q]);
     int64_t c0 = K->dcap, c1 = K->dcap, c2 = K->dcap;
+    K->dcap = 0;  // until the three tables below are in place
     SLAQ_TRY(upload(&K->d_row0, &c0, K->hd_row0, st));
     SLAQ_TRY(upload(&K->d_rows, &c1, K->hd_rows, st));
     SLAQ_TRY(upload(&K->d_goff, &c2, K->hd_goff, st));
     K->dcap = std::min({c0, c1, c2});
     int64_t u0 = K->ucap, u1 = K->ucap, u2 = K->ucap;
+    K->ucap = 0;
     SLAQ_TRY(upload(&K->u_row0, &u0, K->hu_row0, st));
     SLAQ_TRY(upload(&K->u_rows, &u1, K->hu_rows, st));
     SLAQ_TRY(upload(&K->u_graph, &u2, K->hu_graph, st));
     K->ucap = std::min({u0, u1, u2});
     if ((int64_t)K->n_dchunks * kMaxSub > K->G) {
+      K->G = 0;
       SLAQ_TRY(grow(&K->part, (size_t)K->n_dchunks * kMaxSub * 2 * K->s * K->ld));
       K->G = K->n_dchunks * kMaxSub;
     }
@@ -1718,7 +1723,8 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st, bool launch_only
     ++tl_launches;
     k_probe_init<P><<<(unsigned)std::min<int64_t>(ceil_div(n * K->ld, 256), 152LL * 64), 256, 0,
                       st>>>(static_cast<TB *>(K->U), gr->x_old_id, gr->x_graph, geo.S, K->nv,
-                            K->seed_dev, (uint64_t)K->graph_id, K->ymode ? K->yscale : nullptr,
+                            K->seed_dev, (uint64_t)K->graph_id, (uint64_t)K->probe0,
+                            K->ymode ? K->yscale : nullptr,
                             K->ymode ? K->Y : nullptr);
   }
   SLAQ_CHECK_LAUNCH("probe_init");
@@ -1768,18 +1774,15 @@ double default_tol(int precision) {
   return precision == SLAQ_FP64 ? 1e-10 : 1e-4;
 }
 
+// Replaces *p by a new allocation of count elements (the old contents are
+// dropped).  On failure *p is NULL: callers reset the capacity that covers
+// *p before growing, so a later call on the handle grows it again instead of
+// launching a kernel on NULL.
 template <typename T>
 int grow(T **p, size_t count) {
-  if (*p) cudaFree(*p);
+  dmfree(*p);
   *p = nullptr;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    return set_error(SLAQ_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
-                     cudaGetErrorString(e));
-  }
-  return SLAQ_OK;
+  return dmalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
 }
 
 }  // namespace
@@ -1832,11 +1835,10 @@ void krylov_free(slaq_krylov k) {
                   k->gbound,
                   k->d_row0, k->d_rows, k->d_goff, k->u_row0, k->u_rows, k->u_graph,
                   k->pro_full, k->pro_any, k->omega};
-  for (void *p : ptrs)
-    if (p) cudaFree(p);
-  if (k->pro_any_host) cudaFreeHost(k->pro_any_host);
+  for (void *p : ptrs) dmfree(p);
+  hmfree(k->pro_any_host);
   if (k->ev_flag) cudaEventDestroy(k->ev_flag);
-  if (k->seed_dev) cudaFree(k->seed_dev);
+  dmfree(k->seed_dev);
   if (k->gexec) cudaGraphExecDestroy(k->gexec);
   if (k->cap) cudaStreamDestroy(k->cap);
   if (k->ev_fork) cudaEventDestroy(k->ev_fork);
@@ -1847,9 +1849,12 @@ void krylov_free(slaq_krylov k) {
 }
 
 int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int precision,
-                int reorth, cudaStream_t st, slaq_krylov *inout, const slaq_tuning *tune) {
+                int reorth, cudaStream_t st, slaq_krylov *inout, const slaq_tuning *tune,
+                int probe0) {
   if (!g || !inout) return set_error(SLAQ_EINVAL, "NULL graph or output handle");
   if (nv < 1 || nv > 512) return set_error(SLAQ_EINVAL, "nv must be in [1, 512]");
+  if (probe0 < 0 || (int64_t)probe0 + nv > 65536)
+    return set_error(SLAQ_EINVAL, "probes probe0 .. probe0 + nv - 1 must lie in [0, 65536)");
   if (s < 1 || s > 64) return set_error(SLAQ_EINVAL, "s must be in [1, 64]");
   if (graph_id < 0 || graph_id > 0xffff) return set_error(SLAQ_EINVAL, "graph_id must be < 65536");
   if (precision != SLAQ_FP64 && precision != SLAQ_FP32 && precision != SLAQ_FP32_BF16BASIS)
@@ -1860,6 +1865,12 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     return set_error(SLAQ_EUNSUPPORTED,
                      "partial reorthogonalization needs an FP64 or FP32 basis (BF16 storage "
                      "rounds above the semi-orthogonality level)");
+  if (precision != SLAQ_FP64 && g->kind == SLAQ_COMBINATORIAL)
+    return set_error(SLAQ_EUNSUPPORTED,
+                     "the FP32 and BF16-basis forms need the normalized Laplacian: on L = D - A "
+                     "(spectrum up to 2 max d) their basis rounding moves the Ritz values by "
+                     "u * 2 max d, which exp(-t theta) turns into heat-trace errors above 1e-4; "
+                     "run combinatorial Laplacians in SLAQ_FP64");
   if (g->n < 1) return set_error(SLAQ_EINVAL, "graph has no nodes");
   if (g->n > (1LL << 31)) return set_error(SLAQ_EUNSUPPORTED, "too many nodes");
   const int ld = row_ld(nv, precision);
@@ -1884,16 +1895,21 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     slaq_krylov *K;
     bool fresh;
     ~Guard() {
-      if (fresh && *K) krylov_free(*K);
+      if (fresh && *K) {
+        cudaDeviceSynchronize();  // launches of the failed run may still read its buffers
+        krylov_free(*K);
+      }
     }
   } guard{&K, fresh};
   if (graph_id + g->n_graphs - 1 > 0xffff)
     return set_error(SLAQ_EINVAL, "graph_id + n_graphs - 1 must be < 65536");
+  K->ready = false;  // until this run has completed
   K->tune = tune ? *tune : slaq_tuning();
   const int64_t n = g->n;
   const int G = g->n_graphs;
   const Geometry geo = geometry(precision, ld, n, num_sms(), K->tune);
   if (n > K->n_cap) {
+    K->n_cap = 0;  // until every buffer below is grown
     SLAQ_TRY(grow(reinterpret_cast<unsigned char **>(&K->U), (size_t)s * n * ld * basis_bytes(precision)));
     SLAQ_TRY(grow(reinterpret_cast<unsigned char **>(&K->Z), (size_t)n * ld * work_bytes(precision)));
     if (precision == SLAQ_FP32) SLAQ_TRY(grow(&K->Y, (size_t)n * ld));
@@ -1907,12 +1923,14 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   {
     const int64_t need = std::max<int64_t>(1, g->n_heavy * geo.S.nslices());
     if (need > K->hcount_cap) {
+      K->hcount_cap = 0;
       SLAQ_TRY(grow(&K->hcount, (size_t)need));
       SLAQ_CHECK_CUDA(cudaMemsetAsync(K->hcount, 0, need * sizeof(uint32_t), st));
       K->hcount_cap = need;
     }
   }
   if (G > K->gcap) {
+    K->gcap = 0;  // until every per-graph array below is grown
     const size_t ns = (size_t)G * nv * s;
     SLAQ_TRY(grow(&K->dsum, (size_t)G * s * ld));
     SLAQ_TRY(grow(&K->coef, (size_t)G * s * ld));
@@ -1931,16 +1949,19 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     SLAQ_TRY(grow(&K->gbound, (size_t)G));
     K->gcap = G;
   }
-  if (!K->status) SLAQ_TRY(grow(&K->status, 1));
+  // status word (int32 [0]), then two 64-bit words at byte 8 for the monitor
+  if (!K->status) SLAQ_TRY(grow(&K->status, 8));
   if (reorth == 0 && G > K->pro_gcap) {
+    K->pro_gcap = 0;
     SLAQ_TRY(grow(&K->pro_full, (size_t)G * (s + 2)));
     SLAQ_TRY(grow(&K->omega, (size_t)G * nv * 3 * s));
     K->pro_gcap = G;
   }
-  if (reorth == 0 && !K->pro_any) {
-    SLAQ_TRY(grow(&K->pro_any, (size_t)s + 2));
-    SLAQ_CHECK_CUDA(cudaMallocHost(&K->pro_any_host, (size_t)(s + 2) * sizeof(int32_t)));
-    SLAQ_CHECK_CUDA(cudaEventCreateWithFlags(&K->ev_flag, cudaEventDisableTiming));
+  if (reorth == 0) {
+    if (!K->pro_any) SLAQ_TRY(grow(&K->pro_any, (size_t)s + 2));
+    if (!K->pro_any_host)
+      SLAQ_TRY(hmalloc(reinterpret_cast<void **>(&K->pro_any_host), (size_t)(s + 2) * sizeof(int32_t)));
+    if (!K->ev_flag) SLAQ_CHECK_CUDA(cudaEventCreateWithFlags(&K->ev_flag, cudaEventDisableTiming));
   }
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gn, g->gn_dev, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(K->gtrace2, g->gtrace2_dev, G * sizeof(double),
@@ -1958,6 +1979,7 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   K->last_g = g;
   K->last_uid = g->uid;
   K->graph_id = graph_id;
+  K->probe0 = probe0;
   K->reorth = reorth;
   K->n = n;
   K->n_graphs = G;
@@ -1971,8 +1993,16 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   else r = lanczos_form<SLAQ_FP32_BF16BASIS>(g, K, st, false);
   if (r != SLAQ_OK) return r;
   SLAQ_TRY(run_ritz(K, st));
+  K->ready = true;
   *inout = K;
   guard.fresh = false;  // the caller owns it now
+  return SLAQ_OK;
+}
+
+int krylov_ready(slaq_krylov K) {
+  if (!K) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  if (!K->ready)
+    return set_error(SLAQ_EINVAL, "the Krylov handle's last run did not complete; run it again");
   return SLAQ_OK;
 }
 
@@ -1983,6 +2013,7 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
 // reorthogonalization decides on the host between steps and is not replayed.
 int lanczos_rerun(slaq_krylov K, uint64_t seed, cudaStream_t st) {
   if (!K || !K->last_g) return set_error(SLAQ_EINVAL, "Krylov handle has no run to replay");
+  SLAQ_TRY(krylov_ready(K));
   if (!graph_alive(K->last_g, K->last_uid))
     return set_error(SLAQ_EINVAL, "the graph of the run to replay has been destroyed");
   if (K->reorth == 0)

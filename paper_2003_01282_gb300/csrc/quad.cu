@@ -6,6 +6,7 @@
 // are deterministic.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -18,13 +19,19 @@ constexpr int kMaxS = 64;
 constexpr int kMaxNv = 512;
 
 // One thread per (graph, probe) problem; problems are rows of [total][s].
+// The rule size m[p] is clamped to [0, s] (s <= kMaxS): a value outside that
+// range, possible only where the caller supplies m, sets bit 2 of *status;
+// m_out (or NULL) receives the clamped sizes for the quadrature that follows.
 __global__ void k_ritz(const double *__restrict__ alpha, const double *__restrict__ beta,
                        const int32_t *__restrict__ mm, int nv, int s, double *__restrict__ theta,
-                       double *__restrict__ tau2, int32_t *status) {
+                       double *__restrict__ tau2, int32_t *status, int32_t *__restrict__ m_out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;  // nv = number of problems
   if (p >= nv) return;
   double d[kMaxS], e[kMaxS], w[kMaxS];
-  const int m = mm[p];
+  const int m_in = mm[p];
+  const int m = min(max(m_in, 0), min(s, kMaxS));
+  if (m != m_in) atomicOr(status, 2);
+  if (m_out) m_out[p] = m;
   for (int i = 0; i < m; ++i) d[i] = alpha[p * s + i];
   for (int i = 0; i + 1 < m; ++i) e[i] = beta[p * s + i];
   if (tridiag_gauss(d, e, w, m) != 0) atomicOr(status, 1);
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(kTT * kPG)
       S2 += sh_m2[h][tt] + delta * delta * ((double)N * nb / nn);
       N = nn;
     }
-    out[(int64_t)gr * nt + ti] = M;
+    if (out) out[(int64_t)gr * nt + ti] = M;
     if (se) se[(int64_t)gr * nt + ti] = nv > 1 ? sqrt(S2 / (nv - 1) / nv) : nan("");
   }
 }
@@ -512,6 +519,35 @@ __global__ void k_vnge(const double *__restrict__ theta, const double *__restric
   if (threadIdx.x == 0) mean_se(g, nv, out + gr, se ? se + gr : nullptr);
 }
 
+// Orthogonality monitor of problem q = (graph, probe): the largest
+// |u_j^T u_k| / (||u_j|| ||u_k||), j < k < min(m, kcap), over the measured
+// Gram entries of the stored basis, and the smallest beta_k, k < m - 1.
+// Both are non-negative, so their bit patterns order like the values and
+// atomicMax / atomicMin on the 64-bit words combine the problems.
+__global__ void k_monitor(const double *__restrict__ gram_all, const double *__restrict__ beta,
+                          const int32_t *__restrict__ mm, int nv, int s, int ld, int total, int kcap,
+                          unsigned long long *ortho_bits, unsigned long long *beta_bits) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int gr = q / nv, p = q - gr * nv;
+  const double *G = gram_all + (int64_t)gr * s * s * ld;
+  const int m = min(mm[q], s);
+  const int kend = min(m, kcap);
+  double mx = 0.0;
+  for (int k = 1; k < kend; ++k) {
+    const double gkk = G[((int64_t)k * s + k) * ld + p];
+    for (int j = 0; j < k; ++j) {
+      const double gjj = G[((int64_t)j * s + j) * ld + p];
+      const double r = fabs(G[((int64_t)j * s + k) * ld + p]) * rsqrt(gjj * gkk);
+      if (r == r) mx = fmax(mx, r);
+    }
+  }
+  double mb = INFINITY;
+  for (int k = 0; k + 1 < m; ++k) mb = fmin(mb, beta[(int64_t)q * s + k]);
+  atomicMax(ortho_bits, (unsigned long long)__double_as_longlong(mx));
+  if (m >= 2) atomicMin(beta_bits, (unsigned long long)__double_as_longlong(mb));
+}
+
 __global__ void k_distance(const double *a, const double *b, int len, int absdiff, double *out) {
   __shared__ double ps[256], pc[256];
   NeumaierD acc;
@@ -559,10 +595,10 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   } else if (pencil) {
     const int64_t need = (int64_t)total * ((int64_t)K->s * K->s + K->s * (K->s + 1) / 2 + 2 * K->s);
     if (need > K->rscratch_cap) {
-      if (K->rscratch) cudaFree(K->rscratch);
+      dmfree(K->rscratch);
       K->rscratch = nullptr;
       K->rscratch_cap = 0;
-      SLAQ_CHECK_CUDA(cudaMalloc(&K->rscratch, need * sizeof(double)));
+      SLAQ_TRY(dmalloc(reinterpret_cast<void **>(&K->rscratch), need * sizeof(double)));
       K->rscratch_cap = need;
     }
     k_ritz_pencil<<<(unsigned)ceil_div(total, tpb), tpb, 0, st>>>(
@@ -570,7 +606,7 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
         K->theta, K->tau2, K->status);
   } else {
     k_ritz<<<(unsigned)ceil_div(total, tpb), tpb, 0, st>>>(K->alpha, K->beta, K->m, total, K->s,
-                                                            K->theta, K->tau2, K->status);
+                                                            K->theta, K->tau2, K->status, nullptr);
   }
   SLAQ_CHECK_LAUNCH("ritz");
   return SLAQ_OK;
@@ -611,26 +647,49 @@ int trace_heat_cv(slaq_krylov K, const double *t, int nt, int degree, double *ou
   return SLAQ_OK;
 }
 
+// re/im (means) may be NULL when only the per-probe values pp_re/pp_im
+// ([G][nv][nt]) are wanted (slaq_trace_wave_per_probe).
+// The BF16-basis form serves t * bound <= kBf16WaveTB only: cos(t theta) and
+// sin(t theta) turn the first-order movement of its unconverged interior
+// Ritz values (the basis is rounded at 2^-9) into errors that grow with t;
+// up to t * bound = 20 (t = 10 on a normalized Laplacian) they stayed below
+// 1e-5 of max |Re| on every graph measured, and reached 1e-4 from
+// t * bound = 39 (a batch of SBM graphs) to 90 (R-MAT, BA graphs).
+constexpr double kBf16WaveTB = 20.0;
+
 int trace_wave(slaq_krylov K, const double *t, int nt, double *re, double *im, double *se_re,
-               double *se_im, cudaStream_t st) {
-  if (nt < 1 || !t || !re || !im) return set_error(SLAQ_EINVAL, "wave trace needs t, nt, re, im");
+               double *se_im, cudaStream_t st, double *pp_re, double *pp_im) {
+  if (nt < 1 || !t || ((!re || !im) && (!pp_re || !pp_im)))
+    return set_error(SLAQ_EINVAL, "wave trace needs t, nt, and re, im or per-probe outputs");
+  if (K->precision == SLAQ_FP32_BF16BASIS) {
+    std::vector<double> th(nt);
+    SLAQ_CHECK_CUDA(cudaMemcpyAsync(th.data(), t, nt * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < nt; ++i)
+      if (!(std::fabs(th[i]) * K->bound <= kBf16WaveTB))
+        return set_error(SLAQ_EUNSUPPORTED,
+                         "the BF16-basis form's wave trace is served for |t| * bound <= %g only "
+                         "(t = %g, bound %g): beyond it the basis rounding moves cos(t theta) by "
+                         "more than 1e-4 of the trace; use SLAQ_FP32",
+                         kBf16WaveTB, th[i], K->bound);
+  }
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
   const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
   const bool f32 = K->precision != SLAQ_FP64;
   if (f32)
     k_trace_t<1, true><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
-                                                    t, nt, re, se_re, nullptr);
+                                                    t, nt, re, se_re, pp_re);
   else
     k_trace_t<1, false><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
-                                                     t, nt, re, se_re, nullptr);
+                                                     t, nt, re, se_re, pp_re);
   ++tl_launches;
   if (f32)
     k_trace_t<2, true><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
-                                                    t, nt, im, se_im, nullptr);
+                                                    t, nt, im, se_im, pp_im);
   else
     k_trace_t<2, false><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
-                                                     t, nt, im, se_im, nullptr);
+                                                     t, nt, im, se_im, pp_im);
   SLAQ_CHECK_LAUNCH("trace_wave");
   return SLAQ_OK;
 }
@@ -642,6 +701,29 @@ int trace_vnge(slaq_krylov K, double *out, double *se, double *per_probe, cudaSt
   k_vnge<<<K->n_graphs, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, K->gtrace, out,
                                        se, per_probe);
   SLAQ_CHECK_LAUNCH("trace_vnge");
+  return SLAQ_OK;
+}
+
+int krylov_monitor(slaq_krylov K, double *ortho, double *min_beta, cudaStream_t st) {
+  // the Gram column of the newest vector is formed on every step except the
+  // last step of the FP64 form and of partial reorthogonalization (only its
+  // diagonal entry): there the last vector is left out
+  const int kcap = (K->precision == SLAQ_FP64 || K->reorth == 0) ? K->s - 1 : K->s;
+  const int total = K->n_graphs * K->nv;
+  unsigned long long *bits = reinterpret_cast<unsigned long long *>(K->status) + 1;
+  const unsigned long long init[2] = {0ull, (unsigned long long)0x7ff0000000000000ull};  // 0, +inf
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(bits, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  ++tl_launches;
+  k_monitor<<<(unsigned)ceil_div(total, 128), 128, 0, st>>>(K->gram, K->beta, K->m, K->nv, K->s,
+                                                            K->ld, total, kcap, bits, bits + 1);
+  SLAQ_CHECK_LAUNCH("krylov_monitor");
+  unsigned long long h[2];
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(h, bits, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  double v[2];
+  std::memcpy(v, h, sizeof(v));
+  if (ortho) *ortho = v[0];
+  if (min_beta) *min_beta = v[1];
   return SLAQ_OK;
 }
 
@@ -669,11 +751,13 @@ int distance(const double *a, const double *b, int nt, int kind, double *out, cu
 constexpr int kStaticMaxNvS = kMaxNv * kMaxS;  // 512 probes x 64 steps
 static __device__ __align__(256) double g_static_gauss[2 * kStaticMaxNvS];
 static __device__ __align__(256) int32_t g_static_status[8];
+static __device__ __align__(256) int32_t g_static_m[kMaxNv];  // rule sizes clamped to [0, s]
 
 namespace {
 struct StaticScratch {
   double *gauss = nullptr;
   int32_t *status = nullptr;
+  int32_t *m = nullptr;
 };
 std::mutex g_static_mutex;
 StaticScratch g_static_ptr[64];
@@ -697,13 +781,16 @@ int trace_heat_static(const double *alpha, const double *beta, const int32_t *m,
     std::lock_guard<std::mutex> lk(g_static_mutex);
     StaticScratch &slot = g_static_ptr[dev];
     if (!slot.gauss) {
-      void *a = nullptr, *b = nullptr;
+      void *a = nullptr, *b = nullptr, *c = nullptr;
       cudaError_t e1 = cudaGetSymbolAddress(&a, g_static_gauss);
       if (e1 != cudaSuccess) return cuda_status(e1, "cudaGetSymbolAddress(scratch)");
       cudaError_t e2 = cudaGetSymbolAddress(&b, g_static_status);
       if (e2 != cudaSuccess) return cuda_status(e2, "cudaGetSymbolAddress(status)");
+      cudaError_t e3 = cudaGetSymbolAddress(&c, g_static_m);
+      if (e3 != cudaSuccess) return cuda_status(e3, "cudaGetSymbolAddress(rule sizes)");
       slot.gauss = static_cast<double *>(a);
       slot.status = static_cast<int32_t *>(b);
+      slot.m = static_cast<int32_t *>(c);
     }
     sp = slot;
   }
@@ -712,10 +799,13 @@ int trace_heat_static(const double *alpha, const double *beta, const int32_t *m,
   double *tau2 = sp.gauss + (size_t)nv * s;
   SLAQ_CHECK_CUDA(cudaMemsetAsync(sp.status, 0, sizeof(int32_t), st));  // starts at zero
   ++tl_launches;
-  k_ritz<<<(unsigned)ceil_div(nv, 32), 32, 0, st>>>(alpha, beta, m, nv, s, theta, tau2, sp.status);
+  // the caller's m is clamped to [0, s] by k_ritz, and the quadrature reads
+  // the clamped copy, so no row is read past s entries whatever m holds
+  k_ritz<<<(unsigned)ceil_div(nv, 32), 32, 0, st>>>(alpha, beta, m, nv, s, theta, tau2, sp.status,
+                                                    sp.m);
   ++tl_launches;
   k_trace_t<0, false><<<dim3((unsigned)ceil_div(nt, kTT), 1), kTT * kPG, 0, st>>>(
-      theta, tau2, m, nv, s, nullptr, (double)n, t, nt, out, se, nullptr);
+      theta, tau2, sp.m, nv, s, nullptr, (double)n, t, nt, out, se, nullptr);
   if (status_out)
     SLAQ_CHECK_CUDA(cudaMemcpyAsync(status_out, sp.status, sizeof(int32_t),
                                     cudaMemcpyDeviceToDevice, st));

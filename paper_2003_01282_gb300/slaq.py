@@ -50,6 +50,9 @@ _SIGNATURES = {
     "slaq_graph_destroy": (None, [_VP]),
     "slaq_lanczos": (_I, [_VP, _I, _I, _U64, _I, _I, _I, _VP, _PVP]),
     "slaq_lanczos_batched": (_I, [_VP, _I, _I, _I, _U64, _I, _I, _I, C.c_char_p, _VP, _PVP]),
+    "slaq_lanczos_probes": (_I, [_VP, _I, _I, _I, _U64, _I, _I, _I, _VP, _PVP]),
+    "slaq_trace_wave_per_probe": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    "slaq_pool_probes_host": (_I, [_VP, _I, _I, _VP, _VP]),
     "slaq_probes": (_I, [_VP, _I, _U64, _I, _VP, _VP]),
     "slaq_krylov_export": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_krylov_full_steps": (_I, [_VP, _VP, _VP]),
@@ -60,6 +63,7 @@ _SIGNATURES = {
     "slaq_trace_heat_cv": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP, _VP]),
     "slaq_trace_wave": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _VP]),
     "slaq_trace_vnge": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "slaq_krylov_monitor": (_I, [_VP, _VP, _VP, _VP]),
     "slaq_krylov_destroy": (None, [_VP]),
     "slaq_distance": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
     "slaq_descriptors_host": (_I, [_VP, _VP, _I64, _I64, _I, _I, _I, _I, _U64, _I, _VP, _I,
@@ -67,8 +71,11 @@ _SIGNATURES = {
     "slaq_tridiag_gauss_host": (_I, [_VP, _VP, _I, _VP, _VP]),
     "slaq_trace_heat_tridiag_static": (_I, [_VP, _VP, _VP, _I, _I, _I64, _VP, _I, _VP, _VP, _VP,
                                             _VP]),
+    "slaq_debug_fail_alloc": (_I, [_I64]),
+    "slaq_debug_live_allocs": (_I64, []),
     "slaq_profile_enable": (_I, [_I]),
     "slaq_profile_read": (_I, [_I, _VP, _VP]),
+    "slaq_profile_gather_peak": (_I, [_I, _VP]),
 }
 
 PROF_NAMES = ["build", "probes", "spmm", "dots", "update", "reduce", "ritz", "trace", "dist"]
@@ -251,6 +258,20 @@ def lanczos(g, nv: int, s: int, seed: int, graph_id: int = 0, precision=FP64, re
     return Krylov(h)
 
 
+def lanczos_probes(g, nv: int, probe0: int, s: int, seed: int, graph_id: int = 0, precision=FP64,
+                   reorth_passes: int = 1, stream=None, reuse=None):
+    """slaq_lanczos_probes: Lanczos over generator probes probe0 .. probe0 + nv - 1."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    h = C.c_void_p(reuse.ptr.value if reuse is not None else None)
+    _check(lib().slaq_lanczos_probes(_handle(g), int(nv), int(probe0), int(s),
+                                     C.c_uint64(int(seed) & (2**64 - 1)), int(graph_id),
+                                     int(precision), int(reorth_passes), _stream(stream), C.byref(h)))
+    if reuse is not None:
+        return reuse
+    return Krylov(h)
+
+
 def lanczos_rerun(k, seed: int, stream=None):
     """slaq_lanczos_rerun: the handle's last run again with a new probe seed,
     replayed from a captured CUDA graph."""
@@ -366,6 +387,18 @@ def trace_wave(k, t, stream=None):
     return (re, sre), (im, sim)
 
 
+def trace_wave_per_probe(k, t, stream=None):
+    """slaq_trace_wave_per_probe: per-probe Re and Im values, [(G,) nv, nt] each."""
+    torch = _torch()
+    nt = int(t.numel())
+    shape = (*_lead(k), krylov_info(k)["nv"], nt)
+    re = torch.empty(*shape, dtype=torch.float64, device="cuda")
+    im = torch.empty_like(re)
+    _check(lib().slaq_trace_wave_per_probe(_handle(k), _dev(t, torch.float64, "t"), nt, _dev(re),
+                                           _dev(im), _stream(stream)))
+    return re, im
+
+
 def trace_vnge(k, per_probe: bool = False, stream=None):
     torch = _torch()
     lead = _lead(k)
@@ -374,6 +407,14 @@ def trace_vnge(k, per_probe: bool = False, stream=None):
     pp = torch.empty(*lead, krylov_info(k)["nv"], dtype=torch.float64, device="cuda") if per_probe else None
     _check(lib().slaq_trace_vnge(_handle(k), _dev(out), _dev(se), _dev(pp), _stream(stream)))
     return (out, se, pp) if per_probe else (out, se)
+
+
+def krylov_monitor(k, stream=None) -> dict:
+    """slaq_krylov_monitor: {"ortho": max |Q^T Q - I| off the diagonal,
+    "min_beta": smallest beta} of the last run."""
+    o, b = C.c_double(), C.c_double()
+    _check(lib().slaq_krylov_monitor(_handle(k), C.byref(o), C.byref(b), _stream(stream)))
+    return {"ortho": o.value, "min_beta": b.value}
 
 
 def krylov_destroy(k):
@@ -417,6 +458,18 @@ def descriptors_host(src, dst, n_nodes: int, t, kind=NORMALIZED, flags=0, nv: in
     return {"heat": heat, "wave_re": wr, "wave_im": wi, "vnge": float(vn[0])}
 
 
+def pool_probes_host(values):
+    """slaq_pool_probes_host: (mean, stderr) over the rows of a [nprobe, len]
+    array of per-probe values (numpy, host; no GPU needed)."""
+    v, pv = _host(values, np.float64)
+    if v.ndim != 2:
+        raise ValueError("values must be [nprobe, len]")
+    mean, se = np.empty(v.shape[1]), np.empty(v.shape[1])
+    _check(lib().slaq_pool_probes_host(pv, v.shape[0], v.shape[1], mean.ctypes.data_as(C.c_void_p),
+                                       se.ctypes.data_as(C.c_void_p)))
+    return mean, se
+
+
 def tridiag_gauss_host(alpha, beta):
     """Gauss nodes and weights of one tridiagonal matrix (host, no GPU)."""
     a, pa = _host(alpha, np.float64)
@@ -433,7 +486,11 @@ def trace_heat_tridiag_static(alpha, beta, m, n: int, t, stream=None):
     no device memory for it (see slaq_trace_heat_tridiag_static).
     Returns (out, stderr, status) as CUDA tensors."""
     torch = _torch()
+    if alpha.dim() != 2 or tuple(beta.shape) != tuple(alpha.shape):
+        raise ValueError("alpha and beta must both be [nv, s]")
     nv, s = int(alpha.shape[0]), int(alpha.shape[1])
+    if m.dim() != 1 or int(m.numel()) != nv:
+        raise ValueError("m must hold nv entries")
     nt = int(t.numel())
     out = torch.empty(nt, dtype=torch.float64, device=t.device)
     se = torch.empty_like(out)
@@ -446,8 +503,25 @@ def trace_heat_tridiag_static(alpha, beta, m, n: int, t, stream=None):
     return out, se, status
 
 
+def debug_fail_alloc(nth: int):
+    """slaq_debug_fail_alloc: the nth library allocation from now fails (0: off)."""
+    _check(lib().slaq_debug_fail_alloc(int(nth)))
+
+
+def debug_live_allocs() -> int:
+    """slaq_debug_live_allocs: allocations the library holds."""
+    return int(lib().slaq_debug_live_allocs())
+
+
 def profile_enable(on: bool = True):
     _check(lib().slaq_profile_enable(1 if on else 0))
+
+
+def profile_gather_peak(row_bytes: int) -> float:
+    """slaq_profile_gather_peak: L2 row-gather rate in TB/s for rows of row_bytes."""
+    v = C.c_double()
+    _check(lib().slaq_profile_gather_peak(int(row_bytes), C.byref(v)))
+    return v.value
 
 
 def profile_read() -> dict:

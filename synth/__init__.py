@@ -26,6 +26,8 @@ and the torch build).
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 __all__ = [
@@ -181,18 +183,24 @@ def rmat(scale: int, n_edges: int, a=0.57, b=0.19, c=0.19, seed: int = 1,
 
 
 def rmat_torch(scale: int, n_edges: int, a=0.57, b=0.19, c=0.19, seed: int = 1,
-               device="cuda", chunk: int = 1 << 26):
+               device="cuda", chunk: int = 1 << 26, n_nodes: int | None = None):
     """``rmat`` drawn with torch on ``device``: candidate pairs in rounds, the
     first ``n_edges`` distinct undirected non-loop pairs in sampling order,
-    random orientation.  Returns int32 tensors (src, dst) on ``device`` and n."""
+    random orientation.  Returns int32 tensors (src, dst) on ``device`` and n.
+    ``n_nodes`` (< 2^scale) restricts the graph to nodes [0, n_nodes): pairs
+    with an endpoint outside are rejected, the usual way to draw R-MAT graphs
+    whose node count is not a power of two."""
     import torch
 
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
     n = 1 << scale
+    nn = n if n_nodes is None else int(n_nodes)
+    if not 1 < nn <= n:
+        raise ValueError("n_nodes must lie in (1, 2^scale]")
     ab, abc = a + b, a + b + c
     keys = torch.empty(0, dtype=torch.int64, device=device)
-    want = int(n_edges * 1.3) + 1024
+    want = int(n_edges * 1.3 * n / nn) + 1024
     while True:
         parts = [keys]
         while want > 0:
@@ -203,7 +211,7 @@ def rmat_torch(scale: int, n_edges: int, a=0.57, b=0.19, c=0.19, seed: int = 1,
                 r = torch.rand(cnt, generator=gen, device=device)
                 u = (u << 1) | (r >= ab).long()
                 v = (v << 1) | (((r >= a) & (r < ab)) | (r >= abc)).long()
-            keep = u != v
+            keep = (u != v) & (u < nn) & (v < nn)
             u, v = u[keep], v[keep]
             parts.append(torch.minimum(u, v) * n + torch.maximum(u, v))
             want -= cnt
@@ -221,7 +229,44 @@ def rmat_torch(scale: int, n_edges: int, a=0.57, b=0.19, c=0.19, seed: int = 1,
     flip = torch.rand(key.numel(), generator=gen, device=device) < 0.5
     src = torch.where(flip, hi, lo).to(torch.int32)
     dst = torch.where(flip, lo, hi).to(torch.int32)
-    return src, dst, n
+    return src, dst, nn
+
+
+def rewire_torch(src, dst, n: int, frac: float = 1e-3, seed: int = 0):
+    """``rewire`` on the device (torch tensors in, int32 tensors out): the
+    ceil(frac*|E|) edges to delete are a uniform sample without replacement
+    of the sorted unique edges, and the new edges are the first distinct
+    uniformly drawn non-loop non-edges in sampling order.  Node set and ids
+    are kept."""
+    import torch
+
+    dev = src.device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    s, d = src.long(), dst.long()
+    keys = torch.unique(torch.minimum(s, d) * n + torch.maximum(s, d))  # sorted
+    m = keys.numel()
+    k = int(math.ceil(frac * m))
+    drop = torch.randperm(m, generator=gen, device=dev)[:k]
+    keep = torch.ones(m, dtype=torch.bool, device=dev)
+    keep[drop] = False
+    new = torch.empty(0, dtype=torch.int64, device=dev)
+    while new.numel() < k:
+        cnt = 4 * (k - new.numel()) + 1024
+        a = torch.randint(0, n, (cnt,), generator=gen, device=dev)
+        b = torch.randint(0, n, (cnt,), generator=gen, device=dev)
+        ok = a != b
+        cand = (torch.minimum(a, b) * n + torch.maximum(a, b))[ok]
+        pos = torch.searchsorted(keys, cand).clamp(max=m - 1)
+        cand = cand[keys[pos] != cand]
+        cand = torch.cat([new, cand])
+        # first occurrence of each key, in sampling order
+        srt, perm = torch.sort(cand, stable=True)
+        first = torch.ones_like(srt, dtype=torch.bool)
+        first[1:] = srt[1:] != srt[:-1]
+        new = cand[torch.sort(perm[first]).values]
+    allk = torch.cat([keys[keep], new[:k]])
+    return (allk // n).to(torch.int32), (allk % n).to(torch.int32), n
 
 
 def erdos_renyi(n: int, p: float, seed: int = 0):

@@ -66,3 +66,25 @@ def test_rmat_torch_unique_and_skewed():
     assert deg.max() > 20 * np.median(deg[deg > 0])     # R-MAT's heavy tail
     s2, d2, _ = synth.rmat_torch(12, 16 << 12, seed=3, device="cpu")
     assert np.array_equal(s, s2.numpy()) and np.array_equal(d, d2.numpy())
+
+
+def test_rmat_torch_node_restriction_and_rewire_torch():
+    """The graph-pair workload's generators, on torch's CPU device here
+    (the bench draws them on the GPU): R-MAT on a node count that is not a
+    power of two, then a 0.1% rewire that keeps the node set."""
+    torch = pytest.importorskip("torch")
+    n_i = round(2 ** (10 + 4 * 5 / 63))       # 1268 nodes, scale 11
+    s, d, n = synth.rmat_torch(11, 16 * n_i, seed=100, device="cpu", n_nodes=n_i)
+    assert n == n_i and s.numel() == 16 * n_i
+    s, d = s.numpy(), d.numpy()
+    assert s.max() < n_i and d.max() < n_i and not np.any(s == d)
+    pairs = _pairs(s, d)
+    assert len(pairs) == s.size
+    s2, d2, _ = synth.rmat_torch(11, 16 * n_i, seed=100, device="cpu", n_nodes=n_i)
+    assert np.array_equal(s, s2.numpy())
+    r_s, r_d, rn = synth.rewire_torch(torch.as_tensor(s), torch.as_tensor(d), n_i, frac=1e-3, seed=3)
+    new = _pairs(r_s.numpy(), r_d.numpy())
+    k = int(np.ceil(1e-3 * len(pairs)))
+    assert rn == n_i and len(new) == len(pairs)
+    assert len(pairs - new) == k and len(new - pairs) == k
+    assert not np.any(r_s.numpy() == r_d.numpy()) and r_s.max() < n_i and r_d.max() < n_i
