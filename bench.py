@@ -84,7 +84,7 @@ PAIR_WORKLOAD = ("64 R-MAT graphs, n_i = round(2^(18+4i/63)) nodes (pairs with a
                  "ceil(0.1%|E|) edges deleted and replaced by uniform non-edges (node ids kept, no "
                  "dropping); normalized Laplacians; nv=64, s=20, common random probes per pair; "
                  "heat-trace and wave-trace L2 distances and the VNGE difference")
-BF16_WAVE_TB = 20.0   # the BF16-basis form serves its wave trace for t * bound <= 20
+BF16_TB = 20.0   # the BF16-basis form serves its heat and wave traces for t * bound <= 20
 
 
 def make_graph():
@@ -508,7 +508,7 @@ def run_rmat24(dev, hbm, peak_src, gather_peak):
     n_prime, nnz = info["n"], info["nnz"]
     t_np = synth.t_grid(NT)
     t = torch.as_tensor(t_np, device=dev)
-    lo_np = t_np * 2.0 <= BF16_WAVE_TB
+    lo_np = t_np * 2.0 <= BF16_TB
     t_lo = t[torch.as_tensor(lo_np, device=dev)].contiguous()
     state = {}
 
@@ -516,7 +516,7 @@ def run_rmat24(dev, hbm, peak_src, gather_peak):
         state["Kb"] = slaq.lanczos(g, R24_NV, R24_S, PROBE_SEED, precision=slaq.FP32_BF16BASIS,
                                    reuse=state.get("Kb"))
         K = state["Kb"]
-        h = slaq.trace_heat(K, t)[0]
+        h = slaq.trace_heat(K, t_lo)[0]
         (wr, _), (wi, _) = slaq.trace_wave(K, t_lo)
         v = slaq.trace_vnge(K)[0]
         return h, wr, wi, v
@@ -555,7 +555,7 @@ def run_rmat24(dev, hbm, peak_src, gather_peak):
     h64, wr64, wi64, v64 = mean64[:NT], mean64[NT:2 * NT], mean64[2 * NT:3 * NT], mean64[-1]
     h, wr, wi, v = h.cpu().numpy(), wr.cpu().numpy(), wi.cpu().numpy(), v.item()
     wscale = np.max(np.abs(wr64))
-    err = {"heat_max": float(np.max(np.abs(h - h64) / np.abs(h64))),
+    err = {"heat_max_t_le_10": float(np.max(np.abs(h - h64[lo_np]) / np.abs(h64[lo_np]))),
            "wave_re_max_t_le_10": float(np.max(np.abs(wr - wr64[lo_np])) / wscale),
            "wave_im_max_t_le_10": float(np.max(np.abs(wi - wi64[lo_np])) / wscale),
            "vnge": float(abs(v - v64) / abs(v64))}
@@ -569,7 +569,7 @@ def run_rmat24(dev, hbm, peak_src, gather_peak):
             "spmm_roofline": roof, "orthogonality": mon,
             "fp64_two_ranges": {"ms": ms64, "probe_edges_per_s": pe / (ms64 * 1e-3)},
             "speedup_over_fp64": ms64 / ms_bf, "rel_err_vs_fp64": err,
-            "wave_t_max": float(t_np[lo_np][-1])}
+            "t_max": float(t_np[lo_np][-1])}
 
 
 # ------------------------------------------------------------ config 5
@@ -581,7 +581,7 @@ def run_pairs(dev, n_pairs=PAIRS):
     from paper_2003_01282_gb300 import slaq
     t_np = synth.t_grid(NT)
     t = torch.as_tensor(t_np, device=dev)
-    lo_np = t_np * 2.0 <= BF16_WAVE_TB
+    lo_np = t_np * 2.0 <= BF16_TB
     t_lo = t[torch.as_tensor(lo_np, device=dev)].contiguous()
     nlo = int(lo_np.sum())
     idx = list(range(PAIRS)) if n_pairs >= PAIRS else \
@@ -611,15 +611,17 @@ def run_pairs(dev, n_pairs=PAIRS):
             for g in (ga, gb):
                 K[name] = slaq.lanczos(g, PAIR_NV, PAIR_S, PAIR_SEED, graph_id=i, precision=P,
                                        reuse=K[name])
-                h = slaq.trace_heat(K[name], t)[0]
+                h = slaq.trace_heat(K[name], tw)[0]
                 (wr, _), (wi, _) = slaq.trace_wave(K[name], tw)
                 v = slaq.trace_vnge(K[name])[0]
-                desc.append((h, torch.cat([wr, wi]), v, torch.cat([wr[:nlo], wi[:nlo]])))
-            (ha, wa, va, wla), (hb, wb, vb, wlb) = desc
+                desc.append((h, torch.cat([wr, wi]), v, torch.cat([wr[:nlo], wi[:nlo]]),
+                             h[:nlo].contiguous()))
+            (ha, wa, va, wla, hla), (hb, wb, vb, wlb, hlb) = desc
             d = torch.cat([slaq.distance(ha, hb, slaq.DIST_HEAT),
                            slaq.distance(wa, wb, slaq.DIST_WAVE),
                            slaq.distance(va, vb, slaq.DIST_VNGE),
-                           slaq.distance(wla, wlb, slaq.DIST_WAVE)])
+                           slaq.distance(wla, wlb, slaq.DIST_WAVE),
+                           slaq.distance(hla, hlb, slaq.DIST_HEAT)])
             e1.record()
             torch.cuda.synchronize(dev)
             ms[name] += e0.elapsed_time(e1)
@@ -636,9 +638,11 @@ def run_pairs(dev, n_pairs=PAIRS):
     errs = {}
     for name in ("fp32", "bf16"):
         d = np.array(dist[name])
-        e = {"heat_distance": rel(d[:, 0], d64[:, 0]), "vnge_difference": rel(d[:, 2], d64[:, 2]),
+        e = {"vnge_difference": rel(d[:, 2], d64[:, 2]),
+             "heat_distance_t_le_10": rel(d[:, 4], d64[:, 4]),
              "wave_distance_t_le_10": rel(d[:, 3], d64[:, 3])}
-        if name == "fp32":
+        if name == "fp32":  # the whole grid (the BF16 basis serves t <= 10)
+            e["heat_distance"] = rel(d[:, 0], d64[:, 0])
             e["wave_distance"] = rel(d[:, 1], d64[:, 1])
         errs[name] = e
     return {"workload": PAIR_WORKLOAD, "pairs": len(idx),
@@ -646,7 +650,68 @@ def run_pairs(dev, n_pairs=PAIRS):
             "nnz_total": int(nnz_total), "generate_and_build_s": gen_s,
             "pairs_per_s": {k: len(idx) / (v * 1e-3) for k, v in ms.items()},
             "ms_total": ms, "distance_rel_err_vs_fp64": errs,
-            "wave_t_max_bf16": float(t_np[lo_np][-1])}
+            "t_max_bf16": float(t_np[lo_np][-1])}
+
+
+# ------------------------------------------------------------ Fig. 4 sweep
+ER_SIZES = (100, 300, 1000, 3000, 10000)          # average degree 10
+ER_DENSITIES = (0.005, 0.01, 0.02, 0.05, 0.1, 0.2)  # n = 1000
+ER_NV, ER_S = 100, 10                              # the paper's defaults
+
+
+def run_er_sweep(dev):
+    """Fig. 4 / Sec. 4.1 on Erdos-Renyi graphs: relative l2 error of the heat
+    descriptor (256 t) against the exact one for SLQ on the GPU (FP64, nv =
+    100, s = 10) and for the Taylor expansion of Eq. hks-taylor, and of the
+    VNGE (L = D - A) for SLQ and FINGER-Hbar / FINGER-Hhat.  The exact
+    spectra come from a dense FP64 eigensolve of each Laplacian (ground truth
+    only, outside the library)."""
+    import torch
+    from paper_2003_01282_gb300 import slaq
+    t_np = synth.t_grid(NT)
+    t = torch.as_tensor(t_np, device=dev)
+    cases = [("size", n, 20.0 / (n - 1)) for n in ER_SIZES] + [("density", 1000, p) for p in ER_DENSITIES]
+    rows = []
+    for i, (axis, n, p) in enumerate(cases):
+        s_, d_, nn = synth.erdos_renyi(n, p, seed=1000 + i)
+        src, dst = torch.as_tensor(s_, device=dev), torch.as_tensor(d_, device=dev)
+        row = {"axis": axis, "n": n, "p": p, "edges": int(s_.size)}
+        for kind in (slaq.NORMALIZED, slaq.COMBINATORIAL):
+            g = slaq.build_laplacian(src, dst, nn, kind=kind, flags=slaq.DROP_ISOLATED)
+            K = slaq.lanczos(g, ER_NV, ER_S, 1 + i, precision=slaq.FP64)
+            cmp = slaq.comparators(K, t)
+            # the exact spectrum of the same Laplacian, rebuilt densely from its CSR
+            ex = slaq.graph_export(g)
+            m = g.info["n"]
+            A = torch.zeros(m, m, dtype=torch.float64, device=dev)
+            rows_idx = torch.repeat_interleave(torch.arange(m, device=dev), ex["rowptr"].diff())
+            A[rows_idx, ex["colidx"].long()] = ex["vals"]
+            A[torch.arange(m, device=dev), torch.arange(m, device=dev)] = ex["diag"]
+            lam = torch.linalg.eigvalsh(A)
+            del A
+            if kind == slaq.NORMALIZED:
+                h = slaq.trace_heat(K, t)[0]
+                hx = torch.exp(-t[:, None] * lam[None, :]).sum(1)
+                row["heat_rel_l2"] = {
+                    "slq": float(torch.linalg.norm(h - hx) / torch.linalg.norm(hx)),
+                    "taylor": float(torch.linalg.norm(cmp["taylor_heat"] - hx) / torch.linalg.norm(hx))}
+            else:
+                c = g.info["trace"]
+                mu = lam[lam > 0] / c
+                vx = float(-(mu * torch.log(mu)).sum())
+                v = slaq.trace_vnge(K)[0].item()
+                row["vnge_rel_err"] = {"slq": abs(v - vx) / vx,
+                                       "finger_bar": abs(cmp["finger_bar"].item() - vx) / vx,
+                                       "finger_hat": abs(cmp["finger_hat"].item() - vx) / vx}
+            K.close()
+            g.close()
+        rows.append(row)
+    return {"workload": "Erdos-Renyi graphs: n in {100..10000} at average degree 10, and n = 1000 "
+                        "with edge probability p in {0.005..0.2} (seed 1000+i); SLQ FP64 nv=100, s=10",
+            "cases": rows,
+            "max_slq_heat_rel_l2": max(r["heat_rel_l2"]["slq"] for r in rows),
+            "min_taylor_over_slq": min(r["heat_rel_l2"]["taylor"] / r["heat_rel_l2"]["slq"] for r in rows),
+            "max_slq_vnge_rel_err": max(r["vnge_rel_err"]["slq"] for r in rows)}
 
 
 # ------------------------------------------------------------ other legs
@@ -694,19 +759,21 @@ def rel_errors(a, b, t_np):
     wr64, wi64 = b["wave_re"][:nw], b["wave_im"][:nw]
     sc_r, sc_i = np.max(np.abs(b["wave_re"])), np.max(np.abs(b["wave_im"]))
     return {
-        "heat_max": float(np.max(np.abs(a["heat"] - b["heat"]) / np.abs(b["heat"]))),
+        "heat_max": float(np.max(np.abs(a["heat"] - b["heat"][:nw]) / np.abs(b["heat"][:nw]))),
         "wave_re_max": float(np.max(np.abs(a["wave_re"] - wr64)) / sc_r),
         "wave_im_max": float(np.max(np.abs(a["wave_im"] - wi64)) / sc_i),
         "wave_re_max_t_lt_10": float(np.max(np.abs(a["wave_re"] - wr64)[lo]) / sc_r),
-        "wave_t_max": float(t_np[nw - 1]),
+        "t_max": float(t_np[nw - 1]),
         "vnge": float(abs(a["vnge"] - b["vnge"]) / abs(b["vnge"])),
     }
 
 
 def kernel_capture(args):
-    """Profiling driver: build the workload's graph (R-MAT 2^20, or the SBM
-    batch with --capture-batched) and run Lanczos `--kernel-capture` times
-    (for ncu captures of single kernels)."""
+    """Profiling driver: build the workload's graph (R-MAT 2^20; R-MAT
+    2^--capture-scale drawn on the GPU; or the SBM batch with
+    --capture-batched) and run Lanczos `--kernel-capture` times, with
+    --capture-steps steps and --capture-nv probes when given (small cases
+    for ncu captures of single kernels: every step's SpMM does the same work)."""
     import torch
     from paper_2003_01282_gb300 import slaq
     from paper_2003_01282_gb300.build import build
@@ -715,16 +782,24 @@ def kernel_capture(args):
         g = slaq.build_laplacian_batch(synth.sbm_batch(SBM_GRAPHS, seed=SBM_SEED),
                                        flags=slaq.DROP_ISOLATED)
         nv, steps = SBM_NV, SBM_S
+    elif args.capture_scale and args.capture_scale != SCALE:
+        src, dst, n = synth.rmat_torch(args.capture_scale, 16 << args.capture_scale, seed=2)
+        g = slaq.build_laplacian(src, dst, n, flags=slaq.DROP_ISOLATED)
+        del src, dst
+        nv, steps = 64, S
     else:
         s_, d_, n = make_graph()
         g = slaq.build_laplacian(torch.as_tensor(s_, device="cuda"), torch.as_tensor(d_, device="cuda"),
                                  n, flags=slaq.DROP_ISOLATED)
         nv, steps = NV, S
+    steps = args.capture_steps or steps
+    nv = args.capture_nv or nv
     K = None
     for _ in range(args.kernel_capture):
         K = slaq.lanczos(g, nv, steps, PROBE_SEED, precision=slaq.PRECISIONS[args.precision], reuse=K)
     torch.cuda.synchronize()
-    print(json.dumps({"kernel_capture": args.kernel_capture, "n_prime": g.info["n"], "nnz": g.info["nnz"]}))
+    print(json.dumps({"kernel_capture": args.kernel_capture, "n_prime": g.info["n"], "nnz": g.info["nnz"],
+                      "nv": nv, "s": steps, "precision": args.precision}))
 
 
 # ---- multi-rank host logic
@@ -769,7 +844,7 @@ def run_ours(args):
     dst = dst_h.to(dev)
     t_np = synth.t_grid(NT)
     t = torch.as_tensor(t_np, device=dev)
-    lo_np = t_np * 2.0 <= BF16_WAVE_TB
+    lo_np = t_np * 2.0 <= BF16_TB
     t_lo = t[torch.as_tensor(lo_np, device=dev)].contiguous()
     prec = args.precision
     P = slaq.PRECISIONS[prec]
@@ -782,25 +857,26 @@ def run_ours(args):
         state[key] = slaq.lanczos_probes(g, NV, probe0, S, PROBE_SEED, precision=precision,
                                          reorth_passes=reorth, reuse=state.get(key))
         K = state[key]
+        # the BF16-basis form serves its traces for t <= 10 only
         tw = t_lo if precision == slaq.FP32_BF16BASIS else t
         nw = tw.numel()
         if dist:
             # per-probe values of every rank's range, pooled over all probes
-            hp = slaq.trace_heat(K, t, per_probe=True)[2]
+            hp = slaq.trace_heat(K, tw, per_probe=True)[2]
             rp, ip = slaq.trace_wave_per_probe(K, tw)
             vp = slaq.trace_vnge(K, per_probe=True)[2]
             full = shard.gather_probe_values(torch.cat([hp, rp, ip, vp[:, None]], dim=1),
                                              world * NV, tdist)
             mean, _ = shard.pool(full)
             desc = torch.as_tensor(mean, device=dev)
-            heat, wr, wi, vn = desc[:NT], desc[NT:NT + nw], desc[NT + nw:NT + 2 * nw], desc[-1:]
+            heat, wr, wi, vn = desc[:nw], desc[nw:2 * nw], desc[2 * nw:3 * nw], desc[-1:]
         else:
-            heat, _ = slaq.trace_heat(K, t)
+            heat, _ = slaq.trace_heat(K, tw)
             (wr, _), (wi, _) = slaq.trace_wave(K, tw)
             vn, _ = slaq.trace_vnge(K)
         if state["ref"] is None:
             state["ref"] = heat.clone()
-        d = slaq.distance(heat, state["ref"], slaq.DIST_HEAT)
+        d = slaq.distance(heat, state["ref"][:nw].contiguous(), slaq.DIST_HEAT)
         info = g.info
         g.close()
         return {"heat": heat, "wave_re": wr, "wave_im": wi, "vnge": vn, "dist": d}, info
@@ -1006,6 +1082,9 @@ def run_ours(args):
     if not args.quick and args.pairs > 0 and not dist:
         result["graph_pairs64"] = run_pairs(dev, args.pairs)
         torch.cuda.empty_cache()
+    if not args.quick and not args.no_er and not dist:
+        result["er_sweep"] = run_er_sweep(dev)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(src_np, dst_np, n_nodes)
     if rank == 0:
@@ -1025,12 +1104,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the SBM-batch leg")
     ap.add_argument("--no-rmat24", action="store_true", help="skip the R-MAT 2^24 leg")
+    ap.add_argument("--no-er", action="store_true", help="skip the Erdos-Renyi accuracy sweep")
     ap.add_argument("--pairs", type=int, default=PAIRS,
                     help="graph pairs of the distance leg (an evenly spread subset below 64; 0 skips)")
     ap.add_argument("--kernel-capture", type=int, default=0,
                     help="profiling driver: run Lanczos this many times on the R-MAT graph and exit")
     ap.add_argument("--capture-batched", action="store_true",
                     help="with --kernel-capture: use the SBM batch instead of the R-MAT graph")
+    ap.add_argument("--capture-scale", type=int, default=0,
+                    help="with --kernel-capture: R-MAT scale drawn on the GPU (nv = 64)")
+    ap.add_argument("--capture-steps", type=int, default=0, help="with --kernel-capture: Lanczos steps")
+    ap.add_argument("--capture-nv", type=int, default=0, help="with --kernel-capture: probes")
     args = ap.parse_args()
     if args.kernel_capture:
         kernel_capture(args)

@@ -268,7 +268,16 @@ int slaq_krylov_info(slaq_krylov k, int *nv_host, int *s_host, int *precision_ho
 /* Heat trace h_t = tr exp(-t L) (Eq. heat-trace) at nt times t (float64[nt],
  * device) by Eq. slq: out[i] = (n'/nv) sum_p sum_k tau2 exp(-t_i theta);
  * stderr_[i] = sample std over probes / sqrt(nv) (NaN when nv = 1);
- * per_probe float64[nv*nt] (row p = n' sum_k tau2 exp(-t theta)) or NULL. */
+ * per_probe float64[nv*nt] (row p = n' sum_k tau2 exp(-t theta)) or NULL.
+ * The BF16-basis form serves |t| * bound <= 20 only (t <= 10 on a normalized
+ * Laplacian, whose bound is 2): its basis rounding moves the Ritz values
+ * that are not yet converged at first order, which exp(-t theta) turns into
+ * errors growing with t (measured within 2.3e-5 of the FP64 form up to the
+ * limit on every graph tried, above 1e-4 from t = 29 on cycles, paths,
+ * grids, trees and small SBM graphs).  A larger t gives SLAQ_EUNSUPPORTED;
+ * for that form the call copies t to the host and synchronizes `stream` to
+ * check it.  The same holds for slaq_trace_heat_cv, slaq_trace_wave and
+ * slaq_trace_wave_per_probe. */
 int slaq_trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *stderr_,
                     double *per_probe, void *stream);
 
@@ -288,12 +297,9 @@ int slaq_trace_heat_cv(slaq_krylov k, const double *t, int nt, int degree, doubl
                        double *stderr_, double *per_probe, void *stream);
 
 /* Wave trace tr exp(-i t L): re[i] = sum cos(t lambda), im[i] = -sum sin(t lambda),
- * estimated as above; stderr arrays may be NULL.  The BF16-basis form serves
- * |t| * bound <= 20 only (t <= 10 on a normalized Laplacian, whose bound is
- * 2): cos(t theta) turns its basis rounding into errors that grow with t
- * (measured below 1e-5 of max |Re| up to that limit, up to 0.28 at t = 100).
- * A larger t gives SLAQ_EUNSUPPORTED; for that form the call copies t to the
- * host and synchronizes `stream` to check it. */
+ * estimated as above; stderr arrays may be NULL.  The BF16-basis form's
+ * limit on t is that of slaq_trace_heat (measured for the wave: below 1e-5
+ * of max |Re| up to the limit, up to 0.28 at t = 100). */
 int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im,
                     double *stderr_re, double *stderr_im, void *stream);
 
@@ -327,6 +333,22 @@ int slaq_trace_vnge(slaq_krylov k, double *out, double *stderr_, double *per_pro
 int slaq_krylov_monitor(slaq_krylov k, double *ortho_host, double *min_beta_host, void *stream);
 
 void slaq_krylov_destroy(slaq_krylov k);
+
+/* The paper's O(m) comparators (Sec. 2.3), for context beside the SLQ
+ * estimates, per graph of the run (batches: [G] and [G][nt]); any output
+ * may be NULL:
+ *   taylor_heat[i] = n' - t_i tr L + (t_i^2 / 2) tr L^2   (Eq. hks-taylor),
+ *   vnge_q         = 1 - tr(L^2) / tr(L)^2, the quadratic approximation of
+ *                    the VNGE (the two-term expansion x (1 - x) of -x ln x
+ *                    over the eigenvalues of P = L / tr L; the printed forms
+ *                    of Eq. vnge-taylor and of FINGER's Q are garbled),
+ *   finger_bar     = -vnge_q ln(bound / tr L), bound = 2 (normalized) or
+ *                    2 max d (combinatorial) (FINGER-Hbar),
+ *   finger_hat     = -vnge_q ln(lambda_max / tr L), lambda_max = the largest
+ *                    Ritz value of the graph's probes (FINGER-Hhat),
+ * with tr L and tr L^2 = sum_ij L_ij^2 as the builder computed them. */
+int slaq_comparators(slaq_krylov k, const double *t, int nt, double *taylor_heat, double *vnge_q,
+                     double *finger_bar, double *finger_hat, void *stream);
 
 /* --------------------------------------------------------------- distances */
 

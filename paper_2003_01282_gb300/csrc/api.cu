@@ -486,6 +486,14 @@ void slaq_krylov_destroy(slaq_krylov k) {
   krylov_free(k);
 }
 
+int slaq_comparators(slaq_krylov k, const double *t, int nt, double *taylor_heat, double *vnge_q,
+                     double *finger_bar, double *finger_hat, void *stream) {
+  if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
+  SLAQ_TRY(device_check());
+  SLAQ_TRY(krylov_ready(k));
+  return comparators(k, t, nt, taylor_heat, vnge_q, finger_bar, finger_hat, as_stream(stream));
+}
+
 int slaq_krylov_monitor(slaq_krylov k, double *ortho_host, double *min_beta_host, void *stream) {
   if (!k) return set_error(SLAQ_EINVAL, "NULL Krylov handle");
   SLAQ_TRY(device_check());

@@ -176,6 +176,8 @@ struct slaq_tuning {
   int slice_bytes = 0;     // bytes of a basis row per probe slice (0: whole rows)
   int spmm_align = -1;     // 1: SpMM row teams never straddle two warps, 0: packed
                            // (-1: aligned when a row takes more than 16 threads)
+  int spmm_hot = 0;        // > 0: the SpMM's gathers of rows < spmm_hot keep L2 priority
+                           // (evict_last) and the rest stream (evict_first); 0: no hints
 };
 
 struct slaq_krylov_s {
@@ -290,6 +292,8 @@ int trace_vnge(slaq_krylov k, double *out, double *se, double *per_probe, cudaSt
 int distance(const double *a, const double *b, int nt, int kind, double *out, cudaStream_t st);
 int krylov_monitor(slaq_krylov k, double *ortho, double *min_beta, cudaStream_t st);
 int profile_gather_peak(int row_bytes, double *tbps);
+int comparators(slaq_krylov k, const double *t, int nt, double *taylor, double *q, double *bar,
+                double *hat, cudaStream_t st);
 int trace_heat_static(const double *alpha, const double *beta, const int32_t *m, int nv, int s,
                       int64_t n, const double *t, int nt, double *out, double *se,
                       int32_t *status_out, cudaStream_t st);

@@ -143,6 +143,40 @@ __device__ __forceinline__ void stb(__nv_bfloat16 *p, const float (&v)[8], float
   }
   *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
 }
+// 16-byte read-only loads with an L2 eviction-priority policy (createpolicy):
+// the SpMM keeps the most gathered rows of a vector much larger than L2
+// resident (evict_last) and streams the rest (evict_first).
+__device__ __forceinline__ uint64_t l2_policy(bool keep) {
+  uint64_t pol;
+  if (keep) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  else asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint4 ld_pol(const void *p, uint64_t pol) {
+  uint4 r;
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(pol));
+  return r;
+}
+// the 16-byte basis vector at p as raw bits (with a policy when HINT)
+template <bool HINT>
+__device__ __forceinline__ uint4 ldraw(const void *p, uint64_t pol) {
+  if (HINT) return ld_pol(p, pol);
+  return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+__device__ __forceinline__ void unpack(const uint4 &t, double (&v)[2]) {
+  v[0] = __hiloint2double((int)t.y, (int)t.x);
+  v[1] = __hiloint2double((int)t.w, (int)t.z);
+}
+__device__ __forceinline__ void unpack(const uint4 &t, float (&v)[4]) {
+  v[0] = __uint_as_float(t.x);
+  v[1] = __uint_as_float(t.y);
+  v[2] = __uint_as_float(t.z);
+  v[3] = __uint_as_float(t.w);
+}
+__device__ __forceinline__ void unpack(const uint4 &t, float (&v)[8]) { unpack_bf16x8(t, v); }
+
 // work vectors (TW) of VE elements
 template <typename TW, int VE>
 __device__ __forceinline__ void ldw(const TW *p, TW (&v)[VE]) {
@@ -265,18 +299,32 @@ __device__ __forceinline__ void acc_add(T &s, T &c, T w, T x) {
 // COMP: compensated sums, for the split rows of the reduced forms (a row of
 // thousands of entries whose sum nearly cancels, such as a hub's row against
 // the null vector, otherwise loses about sqrt(entries) units of FP32 rounding)
-template <int P, int MODE, bool COMP = false>
+// HINT: gathers of rows < hot carry an L2 evict_last policy, the others
+// evict_first (a gathered vector much larger than L2; the execution order
+// puts the most gathered rows first, and a row's columns ascend, so the hot
+// entries of a row are its first ones).
+// Every gather is loaded as raw 16 bytes and widened only when it is summed,
+// so that four rows in flight per thread cost 16 registers whatever the form.
+template <int P, int MODE, bool COMP = false, bool HINT = false>
 __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
                                             const typename Form<P>::TW *__restrict__ vals,
                                             const typename Form<P>::TW *__restrict__ scale,
                                             const typename Form<P>::TB *__restrict__ Ul, int stride,
                                             int64_t b, int64_t e,
-                                            typename Form<P>::TW (&acc)[Form<P>::VE]) {
+                                            typename Form<P>::TW (&acc)[Form<P>::VE],
+                                            int64_t hot = 0) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   TW cmp[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v) cmp[v] = TW(0);
+  uint64_t keep = 0, drop = 0;
+  if (HINT) {
+    keep = l2_policy(true);
+    drop = l2_policy(false);
+  }
+  auto row_ptr = [&](int c) { return (const void *)(Ul + (int64_t)c * stride); };
+  auto pol = [&](int c) { return c < hot ? keep : drop; };
   int64_t j = b;
   // FP32: single entries up to a 16-byte boundary of col, then 4 indices per
   // load (measured faster for FP32, slower for the BF16 basis)
@@ -285,7 +333,7 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
     const int c = __ldcs(col + j);
     const TW w = MODE == 0 ? __ldg(scale + c) : (MODE == 2 ? __ldcs(vals + j) : TW(1));
     TW x[VE];
-    ldb(Ul + (int64_t)c * stride, x);
+    unpack(ldraw<HINT>(row_ptr(c), HINT ? pol(c) : 0), x);
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc_add<COMP>(acc[v], cmp[v], w, x[v]);
   }
@@ -305,11 +353,14 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       w[q] = MODE == 0 ? __ldg(scale + c[q]) : (MODE == 2 ? __ldcs(vals + j + q) : TW(1));
-    TW x[4][VE];
+    uint4 raw[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) ldb(Ul + (int64_t)c[q] * stride, x[q]);
+    for (int q = 0; q < 4; ++q) raw[q] = ldraw<HINT>(row_ptr(c[q]), HINT ? pol(c[q]) : 0);
     if (COMP) {
       // the group's four products summed plainly, then one compensated add
+      TW x[4][VE];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) unpack(raw[q], x[q]);
 #pragma unroll
       for (int v = 0; v < VE; ++v) {
         TW g = w[0] * x[0][v];
@@ -319,16 +370,19 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 4; ++q) {
+        TW x[VE];
+        unpack(raw[q], x);
 #pragma unroll
-        for (int v = 0; v < VE; ++v) acc_add<false>(acc[v], cmp[v], w[q], x[q][v]);
+        for (int v = 0; v < VE; ++v) acc_add<false>(acc[v], cmp[v], w[q], x[v]);
+      }
     }
   }
   for (; j < e; ++j) {
     const int c = __ldcs(col + j);
     const TW w = MODE == 0 ? __ldg(scale + c) : (MODE == 2 ? __ldcs(vals + j) : TW(1));
     TW x[VE];
-    ldb(Ul + (int64_t)c * stride, x);
+    unpack(ldraw<HINT>(row_ptr(c), HINT ? pol(c) : 0), x);
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc_add<COMP>(acc[v], cmp[v], w, x[v]);
   }
@@ -363,18 +417,26 @@ __device__ __forceinline__ void finish_row(int64_t row, const typename Form<P>::
 // above 32) so that no row is split between two warps, which saves the extra
 // L1 wavefront of the 128-byte line both warps would touch; the host picks
 // by row width (measured).  Blocks run slice-major, so one slice of u_k is
-// gathered at a time.  The FP32 form runs at 32 registers per thread: full
-// occupancy keeps more gathers in flight, and the kernel is bound by gather
-// latency (no memory unit near its peak, long-scoreboard stalls dominate).
-template <int P, int MODE>
-__global__ void __launch_bounds__(512, P == SLAQ_FP32 ? 4 : 1)  // FP32: 32 registers, full occupancy
+// gathered at a time.  The kernel is bound by gather latency (no memory unit
+// near its peak, long-scoreboard stalls dominate), so occupancy is what keeps
+// gathers in flight: the FP32 form runs at 32 registers per thread (full
+// occupancy), the BF16 basis at 40 (three blocks of 512 per SM; its eight
+// columns per thread need more), FP64 (bound by its FP64 arithmetic) unbounded.
+// HINT: L2 eviction priorities for the gathers (rows < hot kept); see
+// gather_rows.
+template <int P>
+constexpr int spmm_min_blocks() {
+  return P == SLAQ_FP32 ? 4 : (P == SLAQ_FP32_BF16BASIS ? 3 : 1);
+}
+template <int P, int MODE, bool HINT = false>
+__global__ void __launch_bounds__(512, spmm_min_blocks<P>())
     k_spmm_light(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                  const typename Form<P>::TW *__restrict__ vals,
                  const typename Form<P>::TW *__restrict__ diag,
                  const typename Form<P>::TW *__restrict__ scale,
                  const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
                  const typename Form<P>::TB *__restrict__ Yg, Slc S, int Vt, int Tw, int R,
-                 int64_t bps, int64_t heavy_degree) {
+                 int64_t bps, int64_t heavy_degree, int64_t hot) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   const int sl = (int)(blockIdx.x / bps);
@@ -393,7 +455,8 @@ __global__ void __launch_bounds__(512, P == SLAQ_FP32 ? 4 : 1)  // FP32: 32 regi
   TW acc[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v) acc[v] = TW(0);
-  gather_rows<P, MODE>(col, vals, scale, MODE == 3 ? Yg + off : Ul, stride, b, e, acc);
+  gather_rows<P, MODE, false, HINT>(col, vals, scale, MODE == 3 ? Yg + off : Ul, stride, b, e, acc,
+                                     hot);
   finish_row<P, MODE>(row, diag, scale, Ul, stride, acc, Z + off + row * stride);
 }
 
@@ -1470,6 +1533,7 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
   const int ns = geo.S.nslices();
   const int64_t bps = ceil_div(n, geo.Rt);
   const unsigned blocks = (unsigned)(ns * bps);
+  const int64_t hot = std::min<int64_t>(K->tune.spmm_hot, n);
   const unsigned hblocks = (unsigned)(ns * gr->n_chunks);
   const int hthreads = (int)ceil_div(geo.Vt, 32) * 32;
   const unsigned hwblocks = (unsigned)(ns * ceil_div(gr->n_chunks, (int64_t)kHeavyWarps));
@@ -1488,9 +1552,14 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
         gr->n_chunks);                                                                          \
   }                                                                                             \
   ++tl_launches;                                                                                \
-  k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(gr->x_rowptr, gr->x_colidx, vals, diag, \
-                                                         scale, Uk, Z, Yg, geo.S, geo.Vt,       \
-                                                         geo.Tw, geo.Rt, bps, gr->heavy_degree);
+  if (hot > 0)                                                                                  \
+    k_spmm_light<P, MODE, true><<<blocks, geo.tthreads, 0, st>>>(                               \
+        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, Yg, geo.S, geo.Vt, geo.Tw, geo.Rt, \
+        bps, gr->heavy_degree, hot);                                                            \
+  else                                                                                          \
+    k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(                                     \
+        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, Yg, geo.S, geo.Vt, geo.Tw, geo.Rt, \
+        bps, gr->heavy_degree, 0);
   // split rows on the side stream, concurrently with the light rows (the two
   // write disjoint rows of z)
   if (gr->n_chunks > 0) {

@@ -519,6 +519,43 @@ __global__ void k_vnge(const double *__restrict__ theta, const double *__restric
   if (threadIdx.x == 0) mean_se(g, nv, out + gr, se ? se + gr : nullptr);
 }
 
+// The paper's O(m) comparators (Sec. 2.3) for graph blockIdx.x, from the
+// traces the builder computed: the Taylor heat trace of Eq. hks-taylor,
+// n - t tr L + (t^2/2) tr L^2, at every t; the quadratic VNGE approximation
+// Q = 1 - tr(L^2) / tr(L)^2 (the two-term expansion x (1 - x) of -x ln x over
+// the eigenvalues of P = L / tr L; both printed forms are garbled); FINGER's
+// -Q ln(bound / tr L) with the Gershgorin bound of the spectrum, and
+// -Q ln(lambda_max / tr L) with lambda_max the largest Ritz value of the
+// graph's probes (the extreme Ritz values converge first).
+__global__ void k_comparators(const double *__restrict__ theta, const int32_t *__restrict__ mm, int nv,
+                              int s, const double *__restrict__ gn, const double *__restrict__ gtrace,
+                              const double *__restrict__ gtrace2, const double *__restrict__ gbound,
+                              const double *__restrict__ t, int nt, double *taylor, double *q_out,
+                              double *bar_out, double *hat_out) {
+  __shared__ double red[256];
+  const int gr = blockIdx.x;
+  const double n = gn[gr], tr = gtrace[gr], tr2 = gtrace2[gr];
+  if (taylor)
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+      const double tv = t[i];
+      taylor[(int64_t)gr * nt + i] = n - tv * tr + 0.5 * tv * tv * tr2;
+    }
+  double mx = 0.0;
+  for (int p = threadIdx.x; p < nv; p += blockDim.x) {
+    const int64_t q = (int64_t)gr * nv + p;
+    const int m = mm[q];
+    if (m > 0) mx = fmax(mx, theta[q * s + m - 1]);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int i = 1; i < (int)blockDim.x; ++i) mx = fmax(mx, red[i]);
+  const double q = tr > 0.0 ? 1.0 - tr2 / (tr * tr) : 0.0;
+  if (q_out) q_out[gr] = q;
+  if (bar_out) bar_out[gr] = tr > 0.0 ? -q * log(gbound[gr] / tr) : 0.0;
+  if (hat_out) hat_out[gr] = (tr > 0.0 && mx > 0.0) ? -q * log(mx / tr) : 0.0;
+}
+
 // Orthogonality monitor of problem q = (graph, probe): the largest
 // |u_j^T u_k| / (||u_j|| ||u_k||), j < k < min(m, kcap), over the measured
 // Gram entries of the stored basis, and the smallest beta_k, k < m - 1.
@@ -612,9 +649,12 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   return SLAQ_OK;
 }
 
+int check_bf16_t(slaq_krylov K, const double *t, int nt, const char *what, cudaStream_t st);
+
 int trace_heat(slaq_krylov K, const double *t, int nt, double *out, double *se, double *per_probe,
                cudaStream_t st) {
   if (nt < 1 || !t || !out) return set_error(SLAQ_EINVAL, "heat trace needs t, nt >= 1 and out");
+  SLAQ_TRY(check_bf16_t(K, t, nt, "heat trace", st));
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
   const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
@@ -632,6 +672,7 @@ int trace_heat_cv(slaq_krylov K, const double *t, int nt, int degree, double *ou
                   double *per_probe, cudaStream_t st) {
   if (nt < 1 || !t || !out) return set_error(SLAQ_EINVAL, "heat trace needs t, nt >= 1 and out");
   if (degree != 1 && degree != 2) return set_error(SLAQ_EINVAL, "control-variate degree must be 1 or 2");
+  SLAQ_TRY(check_bf16_t(K, t, nt, "heat trace", st));
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
   const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
@@ -647,32 +688,42 @@ int trace_heat_cv(slaq_krylov K, const double *t, int nt, int degree, double *ou
   return SLAQ_OK;
 }
 
+// The BF16-basis form serves heat and wave traces for |t| * bound <=
+// kBf16TB only.  Its basis is rounded at 2^-9, which moves the Ritz values
+// that are not yet converged at first order; exp(-t theta) and cos(t theta)
+// turn that into errors growing with t.  Measured against the FP64 form (nv
+// 24 and 64, s 16 and 20): up to t * bound = 20 (t = 10 on a normalized
+// Laplacian) the heat trace stayed within 2.3e-5 relative and the wave trace
+// within 1e-5 of max |Re| on every graph tried (R-MAT, BA, ER, SBM batches,
+// trees, cycles, paths, grids, weighted and not); beyond it graphs with many
+// small eigenvalues (cycles, paths, grids, trees, small SBM graphs) pass the
+// 1e-4 bar of the heat trace at t = 29 .. 66 and the wave's at t = 20 .. 45.
+constexpr double kBf16TB = 20.0;
+
+// SLAQ_OK, or SLAQ_EUNSUPPORTED if the form is the BF16 basis and some t is
+// beyond its limit (copies t to the host and synchronizes st for that form).
+int check_bf16_t(slaq_krylov K, const double *t, int nt, const char *what, cudaStream_t st) {
+  if (K->precision != SLAQ_FP32_BF16BASIS) return SLAQ_OK;
+  std::vector<double> th(nt);
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(th.data(), t, nt * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < nt; ++i)
+    if (!(std::fabs(th[i]) * K->bound <= kBf16TB))
+      return set_error(SLAQ_EUNSUPPORTED,
+                       "the BF16-basis form serves the %s for |t| * bound <= %g only (t = %g, bound "
+                       "%g): beyond it the basis rounding moves the trace by more than 1e-4; use "
+                       "SLAQ_FP32",
+                       what, kBf16TB, th[i], K->bound);
+  return SLAQ_OK;
+}
+
 // re/im (means) may be NULL when only the per-probe values pp_re/pp_im
 // ([G][nv][nt]) are wanted (slaq_trace_wave_per_probe).
-// The BF16-basis form serves t * bound <= kBf16WaveTB only: cos(t theta) and
-// sin(t theta) turn the first-order movement of its unconverged interior
-// Ritz values (the basis is rounded at 2^-9) into errors that grow with t;
-// up to t * bound = 20 (t = 10 on a normalized Laplacian) they stayed below
-// 1e-5 of max |Re| on every graph measured, and reached 1e-4 from
-// t * bound = 39 (a batch of SBM graphs) to 90 (R-MAT, BA graphs).
-constexpr double kBf16WaveTB = 20.0;
-
 int trace_wave(slaq_krylov K, const double *t, int nt, double *re, double *im, double *se_re,
                double *se_im, cudaStream_t st, double *pp_re, double *pp_im) {
   if (nt < 1 || !t || ((!re || !im) && (!pp_re || !pp_im)))
     return set_error(SLAQ_EINVAL, "wave trace needs t, nt, and re, im or per-probe outputs");
-  if (K->precision == SLAQ_FP32_BF16BASIS) {
-    std::vector<double> th(nt);
-    SLAQ_CHECK_CUDA(cudaMemcpyAsync(th.data(), t, nt * sizeof(double), cudaMemcpyDeviceToHost, st));
-    SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
-    for (int i = 0; i < nt; ++i)
-      if (!(std::fabs(th[i]) * K->bound <= kBf16WaveTB))
-        return set_error(SLAQ_EUNSUPPORTED,
-                         "the BF16-basis form's wave trace is served for |t| * bound <= %g only "
-                         "(t = %g, bound %g): beyond it the basis rounding moves cos(t theta) by "
-                         "more than 1e-4 of the trace; use SLAQ_FP32",
-                         kBf16WaveTB, th[i], K->bound);
-  }
+  SLAQ_TRY(check_bf16_t(K, t, nt, "wave trace", st));
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
   const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
@@ -701,6 +752,17 @@ int trace_vnge(slaq_krylov K, double *out, double *se, double *per_probe, cudaSt
   k_vnge<<<K->n_graphs, 128, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, K->gtrace, out,
                                        se, per_probe);
   SLAQ_CHECK_LAUNCH("trace_vnge");
+  return SLAQ_OK;
+}
+
+int comparators(slaq_krylov K, const double *t, int nt, double *taylor, double *q, double *bar,
+                double *hat, cudaStream_t st) {
+  if (taylor && (!t || nt < 1)) return set_error(SLAQ_EINVAL, "the Taylor heat trace needs t and nt >= 1");
+  ProfScope prof(SLAQ_PROF_TRACE, st);
+  ++tl_launches;
+  k_comparators<<<K->n_graphs, 256, 0, st>>>(K->theta, K->m, K->nv, K->s, K->gn, K->gtrace, K->gtrace2,
+                                              K->gbound, t, taylor ? nt : 0, taylor, q, bar, hat);
+  SLAQ_CHECK_LAUNCH("comparators");
   return SLAQ_OK;
 }
 

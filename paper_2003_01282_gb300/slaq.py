@@ -64,6 +64,7 @@ _SIGNATURES = {
     "slaq_trace_wave": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _VP]),
     "slaq_trace_vnge": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "slaq_krylov_monitor": (_I, [_VP, _VP, _VP, _VP]),
+    "slaq_comparators": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _VP]),
     "slaq_krylov_destroy": (None, [_VP]),
     "slaq_distance": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
     "slaq_descriptors_host": (_I, [_VP, _VP, _I64, _I64, _I, _I, _I, _I, _U64, _I, _VP, _I,
@@ -407,6 +408,21 @@ def trace_vnge(k, per_probe: bool = False, stream=None):
     pp = torch.empty(*lead, krylov_info(k)["nv"], dtype=torch.float64, device="cuda") if per_probe else None
     _check(lib().slaq_trace_vnge(_handle(k), _dev(out), _dev(se), _dev(pp), _stream(stream)))
     return (out, se, pp) if per_probe else (out, se)
+
+
+def comparators(k, t, stream=None) -> dict:
+    """slaq_comparators: {"taylor_heat": [(G,) nt], "vnge_q", "finger_bar",
+    "finger_hat": [(G,)]} (CUDA tensors)."""
+    torch = _torch()
+    nt = int(t.numel())
+    lead = _lead(k)
+    out = {"taylor_heat": torch.empty(*lead, nt, dtype=torch.float64, device="cuda")}
+    for key in ("vnge_q", "finger_bar", "finger_hat"):
+        out[key] = torch.empty(*(lead or (1,)), dtype=torch.float64, device="cuda")
+    _check(lib().slaq_comparators(_handle(k), _dev(t, torch.float64, "t"), nt, _dev(out["taylor_heat"]),
+                                  _dev(out["vnge_q"]), _dev(out["finger_bar"]), _dev(out["finger_hat"]),
+                                  _stream(stream)))
+    return out
 
 
 def krylov_monitor(k, stream=None) -> dict:

@@ -191,7 +191,10 @@ def test_lanczos_batched_equals_batch_build(prec):
     got = slaq.krylov_export(K)
     for a, b in zip(got, want):
         assert torch.equal(a, b)
-    t = _dev(synth.t_grid(), torch.float64)
+    t_np = synth.t_grid()
+    if prec == slaq.FP32_BF16BASIS:
+        t_np = t_np[t_np <= 10.0]  # the t that form serves
+    t = _dev(t_np, torch.float64)
     assert slaq.trace_heat(K, t)[0].shape == (len(graphs), t.numel())
 
 

@@ -52,13 +52,15 @@ def test_monitor_orthogonality_and_min_beta(precision, bar):
 
 
 def test_monitor_breakdown_graph_and_batch():
-    # K_9: every probe's Krylov space closes after two vectors (one beta)
+    # K_9: every probe's Krylov space closes after at most two vectors (one
+    # beta); a probe of one sign throughout is the null vector itself (m = 1)
     g = _g(synth.complete(9))
     K = slaq.lanczos(g, 6, 8, 1, precision=slaq.FP64)
     mon = slaq.krylov_monitor(K)
     _, beta, m = slaq.krylov_export(K)
-    assert np.all(m.cpu().numpy() == 2)
-    assert mon["min_beta"] == beta.cpu().numpy()[:, 0].min()
+    m, beta = m.cpu().numpy(), beta.cpu().numpy()
+    assert np.all((m >= 1) & (m <= 2)) and np.any(m == 2)
+    assert mon["min_beta"] == beta[m == 2, 0].min()
     assert mon["ortho"] < 1e-12
     # a batch: the worst over its graphs
     graphs = synth.sbm_batch(40, seed=3)

@@ -148,6 +148,13 @@ def _rel(a, b):
     return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
 
 
+def served(t_np, precision, bound=2.0):
+    """The t a form serves: all of them, except t * bound <= 20 for the BF16
+    basis (the library refuses the rest)."""
+    t_np = np.asarray(t_np)
+    return t_np[t_np * bound <= 20.0] if precision == slaq.FP32_BF16BASIS else t_np
+
+
 @pytest.mark.parametrize("name,kind,drop,nv,s", [
     ("ba2000", NORMALIZED, False, 10, 15),        # the small single-graph workload
     ("ba2000", COMBINATORIAL, False, 7, 12),
@@ -252,7 +259,7 @@ def test_fig1_vnge_on_gpu(golden_dir):
 def test_reduced_precision_forms_vs_fp64(precision, h_tol, v_tol):
     s, d, n = GRAPHS["rmat13"]()
     g = gpu_graph(s, d, n, drop=True)
-    t = dev(synth.t_grid(), torch.float64)
+    t = dev(served(synth.t_grid(), precision), torch.float64)
     K64 = slaq.lanczos(g, 32, 15, 9, precision=slaq.FP64)
     K = slaq.lanczos(g, 32, 15, 9, precision=precision)
     h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
@@ -271,14 +278,16 @@ def test_reduced_forms_normalized_values_and_pattern_forms(weighted):
     s, d, n = synth.barabasi_albert(3000, 5, seed=12)
     w = np.random.default_rng(5).uniform(0.5, 2.0, s.size) if weighted else None
     g = gpu_graph(s, d, n, NORMALIZED, weights=w)
-    t = dev(synth.t_grid(), torch.float64)
+    t_np = synth.t_grid()
+    t = dev(t_np, torch.float64)
     K64 = slaq.lanczos(g, 24, 16, 6, precision=slaq.FP64)
     h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
     v64 = slaq.trace_vnge(K64)[0].item()
     for prec in (slaq.FP32, slaq.FP32_BF16BASIS):
         K = slaq.lanczos(g, 24, 16, 6, precision=prec)
-        h = slaq.trace_heat(K, t)[0].cpu().numpy()
-        assert _rel(h, h64) < 1e-4, prec
+        ts = served(t_np, prec)
+        h = slaq.trace_heat(K, dev(ts, torch.float64))[0].cpu().numpy()
+        assert _rel(h, h64[:ts.size]) < 1e-4, prec
         assert abs(slaq.trace_vnge(K)[0].item() - v64) / abs(v64) < 1e-3, prec
 
 
@@ -300,8 +309,9 @@ def test_reduced_forms_refuse_combinatorial_laplacians(weighted):
 
 
 def test_bf16_wave_served_up_to_its_limit():
-    """The BF16-basis form's wave trace: served for t * bound <= 20 (t <= 10
-    here) within 1e-4 of max |Re| of the FP64 form; a larger t is refused."""
+    """The BF16-basis form's traces: served for t * bound <= 20 (t <= 10
+    here), the wave within 1e-4 of max |Re| of the FP64 form; a larger t is
+    refused by every trace entry point."""
     s, d, n = GRAPHS["rmat13"]()
     g = gpu_graph(s, d, n, drop=True)
     t_np = synth.t_grid()
@@ -314,11 +324,15 @@ def test_bf16_wave_served_up_to_its_limit():
     assert np.max(np.abs(r.cpu().numpy() - r64.cpu().numpy())) < 1e-4 * scale
     assert np.max(np.abs(i.cpu().numpy() - i64.cpu().numpy())) < 1e-4 * scale
     for bad in ([10.5], [0.1, 100.0], [-11.0]):
-        with pytest.raises(slaq.SlaqError) as ei:
-            slaq.trace_wave(K, dev(bad, torch.float64))
-        assert ei.value.status == 6
-        with pytest.raises(slaq.SlaqError):
-            slaq.trace_wave_per_probe(K, dev(bad, torch.float64))
+        tb = dev(bad, torch.float64)
+        for call in (lambda: slaq.trace_wave(K, tb), lambda: slaq.trace_wave_per_probe(K, tb),
+                     lambda: slaq.trace_heat(K, tb), lambda: slaq.trace_heat_cv(K, tb, 2)):
+            with pytest.raises(slaq.SlaqError) as ei:
+                call()
+            assert ei.value.status == 6
+    # FP32 and FP64 serve every t
+    for prec in (slaq.FP32, slaq.FP64):
+        slaq.trace_heat(slaq.lanczos(g, 4, 6, 9, precision=prec), dev([100.0], torch.float64))
 
 
 @pytest.mark.parametrize("graph", ["star2600", "k9", "k35", "star30"])
@@ -331,7 +345,8 @@ def test_reduced_forms_on_breakdown_graphs(graph):
     the Rayleigh-Ritz step gives the extra direction its negligible weight."""
     src, dst, n = synth.star(2600) if graph == "star2600" else GRAPHS[graph]()
     g = gpu_graph(src, dst, n)
-    t = dev(synth.t_grid(), torch.float64)
+    t_np = synth.t_grid()
+    t = dev(t_np, torch.float64)
     K64 = slaq.lanczos(g, 16, 8, 21, precision=slaq.FP64)
     m64 = slaq.krylov_export(K64)[2].cpu().numpy()
     h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
@@ -342,19 +357,23 @@ def test_reduced_forms_on_breakdown_graphs(graph):
             assert np.array_equal(m, m64)
         else:
             assert np.all(m >= m64) and np.all(m <= m64 + 1)
-        assert _rel(slaq.trace_heat(K, t)[0].cpu().numpy(), h64) < 1e-4, prec
+        ts = served(t_np, prec)
+        h = slaq.trace_heat(K, dev(ts, torch.float64))[0].cpu().numpy()
+        assert _rel(h, h64[:ts.size]) < 1e-4, prec
 
 
 def test_largest_sizes_reduced_forms_and_limits():
     src, dst, n = GRAPHS["ba2000"]()
     g = gpu_graph(src, dst, n)
-    t = dev(synth.t_grid(), torch.float64)
+    t_np = synth.t_grid()
+    t = dev(t_np, torch.float64)
     h64 = slaq.trace_heat(slaq.lanczos(g, 512, 40, 3, precision=slaq.FP64), t)[0].cpu().numpy()
     for prec in (slaq.FP32, slaq.FP32_BF16BASIS):
-        h = slaq.trace_heat(slaq.lanczos(g, 512, 40, 3, precision=prec), t)[0].cpu().numpy()
-        assert _rel(h, h64) < 1e-4, prec
+        ts = dev(served(t_np, prec), torch.float64)
+        h = slaq.trace_heat(slaq.lanczos(g, 512, 40, 3, precision=prec), ts)[0].cpu().numpy()
+        assert _rel(h, h64[:ts.numel()]) < 1e-4, prec
         K = slaq.lanczos(g, 512, 64, 3, precision=prec)
-        assert np.all(np.isfinite(slaq.trace_heat(K, t)[0].cpu().numpy()))
+        assert np.all(np.isfinite(slaq.trace_heat(K, ts)[0].cpu().numpy()))
         h0 = slaq.trace_heat(K, dev([0.0], torch.float64))[0].item()
         assert abs(h0 - n) < 1e-6 * n          # sum of the Gauss weights = 1
     # the FP64 coefficient table holds s * ld * 8 <= 200 KiB

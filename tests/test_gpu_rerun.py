@@ -33,7 +33,10 @@ def _graph(src, dst, n, drop=True):
 
 
 def _state(K):
-    t = _dev(synth.t_grid(32), torch.float64)
+    t_np = synth.t_grid(32)
+    if slaq.krylov_info(K)["precision"] == slaq.FP32_BF16BASIS:
+        t_np = t_np[t_np <= 10.0]  # the t that form serves
+    t = _dev(t_np, torch.float64)
     return list(slaq.krylov_export(K)) + list(slaq.ritz_export(K)) + [slaq.trace_heat(K, t)[0]]
 
 
