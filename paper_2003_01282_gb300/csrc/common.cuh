@@ -176,8 +176,6 @@ struct slaq_tuning {
   int slice_bytes = 0;     // bytes of a basis row per probe slice (0: whole rows)
   int spmm_align = -1;     // 1: SpMM row teams never straddle two warps, 0: packed
                            // (-1: aligned when a row takes more than 16 threads)
-  int spmm_hot = 0;        // > 0: the SpMM's gathers of rows < spmm_hot keep L2 priority
-                           // (evict_last) and the rest stream (evict_first); 0: no hints
 };
 
 struct slaq_krylov_s {

@@ -143,28 +143,8 @@ __device__ __forceinline__ void stb(__nv_bfloat16 *p, const float (&v)[8], float
   }
   *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
 }
-// 16-byte read-only loads with an L2 eviction-priority policy (createpolicy):
-// the SpMM keeps the most gathered rows of a vector much larger than L2
-// resident (evict_last) and streams the rest (evict_first).
-__device__ __forceinline__ uint64_t l2_policy(bool keep) {
-  uint64_t pol;
-  if (keep) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-  else asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ uint4 ld_pol(const void *p, uint64_t pol) {
-  uint4 r;
-  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-      : "l"(p), "l"(pol));
-  return r;
-}
-// the 16-byte basis vector at p as raw bits (with a policy when HINT)
-template <bool HINT>
-__device__ __forceinline__ uint4 ldraw(const void *p, uint64_t pol) {
-  if (HINT) return ld_pol(p, pol);
-  return __ldg(reinterpret_cast<const uint4 *>(p));
-}
+// the 16-byte basis vector at p as raw bits (read-only path)
+__device__ __forceinline__ uint4 ldraw(const void *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 __device__ __forceinline__ void unpack(const uint4 &t, double (&v)[2]) {
   v[0] = __hiloint2double((int)t.y, (int)t.x);
   v[1] = __hiloint2double((int)t.w, (int)t.z);
@@ -299,32 +279,21 @@ __device__ __forceinline__ void acc_add(T &s, T &c, T w, T x) {
 // COMP: compensated sums, for the split rows of the reduced forms (a row of
 // thousands of entries whose sum nearly cancels, such as a hub's row against
 // the null vector, otherwise loses about sqrt(entries) units of FP32 rounding)
-// HINT: gathers of rows < hot carry an L2 evict_last policy, the others
-// evict_first (a gathered vector much larger than L2; the execution order
-// puts the most gathered rows first, and a row's columns ascend, so the hot
-// entries of a row are its first ones).
 // Every gather is loaded as raw 16 bytes and widened only when it is summed,
 // so that four rows in flight per thread cost 16 registers whatever the form.
-template <int P, int MODE, bool COMP = false, bool HINT = false>
+template <int P, int MODE, bool COMP = false>
 __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
                                             const typename Form<P>::TW *__restrict__ vals,
                                             const typename Form<P>::TW *__restrict__ scale,
                                             const typename Form<P>::TB *__restrict__ Ul, int stride,
                                             int64_t b, int64_t e,
-                                            typename Form<P>::TW (&acc)[Form<P>::VE],
-                                            int64_t hot = 0) {
+                                            typename Form<P>::TW (&acc)[Form<P>::VE]) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   TW cmp[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v) cmp[v] = TW(0);
-  uint64_t keep = 0, drop = 0;
-  if (HINT) {
-    keep = l2_policy(true);
-    drop = l2_policy(false);
-  }
   auto row_ptr = [&](int c) { return (const void *)(Ul + (int64_t)c * stride); };
-  auto pol = [&](int c) { return c < hot ? keep : drop; };
   int64_t j = b;
   // FP32: single entries up to a 16-byte boundary of col, then 4 indices per
   // load (measured faster for FP32, slower for the BF16 basis)
@@ -333,7 +302,7 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
     const int c = __ldcs(col + j);
     const TW w = MODE == 0 ? __ldg(scale + c) : (MODE == 2 ? __ldcs(vals + j) : TW(1));
     TW x[VE];
-    unpack(ldraw<HINT>(row_ptr(c), HINT ? pol(c) : 0), x);
+    unpack(ldraw(row_ptr(c)), x);
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc_add<COMP>(acc[v], cmp[v], w, x[v]);
   }
@@ -355,7 +324,7 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
       w[q] = MODE == 0 ? __ldg(scale + c[q]) : (MODE == 2 ? __ldcs(vals + j + q) : TW(1));
     uint4 raw[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) raw[q] = ldraw<HINT>(row_ptr(c[q]), HINT ? pol(c[q]) : 0);
+    for (int q = 0; q < 4; ++q) raw[q] = ldraw(row_ptr(c[q]));
     if (COMP) {
       // the group's four products summed plainly, then one compensated add
       TW x[4][VE];
@@ -382,7 +351,7 @@ __device__ __forceinline__ void gather_rows(const int32_t *__restrict__ col,
     const int c = __ldcs(col + j);
     const TW w = MODE == 0 ? __ldg(scale + c) : (MODE == 2 ? __ldcs(vals + j) : TW(1));
     TW x[VE];
-    unpack(ldraw<HINT>(row_ptr(c), HINT ? pol(c) : 0), x);
+    unpack(ldraw(row_ptr(c)), x);
 #pragma unroll
     for (int v = 0; v < VE; ++v) acc_add<COMP>(acc[v], cmp[v], w, x[v]);
   }
@@ -422,13 +391,11 @@ __device__ __forceinline__ void finish_row(int64_t row, const typename Form<P>::
 // gathers in flight: the FP32 form runs at 32 registers per thread (full
 // occupancy), the BF16 basis at 40 (three blocks of 512 per SM; its eight
 // columns per thread need more), FP64 (bound by its FP64 arithmetic) unbounded.
-// HINT: L2 eviction priorities for the gathers (rows < hot kept); see
-// gather_rows.
 template <int P>
 constexpr int spmm_min_blocks() {
   return P == SLAQ_FP32 ? 4 : (P == SLAQ_FP32_BF16BASIS ? 3 : 1);
 }
-template <int P, int MODE, bool HINT = false>
+template <int P, int MODE>
 __global__ void __launch_bounds__(512, spmm_min_blocks<P>())
     k_spmm_light(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                  const typename Form<P>::TW *__restrict__ vals,
@@ -436,7 +403,7 @@ __global__ void __launch_bounds__(512, spmm_min_blocks<P>())
                  const typename Form<P>::TW *__restrict__ scale,
                  const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
                  const typename Form<P>::TB *__restrict__ Yg, Slc S, int Vt, int Tw, int R,
-                 int64_t bps, int64_t heavy_degree, int64_t hot) {
+                 int64_t bps, int64_t heavy_degree) {
   using TW = typename Form<P>::TW;
   constexpr int VE = Form<P>::VE;
   const int sl = (int)(blockIdx.x / bps);
@@ -455,8 +422,7 @@ __global__ void __launch_bounds__(512, spmm_min_blocks<P>())
   TW acc[VE];
 #pragma unroll
   for (int v = 0; v < VE; ++v) acc[v] = TW(0);
-  gather_rows<P, MODE, false, HINT>(col, vals, scale, MODE == 3 ? Yg + off : Ul, stride, b, e, acc,
-                                     hot);
+  gather_rows<P, MODE>(col, vals, scale, MODE == 3 ? Yg + off : Ul, stride, b, e, acc);
   finish_row<P, MODE>(row, diag, scale, Ul, stride, acc, Z + off + row * stride);
 }
 
@@ -1533,7 +1499,6 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
   const int ns = geo.S.nslices();
   const int64_t bps = ceil_div(n, geo.Rt);
   const unsigned blocks = (unsigned)(ns * bps);
-  const int64_t hot = std::min<int64_t>(K->tune.spmm_hot, n);
   const unsigned hblocks = (unsigned)(ns * gr->n_chunks);
   const int hthreads = (int)ceil_div(geo.Vt, 32) * 32;
   const unsigned hwblocks = (unsigned)(ns * ceil_div(gr->n_chunks, (int64_t)kHeavyWarps));
@@ -1552,14 +1517,9 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
         gr->n_chunks);                                                                          \
   }                                                                                             \
   ++tl_launches;                                                                                \
-  if (hot > 0)                                                                                  \
-    k_spmm_light<P, MODE, true><<<blocks, geo.tthreads, 0, st>>>(                               \
-        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, Yg, geo.S, geo.Vt, geo.Tw, geo.Rt, \
-        bps, gr->heavy_degree, hot);                                                            \
-  else                                                                                          \
-    k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(                                     \
-        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, Yg, geo.S, geo.Vt, geo.Tw, geo.Rt, \
-        bps, gr->heavy_degree, 0);
+  k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(                                       \
+      gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, Yg, geo.S, geo.Vt, geo.Tw, geo.Rt,   \
+      bps, gr->heavy_degree);
   // split rows on the side stream, concurrently with the light rows (the two
   // write disjoint rows of z)
   if (gr->n_chunks > 0) {
