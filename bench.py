@@ -458,8 +458,8 @@ def run_batched(args, dev, world=1, rank=0, tdist=None):
         with open(cache) as f:
             line = [x for x in f if not x.startswith("#")][0]
         vals = [int(v) for v in line.split("|")[1].split()]
-        shapes = dict(zip(["spmm_threads", "update_threads", "dots_threads", "slice_bytes", "spmm_align"],
-                          vals))
+        shapes = dict(zip(["spmm_threads", "update_threads", "dots_threads", "slice_bytes", "spmm_align",
+                           "spmm_tma"], vals))
     except Exception:
         pass
     td.cleanup()
@@ -1115,7 +1115,15 @@ def main():
                     help="with --kernel-capture: R-MAT scale drawn on the GPU (nv = 64)")
     ap.add_argument("--capture-steps", type=int, default=0, help="with --kernel-capture: Lanczos steps")
     ap.add_argument("--capture-nv", type=int, default=0, help="with --kernel-capture: probes")
+    ap.add_argument("--spmm-gathers", choices=["tuned", "loads", "tma"], default="tuned",
+                    help="light-row SpMM gathers of every run: the tuning's choice, 16-byte loads, "
+                         "or TMA tile::gather4 loads")
     args = ap.parse_args()
+    if args.spmm_gathers != "tuned":
+        from paper_2003_01282_gb300 import slaq
+        from paper_2003_01282_gb300.build import build
+        build()
+        slaq.set_spmm_gathers(slaq.GATHERS_LOADS if args.spmm_gathers == "loads" else slaq.GATHERS_TMA)
     if args.kernel_capture:
         kernel_capture(args)
         return

@@ -477,6 +477,29 @@ int slaq_profile_read(int category, double *ms_host, int64_t *launches_host);
  * legacy default stream. */
 int slaq_profile_gather_peak(int row_bytes, double *tbps_host);
 
+/* How the SpMM gathers the basis rows of light rows (rows of at most 2048
+ * entries), for every later Lanczos run in this process: mode 1 through the
+ * tensor memory accelerator (cp.async.bulk.tensor tile::gather4 into a
+ * shared-memory ring per warp, Blackwell and later), 0 through 16-byte
+ * loads, -1 (the initial state) as the launch-shape tuning of the run says
+ * (slaq_lanczos_batched's tune cache; loads otherwise).  A performance
+ * choice with the same arithmetic: the two paths differ only in the order
+ * the partial sums of a row are added.  Measured on GB300 the TMA path is
+ * slower than the loads, from 1.6x (R-MAT 2^24, BF16 basis) to 8x (SBM
+ * batches of short rows): its per-row work is serialized per warp.  So the
+ * loads are the default and the tuner does not try it.  The TMA path serves the FP32 and
+ * BF16-basis forms with rows of at most 256 elements and 32 lanes of 16
+ * bytes, unsliced; other runs use loads whatever the mode.  Its waits on
+ * the copies are bounded: a wait that gives up fails the run with
+ * SLAQ_ETIMEOUT.  A run reads the mode once, when it starts (a replay by
+ * slaq_lanczos_rerun keeps its run's path).  SLAQ_EINVAL for a mode outside
+ * [-1, 1]. */
+int slaq_set_spmm_gathers(int mode);
+
+/* *tma_host = 1 if the light rows of k's last run were gathered through
+ * TMA (slaq_set_spmm_gathers), 0 if through loads.  Host-side; no GPU work. */
+int slaq_krylov_gathers(slaq_krylov k, int *tma_host);
+
 /* Gauss rule of one symmetric tridiagonal matrix on the host, with the same
  * implicit-shift QR code the GPU kernel runs (Golub & Van Loan, Sec. 8.3):
  * alpha_host[m] diagonal, beta_host[m-1] off-diagonal; theta_host[m]

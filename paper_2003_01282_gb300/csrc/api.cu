@@ -260,6 +260,21 @@ using namespace slaq;
 
 static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Device-side outcome of a Lanczos run, read after it completes: word 1
+// flags a TMA gather wait that gave up (the run's z vectors are incomplete),
+// word 0 a tridiagonal eigensolver that did not converge.
+static int run_status(slaq_krylov k, cudaStream_t st) {
+  int32_t status[2] = {0, 0};
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(status, k->status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (status[1]) {
+    k->ready = false;
+    return set_error(SLAQ_ETIMEOUT, "a TMA row-gather wait of the SpMM gave up; rerun the handle");
+  }
+  if (status[0]) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
+  return SLAQ_OK;
+}
+
 extern "C" {
 
 int slaq_version(void) { return 100; }
@@ -344,12 +359,7 @@ int slaq_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int p
   SLAQ_TRY(device_check());
   cudaStream_t st = as_stream(stream);
   SLAQ_TRY(run_lanczos(g, nv, s, seed, graph_id, precision, reorth_passes, st, inout));
-  int32_t status = 0;
-  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, (*inout)->status, sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, st));
-  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
-  return SLAQ_OK;
+  return run_status((*inout), st);
 }
 
 int slaq_lanczos_probes(slaq_graph g, int nv, int probe0, int s, uint64_t seed, int graph_id,
@@ -358,12 +368,7 @@ int slaq_lanczos_probes(slaq_graph g, int nv, int probe0, int s, uint64_t seed, 
   cudaStream_t st = as_stream(stream);
   SLAQ_TRY(run_lanczos(g, nv, s, seed, graph_id, precision, reorth_passes, st, inout, nullptr,
                        probe0));
-  int32_t status = 0;
-  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, (*inout)->status, sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, st));
-  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
-  return SLAQ_OK;
+  return run_status((*inout), st);
 }
 
 int slaq_lanczos_rerun(slaq_krylov k, uint64_t seed, void *stream) {
@@ -371,11 +376,7 @@ int slaq_lanczos_rerun(slaq_krylov k, uint64_t seed, void *stream) {
   SLAQ_TRY(device_check());
   cudaStream_t st = as_stream(stream);
   SLAQ_TRY(lanczos_rerun(k, seed, st));
-  int32_t status = 0;
-  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, k->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
-  return SLAQ_OK;
+  return run_status(k, st);
 }
 
 int slaq_lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t seed,
@@ -385,12 +386,7 @@ int slaq_lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_
   cudaStream_t st = as_stream(stream);
   SLAQ_TRY(lanczos_batched(gs, count, nv, s, seed, graph_id, precision, reorth_passes, tune_cache,
                            st, inout));
-  int32_t status = 0;
-  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, (*inout)->status, sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, st));
-  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
-  return SLAQ_OK;
+  return run_status((*inout), st);
 }
 
 int slaq_probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, void *stream) {
@@ -437,6 +433,12 @@ int slaq_krylov_info(slaq_krylov k, int *nv, int *s, int *precision, int64_t *n)
   if (s) *s = k->s;
   if (precision) *precision = k->precision;
   if (n) *n = k->n;
+  return SLAQ_OK;
+}
+
+int slaq_krylov_gathers(slaq_krylov k, int *tma_host) {
+  if (!k || !tma_host) return set_error(SLAQ_EINVAL, "NULL Krylov handle or output");
+  *tma_host = k->tma ? 1 : 0;
   return SLAQ_OK;
 }
 
@@ -556,10 +558,7 @@ int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int6
   if (vnge_host) SLAQ_TRY(trace_vnge(b.k, out + 3 * ntt, nullptr, nullptr, st));
   std::vector<double> h(3 * (size_t)ntt + 1);
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(h.data(), out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  int32_t status = 0;
-  SLAQ_CHECK_CUDA(cudaMemcpyAsync(&status, b.k->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (status) return set_error(SLAQ_ENUMERIC, "tridiagonal eigensolver did not converge");
+  SLAQ_TRY(run_status(b.k, st));
   if (heat_host) std::memcpy(heat_host, h.data(), nt * sizeof(double));
   if (wave_re_host) std::memcpy(wave_re_host, h.data() + ntt, nt * sizeof(double));
   if (wave_im_host) std::memcpy(wave_im_host, h.data() + 2 * ntt, nt * sizeof(double));
@@ -646,6 +645,8 @@ int slaq_pool_probes_host(const double *values, int nprobe, int len, double *mea
   }
   return SLAQ_OK;
 }
+
+int slaq_set_spmm_gathers(int mode) { return set_spmm_gathers(mode); }
 
 int slaq_tridiag_gauss_host(const double *alpha, const double *beta, int m, double *theta,
                             double *tau2) {

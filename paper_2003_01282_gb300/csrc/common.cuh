@@ -1,6 +1,7 @@
 // Internal declarations shared by the libslaq translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -176,6 +177,9 @@ struct slaq_tuning {
   int slice_bytes = 0;     // bytes of a basis row per probe slice (0: whole rows)
   int spmm_align = -1;     // 1: SpMM row teams never straddle two warps, 0: packed
                            // (-1: aligned when a row takes more than 16 threads)
+  int spmm_tma = -1;       // light-row gathers: 1 TMA (tile::gather4), else loads
+                           // (measured slower on every workload: not a tuner candidate,
+                           // set by hand in a cache line)
 };
 
 struct slaq_krylov_s {
@@ -211,7 +215,7 @@ struct slaq_krylov_s {
   int32_t *m = nullptr;     // [nv]
   double *theta = nullptr;  // [nv][s]
   double *tau2 = nullptr;   // [nv][s]
-  int32_t *status = nullptr;  // [8]: [0] device-side error flags; bytes 8..23: monitor words
+  int32_t *status = nullptr;  // [8]: [0] eigensolver flags; [1] SpMM wait timeouts; bytes 8..23: monitor words
   uint32_t *hcount = nullptr; // [n_heavy * slices] arrival counters of split rows (kept zero)
   int64_t hcount_cap = 0;
   // batches: G graphs; per-graph arrays are [G][...] (alpha [G][nv][s], ...)
@@ -246,6 +250,13 @@ struct slaq_krylov_s {
   cudaGraphExec_t gexec = nullptr;  // captured launches of that run, or null
   int64_t graph_nodes = 0;          // nodes of the captured graph (counted as launches)
   cudaStream_t cap = nullptr;       // private stream the capture runs on
+  // light rows through TMA gathers: the tensor map over the gathered vectors
+  // and the work items of the last run (tma false: the load path)
+  bool tma = false;
+  CUtensorMap tma_map;
+  int64_t *tma_task = nullptr;  // [tma_ntasks + 1] first row of each work item
+  int64_t tma_task_cap = 0;
+  int64_t tma_ntasks = 0;
   // side stream on which the split-row SpMM runs beside the light rows
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -276,6 +287,7 @@ void krylov_free(slaq_krylov k);
 // place), else SLAQ_EINVAL: a run that failed part-way (for example out of
 // memory) leaves the handle destroyable and reusable but not readable
 int krylov_ready(slaq_krylov k);
+int set_spmm_gathers(int mode);
 int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st);
 int full_steps(slaq_krylov k, int32_t *out, cudaStream_t st);
 int lanczos_rerun(slaq_krylov k, uint64_t seed, cudaStream_t st);

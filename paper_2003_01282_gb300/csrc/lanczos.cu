@@ -24,10 +24,13 @@
 // ||u_k|| keeps the norms at beta (they would otherwise shrink or grow
 // geometrically and leave the FP32 range within a few dozen steps).
 #include <algorithm>
+#include <atomic>
 #include <limits>
 #include <cmath>
 #include <cstdlib>
 #include <type_traits>
+
+#include <cudaTypedefs.h>
 
 #include "common.cuh"
 
@@ -561,6 +564,362 @@ __global__ void __launch_bounds__(32 * kHeavyWarps)
     finish_row<P, MODE>(row, diag, scale, Ul, stride, acc, Z + off + row * stride);
   }
   if (lane == 0) *counter = 0u;  // ready for the next launch
+}
+
+// ------------------------------------------- light rows through TMA gathers
+// The light rows again, with the row gathers done by the tensor memory
+// accelerator: each warp streams the entries of its rows, and one lane turns
+// every four of them into a cp.async.bulk.tensor tile::gather4 load that
+// copies the four gathered rows of u_k (or y) into shared memory, completing
+// on an mbarrier.  A warp keeps NS stages of eight rows in flight, and
+// unlike the load path the rows in flight hold no registers.  The lanes then
+// sum the staged rows: with rows of more than 16 lanes the whole warp takes
+// each entry; narrower rows split the warp into G groups that take every
+// G-th entry and add their sums at the end of the row.
+//
+// Work items are ranges of kTmaTaskEntries entries: an item owns the rows
+// that start in its range (a row that starts there and runs past it is
+// still the item's), found once per run by a binary search of the row
+// pointers.  Split rows (more than heavy_degree entries) are skipped; the
+// split-row kernels write them.  The tensor map spans the whole stored basis
+// (or y), and gathers are addressed as row0 + j.  Waits are bounded: a wait
+// that gives up sets err and the kernel drains its copies in flight before
+// it returns.
+//
+// Measured on GB300 it is slower than the load path on every workload tried
+// (R-MAT 2^20 FP32: 61 against 21 ms of SpMM per run; BF16 basis at 2^24:
+// 525 against 326 ms): a warp serializes its rows' control work (row ends,
+// the row's own values, the next row's pointers) behind one stage pipeline,
+// while the load path overlaps that work across 64 warps per SM, and most
+// light rows hold only a few entries.  It is kept as an opt-in
+// (slaq_set_spmm_gathers), tested against the load path.
+constexpr int kTmaWarps = 8;                  // warps per block
+constexpr int kTmaG4 = 2;                     // gather4 loads per stage
+constexpr int kTmaStage = 4 * kTmaG4;         // entries per stage
+constexpr int64_t kTmaTaskEntries = 2048;     // entries per work item
+constexpr int kTmaSpinLimit = 1 << 17;        // mbarrier polls before giving up (each
+                                              // suspends up to 20 us: about 2.6 s in all)
+
+// shared memory of one gather4 load (four rows), 128-byte aligned
+__host__ __device__ inline int tma_slot_bytes(int row_bytes) {
+  return (4 * row_bytes + 127) / 128 * 128;
+}
+// one warp: NS stages, then NS mbarriers, NS x 8 weights and NS entry counts
+__host__ __device__ inline int tma_warp_bytes(int row_bytes, int ns) {
+  const int tail = ns * 8 + ns * kTmaStage * 4 + ns * 4;
+  return ns * kTmaG4 * tma_slot_bytes(row_bytes) + (tail + 127) / 128 * 128;
+}
+inline size_t tma_block_smem(int row_bytes, int ns) {
+  return (size_t)kTmaWarps * tma_warp_bytes(row_bytes, ns) + 128;  // + alignment slack
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kTmaSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "r"(20000)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// A walk over the light rows of a work item: row r, next entry j, row end e.
+struct TmaCursor {
+  int64_t r, j, e;
+};
+// Moves c to the first light row at or after r (r1 when none is left).
+__device__ __forceinline__ void tma_seek(TmaCursor &c, int64_t r, int64_t r1,
+                                         const int64_t *__restrict__ rowptr, int64_t heavy) {
+  int64_t b = 0, e = 0;
+  for (; r < r1; ++r) {
+    b = __ldg(rowptr + r);
+    e = __ldg(rowptr + r + 1);
+    if (e - b <= heavy) break;
+  }
+  c.r = r;
+  c.j = b;
+  c.e = e;
+}
+
+// task_row[t] = first row that starts at or after entry t * per (n if none),
+// t = 0 .. ntasks; task t owns rows [task_row[t], task_row[t + 1]).
+__global__ void k_tma_tasks(const int64_t *__restrict__ rowptr, int64_t n, int64_t per,
+                            int64_t ntasks, int64_t *__restrict__ task_row) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntasks;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (t == ntasks) {
+      task_row[t] = n;
+      continue;
+    }
+    const int64_t target = t * per;
+    int64_t lo = 0, hi = n;  // first r in [0, n) with rowptr[r] >= target, else n
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (rowptr[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    task_row[t] = lo;
+  }
+}
+
+template <int P, int MODE, int G, int NS>
+__global__ void __launch_bounds__(32 * kTmaWarps, G == 4 ? 3 : 2)
+    k_spmm_tma(const __grid_constant__ CUtensorMap map, int row0,
+               const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+               const typename Form<P>::TW *__restrict__ vals,
+               const typename Form<P>::TW *__restrict__ diag,
+               const typename Form<P>::TW *__restrict__ scale,
+               const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
+               int ld, int64_t heavy_degree, const int64_t *__restrict__ task_row, int64_t ntasks,
+               int32_t *__restrict__ err) {
+  using TW = typename Form<P>::TW;
+  using TB = typename Form<P>::TB;
+  constexpr int VE = Form<P>::VE;
+  constexpr int LPG = 32 / G;  // lanes per group
+  static_assert(G == 1 || G == 2 || G == 4, "one, two or four row groups per warp");
+  extern __shared__ unsigned char tma_smem[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / LPG, li = lane - grp * LPG;
+  const bool act = li < ld / VE;
+  const int rowb = ld * (int)sizeof(TB);
+  const int slotb = tma_slot_bytes(rowb);
+  const int stageb = kTmaG4 * slotb;
+  unsigned char *base =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tma_smem) + 127) &
+                                        ~(uintptr_t)127) +
+      (size_t)wib * tma_warp_bytes(rowb, NS);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(base + NS * stageb);
+  TW *wst = reinterpret_cast<TW *>(bar + NS);                  // [NS][kTmaStage]
+  int *cnt = reinterpret_cast<int *>(wst + NS * kTmaStage);  // [NS]
+  if (lane == 0)
+    for (int s = 0; s < NS; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + s)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+
+  const int64_t nw = (int64_t)gridDim.x * kTmaWarps;
+  uint32_t pc = 0, cc = 0;  // stages issued and consumed by this warp (phases follow)
+  bool ok = true;
+  TW acc[VE];
+#pragma unroll
+  for (int v = 0; v < VE; ++v) acc[v] = TW(0);
+  for (int64_t t = (int64_t)blockIdx.x * kTmaWarps + wib; t < ntasks && ok; t += nw) {
+    const int64_t r1 = task_row[t + 1];
+    TmaCursor pcur, ccur;
+    tma_seek(pcur, task_row[t], r1, rowptr, heavy_degree);
+    ccur = pcur;
+    bool pdone = false;
+    // The producer prepares stages three deep in registers, so that no load
+    // latency sits on the issue path: stage C has its column loads in
+    // flight, B its weight loads (scale of the column, which needs the
+    // column first), A is complete and is the next to issue.  Lane q holds
+    // entry q of a stage.
+    struct Pre {
+      int c, filled;
+      TW w;
+    };
+    Pre A{0, 0, TW(1)}, B{0, 0, TW(1)}, C{0, 0, TW(1)};
+    auto prepare = [&](Pre &x) {
+      int64_t jq = 0;
+      int filled = 0;
+      if (pcur.r < r1 && pcur.e - pcur.j >= kTmaStage) {  // the stage lies in one row
+        jq = pcur.j + lane;
+        filled = kTmaStage;
+        pcur.j += kTmaStage;
+      } else {
+        while (filled < kTmaStage) {
+          while (pcur.r < r1 && pcur.j == pcur.e)
+            tma_seek(pcur, pcur.r + 1, r1, rowptr, heavy_degree);
+          if (pcur.r >= r1) break;
+          const int take = (int)::min((int64_t)(kTmaStage - filled), pcur.e - pcur.j);
+          if (lane >= filled && lane < filled + take) jq = pcur.j + (lane - filled);
+          filled += take;
+          pcur.j += take;
+        }
+      }
+      x.filled = filled;
+      if (lane < filled) {
+        x.c = __ldcs(col + jq);
+        if (MODE == 2) x.w = __ldcs(vals + jq);
+      }
+    };
+    auto weigh = [&](Pre &x) {
+      if (MODE == 0 && lane < x.filled) x.w = __ldg(scale + x.c);
+    };
+    prepare(A);
+    weigh(A);
+    prepare(B);
+    weigh(B);
+    prepare(C);
+    // issues stage A into the next slot, then shifts the pipeline
+    auto issue = [&]() {
+      const int filled = A.filled;
+      if (filled == 0) {
+        pdone = true;
+        return;
+      }
+      const int slot = (int)(pc % NS);
+      int c = A.c;
+      if ((MODE == 0 || MODE == 2) && lane < filled) wst[slot * kTmaStage + lane] = A.w;
+      // unused slots of the last gather4 repeat the stage's last row (never summed)
+      if (filled < kTmaStage) {
+        const int clast = __shfl_sync(0xffffffffu, c, filled - 1);
+        if (lane >= filled) c = clast;
+      }
+      c += row0;
+      // lanes 0 and 4 issue the two gather4 loads, each with its own four rows
+      const int c1 = __shfl_down_sync(0xffffffffu, c, 1);
+      const int c2 = __shfl_down_sync(0xffffffffu, c, 2);
+      const int c3 = __shfl_down_sync(0xffffffffu, c, 3);
+      const uint32_t b = smem_u32(bar + slot);
+      const int nblk = (filled + 3) >> 2;
+      if (lane == 0) {
+        cnt[slot] = filled;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                     "r"(nblk * 4 * rowb)
+                     : "memory");
+      }
+      __syncwarp();  // weights and count stored, the stage armed, before its loads
+      if ((lane & 3) == 0 && (lane >> 2) < nblk)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::"
+            "bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+                smem_u32(base + (size_t)slot * stageb + (size_t)(lane >> 2) * slotb)),
+            "l"(reinterpret_cast<uint64_t>(&map)), "r"(0), "r"(c), "r"(c1), "r"(c2), "r"(c3),
+            "r"(b)
+            : "memory");
+      ++pc;
+      A = B;
+      B = C;
+      weigh(B);
+      prepare(C);
+    };
+    // The consumer's current row: its own basis values, diagonal and scale,
+    // loaded when the row becomes current and used when it is written.
+    uint4 ru = make_uint4(0, 0, 0, 0);
+    TW rdiag = TW(0), rscale = TW(1);
+    auto load_row = [&]() {
+      if (ccur.r < r1 && grp == 0 && act) {
+        ru = ldraw(U + ccur.r * ld + li * VE);
+        rdiag = __ldg(diag + ccur.r);
+        if (MODE == 0 || MODE == 3) rscale = __ldg(scale + ccur.r);
+      }
+    };
+    // the end of row r: add the groups' sums, write z_r, clear
+    auto flush = [&](int64_t row) {
+      if (G > 1) {
+#pragma unroll
+        for (int v = 0; v < VE; ++v)
+#pragma unroll
+          for (int o = LPG; o < 32; o <<= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+      }
+      if (grp == 0 && act) {
+        TW y[VE], z[VE];
+        unpack(ru, y);
+#pragma unroll
+        for (int v = 0; v < VE; ++v)
+          z[v] = MODE == 2 ? fma(rdiag, y[v], acc[v]) : fma(rdiag, y[v], -rscale * acc[v]);
+        stw_cs<TW, VE>(Z + row * ld + li * VE, z);
+      }
+#pragma unroll
+      for (int v = 0; v < VE; ++v) acc[v] = TW(0);
+    };
+    // rows without entries at the consumer's position are written at once
+    auto settle = [&]() {
+      while (ccur.r < r1 && ccur.j == ccur.e) {
+        flush(ccur.r);
+        tma_seek(ccur, ccur.r + 1, r1, rowptr, heavy_degree);
+        load_row();
+      }
+    };
+    while (pc - cc < (uint32_t)NS && !pdone) issue();
+    __syncwarp();
+    load_row();
+    settle();
+    while (ccur.r < r1) {
+      if (cc == pc) {  // the walks disagree: cannot happen
+        ok = false;
+        break;
+      }
+      const int slot = (int)(cc % NS);
+      if (!mbar_wait(smem_u32(bar + slot), (cc / NS) & 1u)) {
+        ok = false;
+        break;
+      }
+      const int filled = cnt[slot];
+      const unsigned char *stg = base + (size_t)slot * stageb;
+      int q0 = 0;
+      if (filled == kTmaStage && ccur.e - ccur.j >= kTmaStage) {
+        // the whole stage lies in the current row: this group's entries,
+        // unrolled
+        if (act) {
+#pragma unroll
+          for (int i = 0; i < kTmaStage / G; ++i) {
+            const int q = grp + G * i;
+            const TW w = (MODE == 0 || MODE == 2) ? wst[slot * kTmaStage + q] : TW(1);
+            const uint4 raw = *reinterpret_cast<const uint4 *>(stg + (q >> 2) * slotb +
+                                                               (q & 3) * rowb + li * 16);
+            TW x[VE];
+            unpack(raw, x);
+#pragma unroll
+            for (int v = 0; v < VE; ++v) acc[v] = fma(w, x[v], acc[v]);
+          }
+        }
+        q0 = kTmaStage;
+        ccur.j += kTmaStage;
+        if (ccur.j == ccur.e) {
+          flush(ccur.r);
+          tma_seek(ccur, ccur.r + 1, r1, rowptr, heavy_degree);
+          load_row();
+          settle();
+        }
+      }
+      while (q0 < filled) {
+        const int take = (int)::min((int64_t)(filled - q0), ccur.e - ccur.j);
+        if (ccur.r >= r1 || take <= 0) {  // the walks disagree: cannot happen
+          ok = false;
+          break;
+        }
+        for (int q = q0; q < q0 + take; ++q) {
+          if ((q & (G - 1)) != grp || !act) continue;
+          const TW w = (MODE == 0 || MODE == 2) ? wst[slot * kTmaStage + q] : TW(1);
+          const uint4 raw =
+              *reinterpret_cast<const uint4 *>(stg + (q >> 2) * slotb + (q & 3) * rowb + li * 16);
+          TW x[VE];
+          unpack(raw, x);
+#pragma unroll
+          for (int v = 0; v < VE; ++v) acc[v] = fma(w, x[v], acc[v]);
+        }
+        q0 += take;
+        ccur.j += take;
+        if (ccur.j == ccur.e) {
+          flush(ccur.r);
+          tma_seek(ccur, ccur.r + 1, r1, rowptr, heavy_degree);
+          load_row();
+          settle();
+        }
+      }
+      __syncwarp();  // every lane has read the stage before it is refilled
+      ++cc;
+      if (!ok) break;
+      if (!pdone) issue();
+      __syncwarp();
+    }
+    if (ok && cc != pc) ok = false;
+  }
+  if (!ok) {
+    if (lane == 0) atomicOr(err, 1);
+    for (; cc < pc; ++cc)  // copies still in flight land before the block exits
+      if (!mbar_wait(smem_u32(bar + cc % NS), (cc / NS) & 1u)) break;
+  }
 }
 
 // ------------------------------------------------------ compensated sums
@@ -1474,6 +1833,113 @@ int upload(T **dev, int64_t *cap, const std::vector<T> &host, cudaStream_t st) {
   return SLAQ_OK;
 }
 
+// ---------------------------------------------------- TMA light-row path
+// Stages in flight per warp: 8 for rows of at most 128 bytes (the BF16
+// basis with nv <= 64: three blocks of 8 warps still fit an SM), else 4.
+inline int tma_stages(int row_bytes) { return row_bytes <= 128 ? 8 : 4; }
+
+std::atomic<int> g_spmm_gathers{-1};
+
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                        &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<EncodeTiled>(f);
+  }();
+  return fn;
+}
+
+// Decides the light-row path of this run and, for TMA, encodes the tensor
+// map (rows of ld elements over the stored basis, or over y) and builds the
+// work items.  Ineligible shapes keep the load path: sliced rows, rows wider
+// than a TMA box (256 elements) or a warp, or more rows than an int32
+// coordinate holds.
+template <int P>
+int tma_setup(slaq_graph gr, slaq_krylov K, const Geometry &geo, cudaStream_t st) {
+  K->tma = false;
+  if constexpr (P == SLAQ_FP64) {
+    return SLAQ_OK;
+  } else {
+    using TB = typename Form<P>::TB;
+    const int forced = g_spmm_gathers.load();
+    const bool want = forced >= 0 ? forced != 0 : K->tune.spmm_tma > 0;
+    if (!want || gr->n < 1) return SLAQ_OK;
+    const int ld = K->ld;
+    const int64_t rows = K->ymode ? gr->n : (int64_t)K->s * gr->n;
+    const int rowb = ld * (int)sizeof(TB);
+    if (geo.S.w != ld || ld > 256 || ld / Form<P>::VE > 32 || rows > INT32_MAX ||
+        tma_block_smem(rowb, tma_stages(rowb)) > (size_t)227 * 1024)
+      return SLAQ_OK;
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return SLAQ_OK;
+    void *gbase = K->ymode ? static_cast<void *>(K->Y) : K->U;
+    const cuuint64_t gdim[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)rowb};
+    const cuuint32_t box[2] = {(cuuint32_t)ld, 1};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult cr =
+        enc(&K->tma_map,
+            P == SLAQ_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            gbase, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return SLAQ_OK;
+    const int64_t ntasks = gr->nnz / kTmaTaskEntries + 1;
+    if (ntasks + 1 > K->tma_task_cap) {
+      K->tma_task_cap = 0;
+      SLAQ_TRY(grow(&K->tma_task, (size_t)(ntasks + 1)));
+      K->tma_task_cap = ntasks + 1;
+    }
+    ++tl_launches;
+    k_tma_tasks<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntasks + 1, 256), 4096)),
+                  256, 0, st>>>(gr->x_rowptr, gr->n, kTmaTaskEntries, ntasks, K->tma_task);
+    SLAQ_CHECK_LAUNCH("tma_tasks");
+    K->tma_ntasks = ntasks;
+    K->tma = true;
+    return SLAQ_OK;
+  }
+}
+
+template <int P, int MODE, int G, int NS>
+int launch_tma(slaq_graph gr, slaq_krylov K, int row0, const typename Form<P>::TW *vals,
+               const typename Form<P>::TW *diag, const typename Form<P>::TW *scale,
+               const typename Form<P>::TB *Uk, typename Form<P>::TW *Z, cudaStream_t st) {
+  using TB = typename Form<P>::TB;
+  auto kern = k_spmm_tma<P, MODE, G, NS>;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  SLAQ_CHECK_CUDA(attr);
+  const size_t smem = tma_block_smem(K->ld * (int)sizeof(TB), NS);
+  const int per_sm = blocks_per_sm(kern, 32 * kTmaWarps, smem);
+  const int64_t blocks = std::max<int64_t>(
+      1, std::min<int64_t>(ceil_div(K->tma_ntasks, kTmaWarps), (int64_t)per_sm * num_sms()));
+  ++tl_launches;
+  kern<<<(unsigned)blocks, 32 * kTmaWarps, smem, st>>>(K->tma_map, row0, gr->x_rowptr,
+                                                      gr->x_colidx, vals, diag, scale, Uk, Z, K->ld,
+                                                      gr->heavy_degree, K->tma_task, K->tma_ntasks,
+                                                      K->status + 1);
+  return SLAQ_OK;
+}
+
+template <int P, int MODE>
+int spmm_tma(slaq_graph gr, slaq_krylov K, int row0, const typename Form<P>::TW *vals,
+             const typename Form<P>::TW *diag, const typename Form<P>::TW *scale,
+             const typename Form<P>::TB *Uk, typename Form<P>::TW *Z, cudaStream_t st) {
+  // one, two or four rows per warp; rows of at most 8 lanes (128 bytes)
+  // take four rows per warp and 8 stages (tma_stages)
+  const int V = K->ld / Form<P>::VE;
+  if (V > 16) return launch_tma<P, MODE, 1, 4>(gr, K, row0, vals, diag, scale, Uk, Z, st);
+  if (V > 8) return launch_tma<P, MODE, 2, 4>(gr, K, row0, vals, diag, scale, Uk, Z, st);
+  return launch_tma<P, MODE, 4, 8>(gr, K, row0, vals, diag, scale, Uk, Z, st);
+}
+
 template <int P>
 int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t st) {
   ProfScope prof(SLAQ_PROF_SPMM, st);
@@ -1516,10 +1982,16 @@ int spmm(slaq_graph gr, slaq_krylov K, const Geometry &geo, int k, cudaStream_t 
         gr->heavy_row, gr->heavy_first, gr->chunk_slot, K->hcount, Yg, geo.S, geo.Vt,           \
         gr->n_chunks);                                                                          \
   }                                                                                             \
-  ++tl_launches;                                                                                \
-  k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(                                       \
-      gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, Yg, geo.S, geo.Vt, geo.Tw, geo.Rt,   \
-      bps, gr->heavy_degree);
+  if (K->tma) {                                                                                 \
+    if constexpr (P != SLAQ_FP64)                                                               \
+      SLAQ_TRY((spmm_tma<P, MODE>(gr, K, MODE == 3 ? 0 : (int)((int64_t)k * n), vals, diag,      \
+                                  scale, Uk, Z, st)));                                          \
+  } else {                                                                                      \
+    ++tl_launches;                                                                              \
+    k_spmm_light<P, MODE><<<blocks, geo.tthreads, 0, st>>>(                                     \
+        gr->x_rowptr, gr->x_colidx, vals, diag, scale, Uk, Z, Yg, geo.S, geo.Vt, geo.Tw,        \
+        geo.Rt, bps, gr->heavy_degree);                                                         \
+  }
   // split rows on the side stream, concurrently with the light rows (the two
   // write disjoint rows of z)
   if (gr->n_chunks > 0) {
@@ -1743,6 +2215,8 @@ int lanczos_form(slaq_graph gr, slaq_krylov K, cudaStream_t st, bool launch_only
       K->G = K->n_dchunks * kMaxSub;
     }
   }
+  if (!launch_only) SLAQ_TRY(tma_setup<P>(gr, K, geo, st));
+  SLAQ_CHECK_CUDA(cudaMemsetAsync(K->status + 1, 0, sizeof(int32_t), st));
   {
     ProfScope prof(SLAQ_PROF_PROBES, st);
     const int64_t nvt = (int64_t)K->n_graphs * K->nv;
@@ -1863,7 +2337,7 @@ void krylov_free(slaq_krylov k) {
                   k->m, k->theta, k->tau2, k->status, k->hcount, k->gn, k->gtrace, k->gtrace2,
                   k->gbound,
                   k->d_row0, k->d_rows, k->d_goff, k->u_row0, k->u_rows, k->u_graph,
-                  k->pro_full, k->pro_any, k->omega};
+                  k->pro_full, k->pro_any, k->omega, k->tma_task};
   for (void *p : ptrs) dmfree(p);
   hmfree(k->pro_any_host);
   if (k->ev_flag) cudaEventDestroy(k->ev_flag);
@@ -2025,6 +2499,12 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
   K->ready = true;
   *inout = K;
   guard.fresh = false;  // the caller owns it now
+  return SLAQ_OK;
+}
+
+int set_spmm_gathers(int mode) {
+  if (mode < -1 || mode > 1) return set_error(SLAQ_EINVAL, "gather path must be -1, 0 or 1");
+  g_spmm_gathers.store(mode);
   return SLAQ_OK;
 }
 

@@ -83,7 +83,10 @@ __global__ void k_ritz_pencil(const double *__restrict__ gram_all,
   int bad = 0;
   // unit-diagonal scaling D = diag(G)^{-1/2}, kept in RV
   for (int i = 0; i < m; ++i) RV(i) = rsqrt(GE(i, i));
-  // Cholesky of D G D
+  // Cholesky of D G D; ic holds the reciprocal pivots, so that the solves
+  // below multiply (an FP64 division costs several FMAs on the FP64 pipe this
+  // kernel is bound by)
+  double ic[kMaxS];
   for (int j = 0; j < m; ++j) {
     double dj = GE(j, j) * RV(j) * RV(j);
     for (int k = 0; k < j; ++k) dj -= RC(j, k) * RC(j, k);
@@ -93,32 +96,30 @@ __global__ void k_ritz_pencil(const double *__restrict__ gram_all,
     }
     const double cjj = sqrt(dj), icjj = 1.0 / cjj;
     RC(j, j) = cjj;
+    ic[j] = icjj;
     for (int i = j + 1; i < m; ++i) {
       double x = GE(i, j) * RV(i) * RV(j);
       for (int k = 0; k < j; ++k) x -= RC(i, k) * RC(j, k);
       RC(i, j) = x * icjj;
     }
   }
-  // A = C^{-1} (D M D) C^{-T}: forward substitution on the columns, then on the rows
+  // B = C^{-1} (D M D): forward substitution down the columns
   for (int j = 0; j < m; ++j)
     for (int i = 0; i < m; ++i) {
       double x = ME(i, j) * RV(i) * RV(j);
       for (int k = 0; k < i; ++k) x -= RC(i, k) * RA(k, j);
-      RA(i, j) = x / RC(i, i);
+      RA(i, j) = x * ic[i];
     }
+  // A = B C^{-T}, symmetric: only its lower triangle is formed (entry (i, l)
+  // needs B's row i up to column l) and used below
   for (int i = 0; i < m; ++i)
-    for (int l = 0; l < m; ++l) {
+    for (int l = 0; l <= i; ++l) {
       double y = RA(i, l);
       for (int k = 0; k < l; ++k) y -= RC(l, k) * RA(i, k);
-      RA(i, l) = y / RC(l, l);
+      RA(i, l) = y * ic[l];
     }
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < i; ++j) {
-      const double a = 0.5 * (RA(i, j) + RA(j, i));
-      RA(i, j) = a;
-      RA(j, i) = a;
-    }
-  // Householder tridiagonalization; reflector k acts on indices k+1..m-1
+  // Householder tridiagonalization on the lower triangle; reflector k acts
+  // on indices k+1..m-1
   double d[kMaxS], e[kMaxS], w[kMaxS];
   for (int k = 0; k + 2 < m; ++k) {
     double xn2 = 0.0;
@@ -140,7 +141,8 @@ __global__ void k_ritz_pencil(const double *__restrict__ gram_all,
     double pv = 0.0;
     for (int i = k + 1; i < m; ++i) {
       double x = 0.0;
-      for (int j = k + 1; j < m; ++j) x += RA(i, j) * RV(j);
+      for (int j = k + 1; j <= i; ++j) x += RA(i, j) * RV(j);
+      for (int j = i + 1; j < m; ++j) x += RA(j, i) * RV(j);
       x *= b;
       RW(i) = x;
       pv += x * RV(i);
@@ -148,7 +150,7 @@ __global__ void k_ritz_pencil(const double *__restrict__ gram_all,
     const double hw = 0.5 * b * pv;
     for (int i = k + 1; i < m; ++i) RW(i) -= hw * RV(i);
     for (int i = k + 1; i < m; ++i)
-      for (int j = k + 1; j < m; ++j) RA(i, j) -= RV(i) * RW(j) + RW(i) * RV(j);
+      for (int j = k + 1; j <= i; ++j) RA(i, j) -= RV(i) * RW(j) + RW(i) * RV(j);
   }
   for (int i = 0; i < m; ++i) d[i] = RA(i, i);
   if (m >= 2) e[m - 2] = RA(m - 1, m - 2);

@@ -35,7 +35,9 @@ std::string tune_key(slaq_graph g, int nv, int s, int precision, int reorth) {
   return buf;
 }
 
-// Cache file: one line per workload class, "<key> | spmm upd dots slice align".
+// Cache file: one line per workload class,
+// "<key> | spmm upd dots slice align tma" (lines without the last field,
+// written before the TMA gathers existed, read as tma = -1).
 int read_cache(const char *path, std::map<std::string, slaq_tuning> *out) {
   FILE *f = fopen(path, "r");
   if (!f) {
@@ -49,9 +51,10 @@ int read_cache(const char *path, std::map<std::string, slaq_tuning> *out) {
     std::string key(line, bar - line);
     while (!key.empty() && key.back() == ' ') key.pop_back();
     slaq_tuning t;
-    if (sscanf(bar + 1, "%d %d %d %d %d", &t.spmm_threads, &t.upd_threads, &t.dots_threads,
-               &t.slice_bytes, &t.spmm_align) == 5)
-      (*out)[key] = t;
+    const int got = sscanf(bar + 1, "%d %d %d %d %d %d", &t.spmm_threads, &t.upd_threads,
+                           &t.dots_threads, &t.slice_bytes, &t.spmm_align, &t.spmm_tma);
+    if (got == 5) t.spmm_tma = -1;
+    if (got == 5 || got == 6) (*out)[key] = t;
   }
   fclose(f);
   return SLAQ_OK;
@@ -62,11 +65,11 @@ int write_cache(const char *path, const std::map<std::string, slaq_tuning> &all)
   FILE *f = fopen(tmp.c_str(), "w");
   if (!f) return set_error(SLAQ_EINVAL, "cannot write tune cache %s: %s", path, strerror(errno));
   fprintf(f, "# slaq launch-shape cache: <workload class> | spmm_threads upd_threads "
-             "dots_threads slice_bytes spmm_align\n");
+             "dots_threads slice_bytes spmm_align spmm_tma\n");
   for (const auto &kv : all)
-    fprintf(f, "%s | %d %d %d %d %d\n", kv.first.c_str(), kv.second.spmm_threads,
+    fprintf(f, "%s | %d %d %d %d %d %d\n", kv.first.c_str(), kv.second.spmm_threads,
             kv.second.upd_threads, kv.second.dots_threads, kv.second.slice_bytes,
-            kv.second.spmm_align);
+            kv.second.spmm_align, kv.second.spmm_tma);
   const bool ok = fclose(f) == 0;
   if (!ok || rename(tmp.c_str(), path) != 0)
     return set_error(SLAQ_EINVAL, "cannot write tune cache %s: %s", path, strerror(errno));

@@ -77,6 +77,8 @@ _SIGNATURES = {
     "slaq_profile_enable": (_I, [_I]),
     "slaq_profile_read": (_I, [_I, _VP, _VP]),
     "slaq_profile_gather_peak": (_I, [_I, _VP]),
+    "slaq_set_spmm_gathers": (_I, [_I]),
+    "slaq_krylov_gathers": (_I, [_VP, _VP]),
 }
 
 PROF_NAMES = ["build", "probes", "spmm", "dots", "update", "reduce", "ritz", "trace", "dist"]
@@ -527,6 +529,22 @@ def debug_fail_alloc(nth: int):
 def debug_live_allocs() -> int:
     """slaq_debug_live_allocs: allocations the library holds."""
     return int(lib().slaq_debug_live_allocs())
+
+
+GATHERS_TUNED, GATHERS_LOADS, GATHERS_TMA = -1, 0, 1
+
+
+def set_spmm_gathers(mode: int):
+    """slaq_set_spmm_gathers: light-row gathers of later runs through TMA
+    (GATHERS_TMA), loads (GATHERS_LOADS) or the run's tuning (GATHERS_TUNED)."""
+    _check(lib().slaq_set_spmm_gathers(int(mode)))
+
+
+def krylov_gathers(k) -> int:
+    """slaq_krylov_gathers: 1 if k's last run gathered its light rows through TMA."""
+    v = C.c_int()
+    _check(lib().slaq_krylov_gathers(_handle(k), C.byref(v)))
+    return v.value
 
 
 def profile_enable(on: bool = True):

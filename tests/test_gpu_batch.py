@@ -219,7 +219,8 @@ def test_lanczos_batched_tune_cache(tmp_path):
     lines = [ln for ln in cache.read_text().splitlines() if ln and not ln.startswith("#")]
     assert len(lines) == 1 and "nv=8 s=12" in lines[0]
     shape = [int(x) for x in lines[0].split("|")[1].split()]
-    assert len(shape) == 5 and shape[0] in (128, 256, 512) and shape[2] in (0, 64, 128, 256)
+    assert len(shape) == 6 and shape[0] in (128, 256, 512) and shape[2] in (0, 64, 128, 256)
+    assert shape[5] in (-1, 1)
     K2 = slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP64, tune_cache=str(cache))
     assert cache.read_text().splitlines()[1:] == lines        # read, not re-tuned
     for x, y in zip(slaq.krylov_export(K1), slaq.krylov_export(K2)):
@@ -228,8 +229,10 @@ def test_lanczos_batched_tune_cache(tmp_path):
     ref = slaq.krylov_export(slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP64))
     for x, y in zip(slaq.krylov_export(K1)[:2], ref[:2]):
         np.testing.assert_allclose(x.cpu().numpy(), y.cpu().numpy(), rtol=RTOL, atol=RTOL * 2)
-    # every launch shape in the candidate lists runs correctly
-    for line in ("256 256 128 0 1", "512 128 64 128 0", "128 512 256 256 1"):
+    # every launch shape in the candidate lists runs correctly (TMA gathers in
+    # the last field; a line of five fields, from before that field, reads as -1)
+    for line in ("256 256 128 0 1 1", "512 128 64 128 0 -1", "128 512 256 256 1 1",
+                 "256 256 0 0 -1 1", "256 256 128 0 1"):
         cache.write_text(lines[0].split("|")[0] + "| " + line + "\n")
         K3 = slaq.lanczos_batched(hs, nv, s, seed, precision=slaq.FP32, tune_cache=str(cache))
         h3 = slaq.trace_heat(K3, _dev(synth.t_grid(), torch.float64))[0].cpu().numpy()
@@ -272,3 +275,27 @@ def test_batch_graph_with_no_kept_nodes(prec):
                                   flags=slaq.DROP_ISOLATED)
         hs = slaq.trace_heat(slaq.lanczos(gs, nv, s, seed, graph_id=g, precision=prec), t)[0]
         np.testing.assert_allclose(heat[g], hs.cpu().numpy(), rtol=1e-12 if prec == slaq.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("precision", [slaq.FP32, slaq.FP32_BF16BASIS])
+def test_batched_rayleigh_ritz_thread_per_problem_vs_fp64(precision):
+    """>= 4096 problems take the thread-per-problem Rayleigh-Ritz kernel
+    (the batch path); its rule must meet the reduced forms' bars against the
+    FP64 form per graph: heat within relative 1e-4 on the t the form serves,
+    VNGE within 1e-3."""
+    graphs = synth.sbm_batch(220, seed=7)
+    gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
+    nv, s = 20, 15
+    assert 220 * nv >= 4096
+    t_np = synth.t_grid(64)
+    if precision == slaq.FP32_BF16BASIS:
+        t_np = t_np[t_np * 2.0 <= 20.0]
+    t = _dev(t_np, torch.float64)
+    K64 = slaq.lanczos(gb, nv, s, 3, precision=slaq.FP64)
+    K = slaq.lanczos(gb, nv, s, 3, precision=precision)
+    h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
+    h = slaq.trace_heat(K, t)[0].cpu().numpy()
+    assert np.max(np.abs(h - h64) / np.abs(h64)) < 1e-4
+    v64 = slaq.trace_vnge(K64)[0].cpu().numpy()
+    v = slaq.trace_vnge(K)[0].cpu().numpy()
+    assert np.max(np.abs(v - v64) / np.abs(v64)) < 1e-3
