@@ -365,7 +365,15 @@ int slaq_distance(const double *a, const double *b, int nt, int kind, double *ou
 /* The whole path in one call, from host memory to host memory: copies the
  * edge list and t grid to the device, builds the Laplacian, runs Lanczos and
  * the quadrature, and copies heat[nt], wave_re[nt], wave_im[nt] and vnge[1]
- * back (any output may be NULL).  Synchronizes `stream` before returning. */
+ * back (any output may be NULL).  Synchronizes `stream` before returning.
+ * The Krylov workspace of a successful call (s * n' * nv basis values, plus
+ * O(n' nv) work vectors) stays allocated for the next call on the same
+ * device with the same nv, s and precision, which then skips its allocation;
+ * slaq_release_cached frees it. */
+/* Frees the workspaces slaq_descriptors_host keeps between calls, on every
+ * device.  Must not run concurrently with a slaq_descriptors_host call. */
+int slaq_release_cached(void);
+
 int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int64_t n_edges,
                           int64_t n_nodes, int kind, int flags, int nv, int s, uint64_t seed,
                           int precision, const double *t_host, int nt, double *heat_host,

@@ -508,6 +508,61 @@ int slaq_distance(const double *a, const double *b, int nt, int kind, double *ou
   return distance(a, b, nt, kind, out, as_stream(stream));
 }
 
+}  // extern "C"
+
+// The Krylov workspace of slaq_descriptors_host's last call on each device,
+// kept for the next call (its basis alone is s * n' * nv * 4 bytes: 5 GB at
+// R-MAT 2^20 with nv = 100, whose cudaMalloc and cudaFree would otherwise be
+// paid on every call).  A call takes the slot's handle (or none), and gives
+// it back when it succeeds; a second handle for the same device is freed.
+namespace {
+constexpr int kCacheDevices = 64;
+std::mutex g_host_cache_mu;
+slaq_krylov g_host_cache[kCacheDevices] = {};
+
+slaq_krylov host_cache_take(int dev, int nv, int s, int precision) {
+  slaq_krylov k = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_host_cache_mu);
+    if (dev < 0 || dev >= kCacheDevices) return nullptr;
+    k = g_host_cache[dev];
+    g_host_cache[dev] = nullptr;
+  }
+  if (k && (k->nv != nv || k->s != s || k->precision != precision)) {
+    krylov_free(k);  // idle: its last call synchronized its stream
+    k = nullptr;
+  }
+  return k;
+}
+
+void host_cache_put(int dev, slaq_krylov k) {
+  {
+    std::lock_guard<std::mutex> lock(g_host_cache_mu);
+    if (dev >= 0 && dev < kCacheDevices && !g_host_cache[dev]) {
+      g_host_cache[dev] = k;
+      return;
+    }
+  }
+  krylov_free(k);
+}
+}  // namespace
+
+extern "C" {
+
+int slaq_release_cached(void) {
+  std::lock_guard<std::mutex> lock(g_host_cache_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int d = 0; d < kCacheDevices; ++d) {
+    if (!g_host_cache[d]) continue;
+    cudaSetDevice(d);
+    krylov_free(g_host_cache[d]);
+    g_host_cache[d] = nullptr;
+  }
+  cudaSetDevice(cur);
+  return SLAQ_OK;
+}
+
 int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int64_t n_edges,
                           int64_t n_nodes, int kind, int flags, int nv, int s, uint64_t seed,
                           int precision, const double *t_host, int nt, double *heat_host,
@@ -551,6 +606,9 @@ int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int6
   if (t_host && nt > 0)
     SLAQ_CHECK_CUDA(cudaMemcpyAsync(t, t_host, nt * sizeof(double), cudaMemcpyHostToDevice, st));
   SLAQ_TRY(build_laplacian(src, dst, n_edges, n_nodes, nullptr, kind, flags, st, &b.g));
+  int dev = 0;
+  SLAQ_CHECK_CUDA(cudaGetDevice(&dev));
+  b.k = host_cache_take(dev, nv, s, precision);
   SLAQ_TRY(run_lanczos(b.g, nv, s, seed, 0, precision, 1, st, &b.k));
   if (heat_host) SLAQ_TRY(trace_heat(b.k, t, nt, out, nullptr, nullptr, st));
   if (wave_re_host || wave_im_host)
@@ -563,6 +621,8 @@ int slaq_descriptors_host(const int32_t *src_host, const int32_t *dst_host, int6
   if (wave_re_host) std::memcpy(wave_re_host, h.data() + ntt, nt * sizeof(double));
   if (wave_im_host) std::memcpy(wave_im_host, h.data() + 2 * ntt, nt * sizeof(double));
   if (vnge_host) *vnge_host = h[3 * ntt];
+  host_cache_put(dev, b.k);  // b's destructor synchronizes st before the next call can take it
+  b.k = nullptr;
   return SLAQ_OK;
 }
 

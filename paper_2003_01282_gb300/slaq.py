@@ -78,6 +78,7 @@ _SIGNATURES = {
     "slaq_profile_read": (_I, [_I, _VP, _VP]),
     "slaq_profile_gather_peak": (_I, [_I, _VP]),
     "slaq_set_spmm_gathers": (_I, [_I]),
+    "slaq_release_cached": (_I, []),
     "slaq_krylov_gathers": (_I, [_VP, _VP]),
 }
 
@@ -529,6 +530,11 @@ def debug_fail_alloc(nth: int):
 def debug_live_allocs() -> int:
     """slaq_debug_live_allocs: allocations the library holds."""
     return int(lib().slaq_debug_live_allocs())
+
+
+def release_cached():
+    """slaq_release_cached: free the workspace descriptors_host keeps between calls."""
+    _check(lib().slaq_release_cached())
 
 
 GATHERS_TUNED, GATHERS_LOADS, GATHERS_TMA = -1, 0, 1

@@ -169,10 +169,25 @@ def test_batched_rayleigh_ritz_and_host_entry_point():
     parts = [slaq.build_laplacian(_dev(a), _dev(b), nn) for a, b, nn in graphs[:5]]
     fails, Kb = _walk(lambda: slaq.lanczos_batched(parts, 8, 6, 1, precision=slaq.FP64))
     assert fails >= 10
-    # the host-memory entry point
+    # the host-memory entry point (with no workspace kept from an earlier
+    # call; the successful call keeps its own, which the second call reuses)
     s, d, n = _graph_edges()
     tn = synth.t_grid(8)
+    slaq.release_cached()
+    base = slaq.debug_live_allocs()
     fails, out = _walk(lambda: slaq.descriptors_host(s, d, n, tn, nv=6, s=8, seed=1))
     assert fails >= 10
+    kept = slaq.debug_live_allocs()
+    assert kept > base
     ref = slaq.descriptors_host(s, d, n, tn, nv=6, s=8, seed=1)
     np.testing.assert_array_equal(out["heat"], ref["heat"])
+    assert slaq.debug_live_allocs() == kept
+    # a call failing before it reaches the kept workspace leaves it alone
+    slaq.debug_fail_alloc(1)
+    with pytest.raises(slaq.SlaqError):
+        slaq.descriptors_host(s, d, n, tn, nv=6, s=8, seed=1)
+    slaq.debug_fail_alloc(0)
+    torch.cuda.synchronize()
+    assert slaq.debug_live_allocs() == kept
+    slaq.release_cached()
+    assert slaq.debug_live_allocs() == base

@@ -75,8 +75,9 @@ def _check(g, nv, s, seed, precision, close):
     return Kt
 
 
-# (nv, precision): 16-byte lanes per row 26 / 5 (FP32), 8 / 13 / 25 (BF16)
-# cover one, two and four rows per warp
+# (nv, precision): 16-byte lanes per row 26 / 6 / 10 (FP32 nv = 100, 20, 37)
+# and 8 / 14 / 26 (BF16 basis nv = 64, 100, 200) cover one, two and four rows
+# per warp
 @pytest.mark.parametrize("nv,precision,close", [
     (100, slaq.FP32, 1e-6), (20, slaq.FP32, 1e-6), (37, slaq.FP32, 1e-6),
     (64, slaq.FP32_BF16BASIS, 3e-5), (100, slaq.FP32_BF16BASIS, 3e-5),
