@@ -329,8 +329,8 @@ class ClockSampler:
 # R-MAT 2^20 workload from an ncu capture of step 16; it describes the
 # kernels only while csrc/lanczos.cu is byte-identical to the captured source.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1955883000 + 350987008 + 561419000 + 8566272,
-    "source_sha256": "539318e1736260c06e3e5c38220af5c6f958ea6afc09843f63491855f31327bf",
+    "bytes_per_spmm": 1952902000 + 350649856 + 560528000 + 8230912,
+    "source_sha256": "0f17b87e0ad4b9b11e62e17e971836e132b461f47bf67fb2db9ed7359be3316a",
 }
 
 
@@ -343,6 +343,12 @@ def spmm_traffic(prec):
 
 
 BASIS_BYTES = {"fp64": 8, "fp32": 4, "bf16": 2}
+
+
+def row_ld(nv, prec):
+    """Stored basis row length: nv rounded up to a whole 32-byte sector."""
+    b = BASIS_BYTES[prec]
+    return (nv * b + 31) // 32 * 32 // b
 
 
 def spmm_algorithmic_bytes(n, nnz, prec, nv=NV):
@@ -375,7 +381,8 @@ def spmm_roofline(prof_spmm_ms, runs, n, nnz, prec, nv, s, hbm, peak_src, gather
     unit_ms = prof_spmm_ms / units
     unit_bytes = spmm_algorithmic_bytes(n, nnz, prec, nv)
     achieved = unit_bytes / (unit_ms * 1e-3) / 1e9
-    gathered = nnz * nv * (8 if prec == "fp64" else (4 if prec == "fp32" else 2))
+    # rows as stored and gathered (ld columns, the probe's row width)
+    gathered = nnz * row_ld(nv, prec) * BASIS_BYTES[prec]
     out = {"bound": "hbm", "kernel": "spmm", "achieved": achieved, "peak": hbm,
            "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm,
            "unit_of_work": "one SpMM z = L u_k (light-row and split-row kernels)",
@@ -921,12 +928,13 @@ def run_ours(args):
 
     hbm, peak_src = peaks()
     gather_peak = {}
-    for nvq in (NV * 4, 64 * 2):  # the FP32 headline's rows; the 2^24 BF16 rows
-        rb = (nvq + 15) // 16 * 16
+    # the gathered row widths as stored (ld columns): the FP32 headline's and
+    # the 2^24 BF16 rows
+    for key, rb in ((NV * 4, row_ld(NV, "fp32") * 4), (64 * 2, row_ld(64, "bf16") * 2)):
         try:
-            gather_peak[nvq] = slaq.profile_gather_peak(min(rb, 512))
+            gather_peak[key] = slaq.profile_gather_peak(min(rb, 512))
         except Exception:
-            gather_peak[nvq] = None
+            gather_peak[key] = None
     alg = algorithmic_bytes(n_prime, nnz, prec)
     kernels = {}
     for name in ("spmm", "dots", "update", "reduce", "build", "ritz", "trace", "probes", "dist"):

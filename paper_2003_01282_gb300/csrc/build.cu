@@ -145,8 +145,8 @@ int exclusive_scan(const TI *in, int64_t n, int64_t *out, int64_t *total_dev, cu
 // ------------------------------------------------------------- radix sort
 constexpr int kRsThreads = 512;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsRounds = 16;                       // 32-key rounds per warp
-constexpr int kRsTile = kRsThreads * kRsRounds;     // 8192 keys per block
+constexpr int kRsRounds = 8;                        // 32-key rounds per warp
+constexpr int kRsTile = kRsThreads * kRsRounds;     // 4096 keys per block
 constexpr int kRsHistThreads = 256;
 
 __global__ void __launch_bounds__(kRsHistThreads)
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kRsHistThreads)
   counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
 }
 
-// Stable scatter of one tile.  Warp w owns keys [tile + 512 w, tile + 512 (w+1))
+// Stable scatter of one tile.  Warp w owns keys [tile + 256 w, tile + 256 (w+1))
 // and ranks them round by round (32 keys per round, lane order), so equal
 // digits keep their input order inside the warp; warps are ordered by a
 // per-digit prefix over warps.  The tile is first reordered by digit in
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kRsHistThreads)
 // store consecutive addresses of one digit's run; tiles are ordered by the
 // digit-major global scan of the per-tile counts.
 template <bool PAYLOAD>
-__global__ void __launch_bounds__(kRsThreads, 2)
+__global__ void __launch_bounds__(kRsThreads, 3)
     k_radix_scatter(const uint64_t *__restrict__ kin, const double *__restrict__ pin,
                     uint64_t *__restrict__ kout, double *__restrict__ pout, int64_t n, int shift,
                     const int64_t *__restrict__ offsets, int64_t ntiles) {
