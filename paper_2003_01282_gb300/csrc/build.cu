@@ -1239,20 +1239,21 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
 
 // --------------------------------------------------------------- unions
 namespace {
-// dst[i] = src[h][i - off[h]] + add[h] for the part h with off[h] <= i < off[h+1]
+// One block per chunk of one part: dst[dst0 + i] = src[part][src0 + i] + add
+// for i < len (coalesced copies, no search for the part).
+struct ConcatChunk {
+  int64_t src0, dst0;
+  int32_t part, len;
+};
+constexpr int kConcatChunk = 8192;
+
 template <typename T>
-__global__ void k_concat(const T *const *src, const int64_t *off, const T *add, int parts,
-                         int64_t total, T *dst) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = parts - 1;  // last part with off <= i
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (off[mid] <= i) lo = mid;
-      else hi = mid - 1;
-    }
-    dst[i] = src[lo][i - off[lo]] + (add ? add[lo] : T(0));
-  }
+__global__ void k_concat(const T *const *src, const ConcatChunk *chunks, const T *add, T *dst) {
+  const ConcatChunk c = chunks[blockIdx.x];
+  const T *s = src[c.part] + c.src0;
+  const T a = add ? add[c.part] : T(0);
+  T *d = dst + c.dst0;
+  for (int i = threadIdx.x; i < c.len; i += blockDim.x) d[i] = s[i] + a;
 }
 
 // Concatenates one array over the parts: part h contributes count[h]
@@ -1261,25 +1262,32 @@ template <typename T>
 int concat(Temps &tmp, const std::vector<const T *> &srcs, const std::vector<int64_t> &count,
            const std::vector<T> &add, T *dst, cudaStream_t st) {
   const int parts = (int)srcs.size();
-  std::vector<int64_t> off(parts + 1, 0);
-  for (int h = 0; h < parts; ++h) off[h + 1] = off[h] + count[h];
-  if (off[parts] == 0) return SLAQ_OK;
+  std::vector<ConcatChunk> chunks;
+  int64_t off = 0;
+  for (int h = 0; h < parts; ++h) {
+    for (int64_t q = 0; q < count[h]; q += kConcatChunk)
+      chunks.push_back({q, off + q, (int32_t)h, (int32_t)std::min<int64_t>(kConcatChunk, count[h] - q)});
+    off += count[h];
+  }
+  if (chunks.empty()) return SLAQ_OK;
+  if (chunks.size() > 0x7fffffffu) return set_error(SLAQ_EUNSUPPORTED, "batch too large to concatenate");
   const T **d_src = nullptr;
-  int64_t *d_off = nullptr;
+  ConcatChunk *d_chunks = nullptr;
   T *d_add = nullptr;
   SLAQ_TRY(tmp.get(&d_src, parts));
-  SLAQ_TRY(tmp.get(&d_off, parts + 1));
+  SLAQ_TRY(tmp.get(&d_chunks, (int64_t)chunks.size()));
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_src, srcs.data(), parts * sizeof(T *), cudaMemcpyHostToDevice, st));
-  SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_off, off.data(), (parts + 1) * sizeof(int64_t),
+  SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * sizeof(ConcatChunk),
                                   cudaMemcpyHostToDevice, st));
   if (!add.empty()) {
     SLAQ_TRY(tmp.get(&d_add, parts));
     SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_add, add.data(), parts * sizeof(T), cudaMemcpyHostToDevice, st));
   }
   ++tl_launches;
-  k_concat<T><<<grid_for(off[parts], 256), 256, 0, st>>>(d_src, d_off, d_add, parts, off[parts], dst);
+  k_concat<T><<<(unsigned)chunks.size(), 256, 0, st>>>(d_src, d_chunks, d_add, dst);
   SLAQ_CHECK_LAUNCH("concat");
-  return SLAQ_OK;  // copies from pageable memory are staged before they return
+  // the host vectors are staged before the copies from pageable memory return
+  return SLAQ_OK;
 }
 }  // namespace
 
@@ -1317,7 +1325,7 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   g->n_graphs = (int)G;
   g->goff.assign(1, 0);
   std::vector<int64_t> n_of(count), nnz_of(count), np1_of(count);
-  std::vector<int64_t> node_add(count), entry_add(count), input_add(count);
+  std::vector<int64_t> entry_add(count);
   std::vector<int32_t> col_add(count), graph_add(count);
   int64_t n = 0, nnz = 0, n_in = 0;
   int32_t gfirst = 0;
@@ -1326,10 +1334,8 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
     n_of[h] = a->n;
     nnz_of[h] = a->nnz;
     np1_of[h] = a->n;  // rowptr: the first n entries of each part, the end appended
-    node_add[h] = n;
     col_add[h] = (int32_t)n;
     entry_add[h] = nnz;
-    input_add[h] = n_in;
     graph_add[h] = gfirst;
     for (int q = 0; q < a->n_graphs; ++q) {
       g->goff.push_back(n + a->goff[q + 1]);
@@ -1349,15 +1355,9 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   g->trace = g->gtrace[0];
   g->bound = *std::max_element(g->gbound.begin(), g->gbound.end());
   const bool w = g->weighted;
-  SLAQ_TRY(persistent(&g->rowptr, n + 1, st));
-  SLAQ_TRY(persistent(&g->colidx, nnz, st));
-  SLAQ_TRY(persistent(&g->vals, nnz, st));
-  if (w) SLAQ_TRY(persistent(&g->vals32, nnz, st));
-  SLAQ_TRY(persistent(&g->diag, n, st));
-  SLAQ_TRY(persistent(&g->scale, n, st));
-  SLAQ_TRY(persistent(&g->diag32, n, st));
-  SLAQ_TRY(persistent(&g->scale32, n, st));
-  SLAQ_TRY(persistent(&g->old_id, n, st));
+  // The union lives inside slaq_lanczos_batched's Krylov handle and is never
+  // exported: it carries the execution copy and the per-graph scalars only,
+  // not the canonical CSR.
   SLAQ_TRY(persistent(&g->x_rowptr, n + 1, st));
   SLAQ_TRY(persistent(&g->x_colidx, nnz, st));
   if (w) SLAQ_TRY(persistent(&g->x_vals, nnz, st));
@@ -1376,29 +1376,17 @@ int union_graphs(const slaq_graph *gs, int count, cudaStream_t st, slaq_graph *o
   };
   const std::vector<double> no_d;
   const std::vector<float> no_f;
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::rowptr), np1_of, entry_add, g->rowptr, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_rowptr), np1_of, entry_add, g->x_rowptr, st));
-  SLAQ_CHECK_CUDA(cudaMemcpyAsync(g->rowptr + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st));
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(g->x_rowptr + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::colidx), nnz_of, col_add, g->colidx, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_colidx), nnz_of, col_add, g->x_colidx, st));
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::vals), nnz_of, no_d, g->vals, st));
   if (w) SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_vals), nnz_of, no_d, g->x_vals, st));
-  if (w) {
-    SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::vals32), nnz_of, no_f, g->vals32, st));
-    SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_vals32), nnz_of, no_f, g->x_vals32, st));
-  }
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::diag), n_of, no_d, g->diag, st));
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::scale), n_of, no_d, g->scale, st));
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::diag32), n_of, no_f, g->diag32, st));
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::scale32), n_of, no_f, g->scale32, st));
+  if (w) SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_vals32), nnz_of, no_f, g->x_vals32, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_diag), n_of, no_d, g->x_diag, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_scale), n_of, no_d, g->x_scale, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_diag32), n_of, no_f, g->x_diag32, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_scale32), n_of, no_f, g->x_scale32, st));
-  // canonical ids live in the union's input numbering, execution ids stay
-  // local to their graph (the probe signs), graph numbers are shifted
-  SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::old_id), n_of, input_add, g->old_id, st));
+  // execution ids stay local to their graph (the probe signs), graph numbers
+  // are shifted
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_old_id), n_of, std::vector<int64_t>(), g->x_old_id, st));
   SLAQ_TRY(concat(tmp, ptrs(&slaq_graph_s::x_graph), n_of, graph_add, g->x_graph, st));
   {
