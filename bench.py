@@ -65,6 +65,7 @@ WORKLOAD = ("R-MAT scale 20 (2^20 nodes, 16Mi unique undirected edges, a,b,c,d=.
             "s=20 Lanczos steps, full CGS reorthogonalization; heat + wave traces on 256 "
             "log-spaced t in [1e-2,1e2] + VNGE")
 CPU_PROBES_PER_WORKER = 2   # probes per pool worker in the CPU-oracle sample
+CPU_SBM_STRIDE = 10         # every 10th graph of the SBM batch in the CPU-oracle sample
 # batched workload: 5000 SBM graphs, nv = 20, s = 15, heat traces at 256 t
 SBM_GRAPHS, SBM_NV, SBM_S, SBM_SEED = 5000, 20, 15, 3
 SBM_WORKLOAD = ("5000 stochastic-block-model graphs (sizes lognormal, median 300, clipped to "
@@ -165,6 +166,23 @@ def _pool_probes(ids):
     return list(ids), heat, wr, wi, vn
 
 
+def _pool_sbm(gids):
+    """The oracle on graphs `gids` of the SBM batch: SLQ (nv, s of the batch
+    leg) and the heat trace; seconds spent in them (generation and the CSR
+    build excluded, as the GPU leg times prebuilt handles)."""
+    from oracle import descriptors as od
+    from oracle.laplacian import build_laplacian
+    t, sec = _WORKER["t"], 0.0
+    for g in gids:
+        s_, d_, n = synth.sbm_batch_graph(int(g), SBM_SEED)
+        lap = build_laplacian(s_, d_, n, drop_isolated=True)
+        t0 = time.perf_counter()
+        runs = od.slq_runs(lap, SBM_S, SBM_NV, PROBE_SEED, graph=int(g))
+        od.heat_trace(runs, lap.n, t)
+        sec += time.perf_counter() - t0
+    return sec
+
+
 class OraclePool:
     """The oracle's Laplacian of the workload and a spawn pool of workers."""
 
@@ -209,6 +227,13 @@ class OraclePool:
         out = self.pool.map_async(_pool_probes, [c.tolist() for c in chunks], chunksize=1).get(timeout=1800)
         return time.perf_counter() - t0, out
 
+    def sbm_graphs(self, gids):
+        """Graphs per second of the SBM-batch sample `gids` over the pool:
+        the graphs over the longest worker's SLQ time."""
+        chunks = [c.tolist() for c in np.array_split(np.asarray(gids), min(self.workers, len(gids)))]
+        secs = self.pool.map_async(_pool_sbm, chunks, chunksize=1).get(timeout=1800)
+        return len(gids) / max(secs), max(secs)
+
     def close(self):
         self.pool.close()
         self.pool.join()
@@ -227,11 +252,33 @@ def cpu_baseline(src, dst, n):
         sec, _ = pool.probes(range(nprobe))
         total = pool.build_s + sec
         nnz = pool.lap.nnz
-        return {"value": nnz * nprobe * S / total, "unit": UNIT, "cores": pool.workers,
-                "kind": "oracle", **pool.info,
-                "sample": f"CSR build of the full graph on one core ({pool.build_s:.1f} s) + {nprobe} of "
-                          f"{NV} probes x {S} Lanczos steps with heat/wave/VNGE quadrature over a "
-                          f"{pool.workers}-process pool ({sec:.1f} s)"}
+        out = {"value": nnz * nprobe * S / total, "unit": UNIT, "cores": pool.workers,
+               "kind": "oracle", **pool.info,
+               "sample": f"CSR build of the full graph on one core ({pool.build_s:.1f} s) + {nprobe} of "
+                         f"{NV} probes x {S} Lanczos steps with heat/wave/VNGE quadrature over a "
+                         f"{pool.workers}-process pool ({sec:.1f} s)"}
+        # the other configurations: the small graph in full on one core, and a
+        # sample of the SBM batch over the pool
+        from oracle import descriptors as od
+        from oracle.laplacian import build_laplacian
+        s_, d_, n1 = synth.barabasi_albert(2000, 4, seed=0)
+        lap1 = build_laplacian(s_, d_, n1)
+        t_np = synth.t_grid(NT)
+        t0 = time.perf_counter()
+        runs = od.slq_runs(lap1, 15, 10, 1)
+        od.heat_trace(runs, lap1.n, t_np)
+        od.wave_trace(runs, lap1.n, t_np)
+        od.vnge(runs, lap1.n, lap1.trace)
+        out["ba2000"] = {"ms_per_run": (time.perf_counter() - t0) * 1e3, "cores": 1,
+                         "sample": "BA n=2000 m=4 seed 0, normalized; nv=10, s=15 with "
+                                   "heat/wave/VNGE quadrature, in full, one core"}
+        gids = list(range(0, SBM_GRAPHS, CPU_SBM_STRIDE))
+        gps, longest = pool.sbm_graphs(gids)
+        out["sbm_batch"] = {"value": gps, "unit": "graphs/s", "cores": pool.workers,
+                            "sample": f"every {CPU_SBM_STRIDE}th graph of the batch ({len(gids)} graphs), "
+                                      f"nv={SBM_NV}, s={SBM_S}, heat trace at {NT} t; longest worker "
+                                      f"{longest:.1f} s (generation and CSR build excluded)"}
+        return out
     finally:
         pool.close()
 

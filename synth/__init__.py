@@ -329,17 +329,21 @@ def sbm_batch(n_graphs: int, seed: int = 3, median: float = 300.0,
     """Batch of SBM graphs: node counts lognormal(ln median, sigma) clipped to
     [lo, hi]; 2-6 blocks as equal as possible; p_in ~ U[0.05, 0.3];
     p_out = p_in / U[5, 20].  Graph g uses seed ``seed + g``."""
-    out = []
-    for g in range(n_graphs):
-        rng = np.random.default_rng(seed + g)
-        n = int(np.clip(round(rng.lognormal(np.log(median), sigma)), lo, hi))
-        nb = int(rng.integers(2, 7))
-        base, rem = divmod(n, nb)
-        sizes = [base + (1 if k < rem else 0) for k in range(nb)]
-        p_in = float(rng.uniform(0.05, 0.3))
-        p_out = p_in / float(rng.uniform(5.0, 20.0))
-        out.append(sbm(sizes, p_in, p_out, seed=seed + g + 1_000_000))
-    return out
+    return [sbm_batch_graph(g, seed, median, sigma, lo, hi) for g in range(n_graphs)]
+
+
+def sbm_batch_graph(g: int, seed: int = 3, median: float = 300.0, sigma: float = 1.0,
+                    lo: int = 10, hi: int = 5000):
+    """Graph g of ``sbm_batch(..., seed, ...)`` on its own (it depends on
+    seed + g only)."""
+    rng = np.random.default_rng(seed + g)
+    n = int(np.clip(round(rng.lognormal(np.log(median), sigma)), lo, hi))
+    nb = int(rng.integers(2, 7))
+    base, rem = divmod(n, nb)
+    sizes = [base + (1 if k < rem else 0) for k in range(nb)]
+    p_in = float(rng.uniform(0.05, 0.3))
+    p_out = p_in / float(rng.uniform(5.0, 20.0))
+    return sbm(sizes, p_in, p_out, seed=seed + g + 1_000_000)
 
 
 def rewire(src, dst, n: int, frac: float = 1e-3, seed: int = 0):
