@@ -201,8 +201,9 @@ int slaq_lanczos_probes(slaq_graph g, int nv, int probe0, int s, uint64_t seed, 
  * Lanczos steps, the Gauss rules) into a CUDA graph; every rerun then copies
  * the seed to the device and launches that graph, so a run costs one launch
  * on the host instead of about 5 s + 10.  The graph handle of the last call
- * must still be alive (a batched call's concatenation is owned by k).  Any
- * slaq_lanczos call on k discards the captured graph.  Not available with
+ * must still be alive (a batched call's concatenation of two or more
+ * handles is owned by k).  Any slaq_lanczos call on k discards the captured
+ * graph.  Not available with
  * partial reorthogonalization (its steps are decided on the host):
  * SLAQ_EUNSUPPORTED.  Synchronizes `stream`; SLAQ_ENUMERIC as for
  * slaq_lanczos. */
@@ -211,7 +212,8 @@ int slaq_lanczos_rerun(slaq_krylov k, uint64_t seed, void *stream);
 /* slaq_lanczos for a batch of separately built graphs gs[0..count): the
  * graphs (each a single graph or itself a batch) are concatenated on the
  * device into one block-diagonal Laplacian owned by the Krylov handle, and
- * all of them run through the same launches.  Graph g of the concatenation
+ * all of them run through the same launches (one handle, count = 1, runs as
+ * it is, without a copy).  Graph g of the concatenation
  * (in order, sub-graphs of batch handles expanded) gets probe graph field
  * graph_id + g, so its results equal slaq_lanczos(gs[g], ..., graph_id + g)
  * up to rounding order.  All graphs must share the Laplacian kind and be all
@@ -220,12 +222,16 @@ int slaq_lanczos_rerun(slaq_krylov k, uint64_t seed, void *stream);
  * text file: if it holds a line for this workload class (precision, nv, s,
  * reorth_passes, log2 of n', of nnz/n' and of the graph count, SM count) the
  * launch shapes on it are used (line format "<class> | spmm_threads
- * update_threads dots_threads slice_bytes spmm_align"); if not, the call first times candidate
+ * update_threads dots_threads slice_bytes spmm_align spmm_tma", the last
+ * field optional and 1 for the TMA gathers of slaq_set_spmm_gathers); if
+ * not, the call first times candidate
  * shapes on this batch (coordinate descent, about a dozen full runs), keeps
  * the fastest and adds its line (the file is rewritten through a temporary
  * beside it).  An unreadable or unwritable file gives SLAQ_EINVAL.
- * The inputs gs may be destroyed once the call returns.  Synchronizes
- * `stream`; other arguments and errors as for slaq_lanczos. */
+ * The inputs gs may be destroyed once the call returns; only a rerun
+ * (slaq_lanczos_rerun) of a call with one input needs that input alive, as
+ * after slaq_lanczos.  Synchronizes `stream`; other arguments and errors as
+ * for slaq_lanczos. */
 int slaq_lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t seed,
                          int graph_id, int precision, int reorth_passes,
                          const char *tune_cache, void *stream, slaq_krylov *inout);
@@ -503,6 +509,14 @@ int slaq_profile_gather_peak(int row_bytes, double *tbps_host);
  * slaq_lanczos_rerun keeps its run's path).  SLAQ_EINVAL for a mode outside
  * [-1, 1]. */
 int slaq_set_spmm_gathers(int mode);
+
+/* Test hook, off by default: on != 0 makes every warp of the TMA light-row
+ * SpMM treat its first wait on a stage as one that ran out of polls (the
+ * copies it issued still land: the kernel drains them before it returns), so
+ * that a run on the TMA path fails with SLAQ_ETIMEOUT and leaves its handle
+ * not ready.  Exercises the bounded-wait error path without faulting the
+ * device; on == 0 restores normal waits.  Process-wide. */
+int slaq_debug_tma_giveup(int on);
 
 /* *tma_host = 1 if the light rows of k's last run were gathered through
  * TMA (slaq_set_spmm_gathers), 0 if through loads.  Host-side; no GPU work. */

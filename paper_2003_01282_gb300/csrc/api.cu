@@ -708,6 +708,8 @@ int slaq_pool_probes_host(const double *values, int nprobe, int len, double *mea
 
 int slaq_set_spmm_gathers(int mode) { return set_spmm_gathers(mode); }
 
+int slaq_debug_tma_giveup(int on) { return debug_tma_giveup(on); }
+
 int slaq_tridiag_gauss_host(const double *alpha, const double *beta, int m, double *theta,
                             double *tau2) {
   if (m < 1 || m > 4096 || !alpha || !theta || !tau2 || (m > 1 && !beta))

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <vector>
@@ -288,6 +289,8 @@ void krylov_free(slaq_krylov k);
 // memory) leaves the handle destroyable and reusable but not readable
 int krylov_ready(slaq_krylov k);
 int set_spmm_gathers(int mode);
+extern std::atomic<int> g_tma_giveup;  // test hook: TMA waits give up (slaq_debug_tma_giveup)
+int debug_tma_giveup(int on);
 int probes(slaq_graph g, int nv, uint64_t seed, int graph_id, double *out, cudaStream_t st);
 int full_steps(slaq_krylov k, int32_t *out, cudaStream_t st);
 int lanczos_rerun(slaq_krylov k, uint64_t seed, cudaStream_t st);

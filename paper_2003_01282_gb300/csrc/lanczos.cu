@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(32 * kTmaWarps, G == 4 ? 3 : 2)
                const typename Form<P>::TW *__restrict__ scale,
                const typename Form<P>::TB *__restrict__ U, typename Form<P>::TW *__restrict__ Z,
                int ld, int64_t heavy_degree, const int64_t *__restrict__ task_row, int64_t ntasks,
-               int32_t *__restrict__ err) {
+               int32_t *__restrict__ err, int giveup) {
   using TW = typename Form<P>::TW;
   using TB = typename Form<P>::TB;
   constexpr int VE = Form<P>::VE;
@@ -850,7 +850,9 @@ __global__ void __launch_bounds__(32 * kTmaWarps, G == 4 ? 3 : 2)
         break;
       }
       const int slot = (int)(cc % NS);
-      if (!mbar_wait(smem_u32(bar + slot), (cc / NS) & 1u)) {
+      // giveup (a test hook): the warp's first wait gives up at once, as a
+      // wait that ran out of polls would
+      if ((giveup && cc == 0) || !mbar_wait(smem_u32(bar + slot), (cc / NS) & 1u)) {
         ok = false;
         break;
       }
@@ -921,6 +923,17 @@ __global__ void __launch_bounds__(32 * kTmaWarps, G == 4 ? 3 : 2)
       if (!mbar_wait(smem_u32(bar + cc % NS), (cc / NS) & 1u)) break;
   }
 }
+
+}  // namespace
+
+std::atomic<int> g_tma_giveup{0};
+
+int debug_tma_giveup(int on) {
+  g_tma_giveup.store(on ? 1 : 0);
+  return SLAQ_OK;
+}
+
+namespace {
 
 // ------------------------------------------------------ compensated sums
 // Per-thread running sums of chunk sums.  FP64 form: plain FP64.  FP32
@@ -1924,7 +1937,7 @@ int launch_tma(slaq_graph gr, slaq_krylov K, int row0, const typename Form<P>::T
   kern<<<(unsigned)blocks, 32 * kTmaWarps, smem, st>>>(K->tma_map, row0, gr->x_rowptr,
                                                       gr->x_colidx, vals, diag, scale, Uk, Z, K->ld,
                                                       gr->heavy_degree, K->tma_task, K->tma_ntasks,
-                                                      K->status + 1);
+                                                      K->status + 1, g_tma_giveup.load());
   return SLAQ_OK;
 }
 

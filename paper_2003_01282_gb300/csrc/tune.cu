@@ -148,8 +148,19 @@ int lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t see
                     int precision, int reorth, const char *tune_cache, cudaStream_t st,
                     slaq_krylov *inout) {
   if (!inout) return set_error(SLAQ_EINVAL, "NULL output handle");
+  // one input handle (a single graph or a batch) runs as it is; a list is
+  // concatenated into a union the Krylov handle owns
   slaq_graph u = nullptr;
-  SLAQ_TRY(union_graphs(gs, count, st, &u));
+  slaq_graph input = nullptr;
+  if (gs && count == 1) {
+    int dev = 0;
+    SLAQ_CHECK_CUDA(cudaGetDevice(&dev));
+    if (!gs[0]) return set_error(SLAQ_EINVAL, "graph 0 is NULL");
+    if (gs[0]->device != dev) return set_error(SLAQ_EINVAL, "graph 0 lives on another device");
+    input = gs[0];
+  } else {
+    SLAQ_TRY(union_graphs(gs, count, st, &u));
+  }
   struct Own {
     slaq_graph *u;
     cudaStream_t st;
@@ -157,23 +168,25 @@ int lanczos_batched(const slaq_graph *gs, int count, int nv, int s, uint64_t see
       if (*u) graph_free(*u, st);
     }
   } own{&u, st};
+  slaq_graph g = input ? input : u;
   slaq_tuning tune;
   if (tune_cache) {
     std::map<std::string, slaq_tuning> all;
     SLAQ_TRY(read_cache(tune_cache, &all));
-    const std::string key = tune_key(u, nv, s, precision, reorth);
+    const std::string key = tune_key(g, nv, s, precision, reorth);
     auto it = all.find(key);
     if (it != all.end()) {
       tune = it->second;
     } else {
-      SLAQ_TRY(autotune(u, nv, s, seed, graph_id, precision, reorth, st, inout, &tune));
+      SLAQ_TRY(autotune(g, nv, s, seed, graph_id, precision, reorth, st, inout, &tune));
       all[key] = tune;
       SLAQ_TRY(write_cache(tune_cache, all));
     }
   }
-  SLAQ_TRY(run_lanczos(u, nv, s, seed, graph_id, precision, reorth, st, inout, &tune));
-  // the Krylov handle keeps the union alive until it is destroyed or reused
-  graph_free((*inout)->owned, st);
+  SLAQ_TRY(run_lanczos(g, nv, s, seed, graph_id, precision, reorth, st, inout, &tune));
+  // the Krylov handle keeps a union alive until it is destroyed or reused (a
+  // single input stays the caller's, as with slaq_lanczos)
+  if ((*inout)->owned != u) graph_free((*inout)->owned, st);
   (*inout)->owned = u;
   u = nullptr;
   return SLAQ_OK;

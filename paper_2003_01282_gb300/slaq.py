@@ -80,6 +80,7 @@ _SIGNATURES = {
     "slaq_set_spmm_gathers": (_I, [_I]),
     "slaq_release_cached": (_I, []),
     "slaq_krylov_gathers": (_I, [_VP, _VP]),
+    "slaq_debug_tma_giveup": (_I, [_I]),
 }
 
 PROF_NAMES = ["build", "probes", "spmm", "dots", "update", "reduce", "ritz", "trace", "dist"]
@@ -544,6 +545,11 @@ def set_spmm_gathers(mode: int):
     """slaq_set_spmm_gathers: light-row gathers of later runs through TMA
     (GATHERS_TMA), loads (GATHERS_LOADS) or the run's tuning (GATHERS_TUNED)."""
     _check(lib().slaq_set_spmm_gathers(int(mode)))
+
+
+def debug_tma_giveup(on: bool):
+    """slaq_debug_tma_giveup: TMA stage waits give up at once (test hook)."""
+    _check(lib().slaq_debug_tma_giveup(1 if on else 0))
 
 
 def krylov_gathers(k) -> int:

@@ -96,3 +96,22 @@ def test_rerun_after_reuse_and_errors():
     with pytest.raises(slaq.SlaqError) as ei:
         slaq.lanczos_rerun(K, 2)
     assert ei.value.status == 1
+
+
+def test_batched_single_input_runs_in_place():
+    """slaq_lanczos_batched with one handle runs on it without a copy: equal
+    to slaq_lanczos on that handle bit for bit, replayable while the input
+    lives, refused after it is destroyed."""
+    graphs = synth.sbm_batch(12, seed=4)
+    gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
+    Kb = slaq.lanczos_batched([gb], 6, 10, 3, precision=slaq.FP32)
+    _same(Kb, slaq.lanczos(gb, 6, 10, 3, precision=slaq.FP32))
+    slaq.lanczos_rerun(Kb, 5)
+    _same(Kb, slaq.lanczos(gb, 6, 10, 5, precision=slaq.FP32))
+    gb.close()
+    with pytest.raises(slaq.SlaqError) as ei:
+        slaq.lanczos_rerun(Kb, 6)
+    assert ei.value.status == 1
+    # the traces of the completed run stay readable
+    t = torch.as_tensor(synth.t_grid(8), device="cuda")
+    assert torch.isfinite(slaq.trace_heat(Kb, t)[0]).all()

@@ -152,3 +152,31 @@ def _run_mode(g, nv, precision):
     slaq.set_spmm_gathers(slaq.GATHERS_TMA)
     K = slaq.lanczos(g, nv, 6, 1, precision=precision)
     return slaq.krylov_gathers(K)
+
+
+def test_tma_wait_giveup_reports_timeout():
+    """The bounded-wait error path (slaq_debug_tma_giveup): every warp's first
+    stage wait gives up, the kernel drains its copies and flags the run, which
+    returns SLAQ_ETIMEOUT and leaves the handle not ready; the next run on the
+    handle is bit-equal to the one before; the load path ignores the hook."""
+    g = _graph(synth.rmat(12, 16 << 12, seed=9))
+    t = _dev(synth.t_grid(16), torch.float64)
+    K = _run(g, 32, 8, 1, slaq.FP32, slaq.GATHERS_TMA)
+    want = slaq.trace_heat(K, t)[0].clone()
+    slaq.debug_tma_giveup(True)
+    try:
+        with pytest.raises(slaq.SlaqError) as ei:
+            slaq.lanczos(g, 32, 8, 1, precision=slaq.FP32, reuse=K)
+        assert ei.value.status == 5  # SLAQ_ETIMEOUT
+        with pytest.raises(slaq.SlaqError) as ei:
+            slaq.trace_heat(K, t)
+        assert ei.value.status == 1
+        slaq.set_spmm_gathers(slaq.GATHERS_LOADS)
+        Kl = slaq.lanczos(g, 32, 8, 1, precision=slaq.FP32)
+        assert slaq.krylov_gathers(Kl) == 0
+    finally:
+        slaq.debug_tma_giveup(False)
+    K2 = _run(g, 32, 8, 1, slaq.FP32, slaq.GATHERS_TMA)
+    assert torch.equal(slaq.trace_heat(K2, t)[0], want)
+    K3 = slaq.lanczos(g, 32, 8, 1, precision=slaq.FP32, reuse=K)
+    assert torch.equal(slaq.trace_heat(K3, t)[0], want)
