@@ -376,8 +376,8 @@ class ClockSampler:
 # R-MAT 2^20 workload from an ncu capture of step 16; it describes the
 # kernels only while csrc/lanczos.cu is byte-identical to the captured source.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1952902000 + 350649856 + 560528000 + 8230912,
-    "source_sha256": "0f17b87e0ad4b9b11e62e17e971836e132b461f47bf67fb2db9ed7359be3316a",
+    "bytes_per_spmm": 1956087000 + 350586368 + 561745000 + 8384000,
+    "source_sha256": "c3d453703345c034b098d90cce3a8aee45c5c6c26e98b53dbd6a0ba651c1e798",
 }
 
 

@@ -343,16 +343,19 @@ __device__ void mean_se(const double *g, int nv, double *mean_out, double *se_ou
 // FP64 for cos / sin), the function is evaluated in FP32; used by the FP32
 // forms, whose Ritz values carry FP32-level errors anyway.  FP64 is scarce on
 // this chip and these evaluations dominate batched quadratures.
+template <int FUN>
+__device__ __forceinline__ float fval32(double t, double th) {
+  const double x = t * th;
+  if (FUN == 0) return expf((float)(-x));
+  const double two_pi = 6.283185307179586, inv_two_pi = 0.15915494309189535;
+  const double r = x - two_pi * rint(x * inv_two_pi);
+  if (FUN == 1) return cosf((float)r);
+  return -sinf((float)r);
+}
 template <int FUN, bool F32>
 __device__ __forceinline__ double fval(double t, double th) {
+  if (F32) return (double)fval32<FUN>(t, th);
   const double x = t * th;
-  if (F32) {
-    if (FUN == 0) return (double)expf((float)(-x));
-    const double two_pi = 6.283185307179586, inv_two_pi = 0.15915494309189535;
-    const double r = x - two_pi * rint(x * inv_two_pi);
-    if (FUN == 1) return (double)cosf((float)r);
-    return -(double)sinf((float)r);
-  }
   if (FUN == 0) return exp(-x);
   if (FUN == 1) return cos(x);
   return -sin(x);
@@ -384,7 +387,16 @@ __global__ void __launch_bounds__(kTT * kPG)
       const int64_t q = (int64_t)gr * nv + p;
       double acc = 0.0;
       const int m = mm[q];
-      for (int k = 0; k < m; ++k) acc += tau2[q * s + k] * fval<FUN, F32>(tv, theta[q * s + k]);
+      if (F32) {
+        // FP32 values summed in FP32 (m <= 64 terms of weights summing to 1):
+        // the sum's rounding is of the size of the values' own
+        float af = 0.0f;
+        for (int k = 0; k < m; ++k)
+          af = fmaf((float)tau2[q * s + k], fval32<FUN>(tv, theta[q * s + k]), af);
+        acc = (double)af;
+      } else {
+        for (int k = 0; k < m; ++k) acc += tau2[q * s + k] * fval<FUN, false>(tv, theta[q * s + k]);
+      }
       const double x = n * acc;
       if (per_probe) per_probe[q * nt + ti] = x;
       ++cnt;
