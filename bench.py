@@ -376,8 +376,8 @@ class ClockSampler:
 # R-MAT 2^20 workload from an ncu capture of step 16; it describes the
 # kernels only while csrc/lanczos.cu is byte-identical to the captured source.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1956087000 + 350586368 + 561745000 + 8384000,
-    "source_sha256": "c3d453703345c034b098d90cce3a8aee45c5c6c26e98b53dbd6a0ba651c1e798",
+    "bytes_per_spmm": 1956395000 + 350863872 + 561344000 + 8396288,
+    "source_sha256": "8418a32ea6686eb7f759a6df2a314e77b04a66c6d95184af36e46fb04d248806",
 }
 
 
