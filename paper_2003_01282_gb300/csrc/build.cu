@@ -351,19 +351,28 @@ __device__ __forceinline__ int find_segment(const int64_t *off, int G, int64_t x
   return lo;
 }
 
-__global__ void k_union_ids(const int32_t *src, const int32_t *dst, const double *w, int64_t m,
-                            const int64_t *edge_off, const int64_t *node_off, int G, int32_t *usrc,
+// A batch's edges by chunks of one graph: edges [e0, e0 + len) of graph g.
+struct EdgeChunk {
+  int64_t e0;
+  int32_t g, len;
+};
+constexpr int kEdgeChunk = 8192;
+
+// One block per chunk (the graph of its edges is known, no search): local
+// ids checked against the graph's node count and shifted to union ids.
+__global__ void k_union_ids(const int32_t *src, const int32_t *dst, const double *w,
+                            const EdgeChunk *chunks, const int64_t *node_off, int32_t *usrc,
                             int32_t *udst, int32_t *bad, unsigned long long *loops) {
+  const EdgeChunk c = chunks[blockIdx.x];
+  const int64_t base = node_off[c.g], ng = node_off[c.g + 1] - base;
   unsigned cnt = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int g = find_segment(edge_off, G, e);
-    const int64_t ng = node_off[g + 1] - node_off[g];
+  for (int i = threadIdx.x; i < c.len; i += blockDim.x) {
+    const int64_t e = c.e0 + i;
     const int32_t a = src[e], b = dst[e];
     if (a < 0 || b < 0 || a >= ng || b >= ng) atomicOr(bad, 1);
     if (w && !(w[e] > 0.0)) atomicOr(bad, 2);
-    usrc[e] = (int32_t)(node_off[g] + (a < 0 ? 0 : a));
-    udst[e] = (int32_t)(node_off[g] + (b < 0 ? 0 : b));
+    usrc[e] = (int32_t)(base + (a < 0 ? 0 : a));
+    udst[e] = (int32_t)(base + (b < 0 ? 0 : b));
     cnt += a == b;
   }
   add_loops(cnt, loops);
@@ -925,16 +934,22 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
     SLAQ_CHECK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
     SLAQ_CHECK_CUDA(cudaMemsetAsync(loops, 0, sizeof(unsigned long long), st));
     if (batch) {
-      int64_t *d_edge_off = nullptr;
+      std::vector<EdgeChunk> chunks;
+      for (int g = 0; g < G; ++g)
+        for (int64_t e = edge_off_host[g]; e < edge_off_host[g + 1]; e += kEdgeChunk)
+          chunks.push_back({e, (int32_t)g,
+                            (int32_t)std::min<int64_t>(kEdgeChunk, edge_off_host[g + 1] - e)});
+      EdgeChunk *d_chunks = nullptr;
       int32_t *usrc = nullptr, *udst = nullptr;
-      SLAQ_TRY(tmp.get(&d_edge_off, G + 1));
+      SLAQ_TRY(tmp.get(&d_chunks, std::max<int64_t>(1, (int64_t)chunks.size())));
       SLAQ_TRY(tmp.get(&usrc, m));
       SLAQ_TRY(tmp.get(&udst, m));
-      SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_edge_off, edge_off_host, (G + 1) * sizeof(int64_t),
+      // pageable source: staged before the call returns
+      SLAQ_CHECK_CUDA(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * sizeof(EdgeChunk),
                                       cudaMemcpyHostToDevice, st));
       ++tl_launches;
-      k_union_ids<<<grid_for(m, 256), 256, 0, st>>>(src, dst, weights, m, d_edge_off, d_node_off, G,
-                                                    usrc, udst, bad, loops);
+      k_union_ids<<<(unsigned)chunks.size(), 256, 0, st>>>(src, dst, weights, d_chunks, d_node_off,
+                                                          usrc, udst, bad, loops);
       src = usrc;
       dst = udst;  // csrc / cdst keep the local ids
     } else {
