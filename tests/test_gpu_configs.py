@@ -22,6 +22,13 @@
   the reduced forms' heat and VNGE distances are within relative 1e-3 of
   FP64's, wave distances within 1e-2 (the BF16 basis over the t <= 10 it
   serves, as above).
+* The 5000-graph SBM batch at full size (sizes lognormal, median 300, seed
+  3; isolated nodes dropped; nv = 20, s = 15, probe seed 1) through
+  slaq_lanczos_batched on the batch handle, as the bench runs it: FP64
+  coefficients and heat traces of sampled graphs (the largest, the smallest
+  and every 500th) equal the oracle's for that graph alone within relative
+  1e-10; every graph's FP32 heat trace within 1e-4 of FP64 and its VNGE
+  within 1e-3 (absolute where the VNGE is below 1).
 """
 import numpy as np
 import pytest
@@ -162,3 +169,36 @@ def test_graph_pair_distances():
         hcol, wcol = (0, 1) if prec == slaq.FP32 else (4, 3)
         assert _rel(dist[prec][:, [hcol, 2]], dist[slaq.FP64][:, [hcol, 2]]) < 1e-3, prec
         assert _rel(dist[prec][:, wcol], dist[slaq.FP64][:, wcol]) < 1e-2, prec
+
+
+def test_sbm5000_batch_full_size_sampled_graphs():
+    graphs = synth.sbm_batch(5000, seed=3)
+    gb = slaq.build_laplacian_batch(graphs, flags=slaq.DROP_ISOLATED)
+    nv, s, seed = 20, 15, 1
+    t_np = synth.t_grid(64)
+    t = torch.as_tensor(t_np, device="cuda", dtype=torch.float64)
+    K64 = slaq.lanczos_batched([gb], nv, s, seed, precision=slaq.FP64)
+    K32 = slaq.lanczos_batched([gb], nv, s, seed, precision=slaq.FP32)
+    h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
+    h32 = slaq.trace_heat(K32, t)[0].cpu().numpy()
+    v64 = slaq.trace_vnge(K64)[0].cpu().numpy()
+    v32 = slaq.trace_vnge(K32)[0].cpu().numpy()
+    assert h64.shape == (5000, 64)
+    # every graph: the FP32 form against FP64
+    assert _rel(h32, h64) < 1e-4
+    # VNGE: relative 1e-3, absolute below 1 (a graph left with one edge has
+    # VNGE exactly 0, where a relative bar means nothing)
+    assert np.all(np.abs(v32 - v64) <= 1e-3 * np.maximum(np.abs(v64), 1.0))
+    # sampled graphs one by one against the oracle
+    alpha, beta, m = (x.cpu().numpy() for x in slaq.krylov_export(K64))
+    sizes = np.array([g[2] for g in graphs])
+    sample = sorted({int(sizes.argmax()), int(sizes.argmin()), *range(0, 5000, 500)})
+    for g in sample:
+        src, dst, n = graphs[g]
+        lap = build_laplacian(src, dst, n, drop_isolated=True)
+        runs = odesc.slq_runs(lap, s, nv, seed, graph=g)
+        for p, r in enumerate(runs):
+            assert m[g, p] == r.m
+            np.testing.assert_allclose(alpha[g, p, :r.m], r.alpha, rtol=1e-10, atol=1e-12)
+        want, _ = odesc.heat_trace(runs, lap.n, t_np)
+        assert _rel(h64[g], want) < 1e-10, g
