@@ -1,7 +1,10 @@
 """The web-scale and graph-pair workloads as parity cases, through the C ABI.
 
 * R-MAT 2^24 with 16 * 2^24 unique undirected edges (a, b, c, d = .57, .19,
-  .19, .05), isolated nodes dropped, normalized Laplacian, nv = 64, s = 20:
+  .19, .05), isolated nodes dropped, normalized Laplacian, nv = 64, s = 20.
+  Too large for the oracle, the FP64 run is held to invariants that hold at
+  any size (the Gauss rules' first two moments against q^T L q and ||L q||^2
+  of a direct sparse product, h(0) = n'), and
   the BF16-basis form (and the FP32 form) against the FP64 form on the same
   probes.  The FP64 run takes the first 32 probes, whose basis alone is
   46 GB (nv = 64 would double it); every probe's Lanczos run is independent
@@ -30,6 +33,8 @@
   1e-10; every graph's FP32 heat trace within 1e-4 of FP64 and its VNGE
   within 1e-3 (absolute where the VNGE is below 1).
 """
+import warnings
+
 import numpy as np
 import pytest
 
@@ -71,6 +76,7 @@ def test_rmat24_reduced_forms_vs_fp64():
     v64 = slaq.trace_vnge(K64)[0].item()
     (w64, _), _ = slaq.trace_wave(K64, t)
     w64 = w64.cpu().numpy()
+    _check_moments(g, K64, 32, seed=2)
     del K64
     t_np = synth.t_grid()
     lo = t_np <= 10.0
@@ -92,6 +98,35 @@ def test_rmat24_reduced_forms_vs_fp64():
         assert np.max(werr) < 1e-4 * np.max(np.abs(w64)), prec
         assert abs(slaq.trace_vnge(K)[0].item() - v64) / v64 < 1e-3, prec
         del K
+
+
+def _check_moments(g, K, nv, seed):
+    """Invariants of the FP64 run that hold at any size: the Gauss rule of
+    probe q is exact for polynomials up to degree 2m - 1, so its first two
+    moments equal q^T L q / q^T q and ||L q||^2 / q^T q, computed here from
+    the exported CSR and probes by one FP64 sparse product (cuSPARSE through
+    torch), independently of the Lanczos kernels; and h(0) = n' (the
+    weights of every probe sum to one)."""
+    ex = slaq.graph_export(g)
+    n = g.info["n"]
+    with warnings.catch_warnings():  # torch marks sparse CSR tensors as beta
+        warnings.simplefilter("ignore", UserWarning)
+        A = torch.sparse_csr_tensor(ex["rowptr"], ex["colidx"].to(torch.int64), ex["vals"],
+                                    size=(n, n))
+    q = slaq.probes(g, nv, seed)
+    y = torch.matmul(A, q) + ex["diag"][:n, None] * q
+    del A, ex
+    qq = (q * q).sum(0)
+    m1 = ((q * y).sum(0) / qq).cpu().numpy()
+    m2 = ((y * y).sum(0) / qq).cpu().numpy()
+    del q, y
+    theta, tau2 = slaq.ritz_export(K)
+    g1 = (tau2 * theta).sum(1).cpu().numpy()
+    g2 = (tau2 * theta * theta).sum(1).cpu().numpy()
+    assert np.max(np.abs(g1 - m1) / np.abs(m1)) < 1e-10
+    assert np.max(np.abs(g2 - m2) / np.abs(m2)) < 1e-10
+    h0 = slaq.trace_heat(K, torch.zeros(1, dtype=torch.float64, device="cuda"))[0].item()
+    assert abs(h0 - n) <= 1e-12 * n
 
 
 def _pairs():
