@@ -264,14 +264,18 @@ def cpu_baseline(src, dst, n):
         s_, d_, n1 = synth.barabasi_albert(2000, 4, seed=0)
         lap1 = build_laplacian(s_, d_, n1)
         t_np = synth.t_grid(NT)
-        t0 = time.perf_counter()
-        runs = od.slq_runs(lap1, 15, 10, 1)
-        od.heat_trace(runs, lap1.n, t_np)
-        od.wave_trace(runs, lap1.n, t_np)
-        od.vnge(runs, lap1.n, lap1.trace)
-        out["ba2000"] = {"ms_per_run": (time.perf_counter() - t0) * 1e3, "cores": 1,
+        best = None
+        for _ in range(3):  # the best of three: the run takes tens of ms
+            t0 = time.perf_counter()
+            runs = od.slq_runs(lap1, 15, 10, 1)
+            od.heat_trace(runs, lap1.n, t_np)
+            od.wave_trace(runs, lap1.n, t_np)
+            od.vnge(runs, lap1.n, lap1.trace)
+            sec = time.perf_counter() - t0
+            best = sec if best is None else min(best, sec)
+        out["ba2000"] = {"ms_per_run": best * 1e3, "cores": 1,
                          "sample": "BA n=2000 m=4 seed 0, normalized; nv=10, s=15 with "
-                                   "heat/wave/VNGE quadrature, in full, one core"}
+                                   "heat/wave/VNGE quadrature, in full, one core, best of 3"}
         gids = list(range(0, SBM_GRAPHS, CPU_SBM_STRIDE))
         gps, longest = pool.sbm_graphs(gids)
         out["sbm_batch"] = {"value": gps, "unit": "graphs/s", "cores": pool.workers,
