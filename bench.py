@@ -717,6 +717,49 @@ ER_DENSITIES = (0.005, 0.01, 0.02, 0.05, 0.1, 0.2)  # n = 1000
 ER_NV, ER_S = 100, 10                              # the paper's defaults
 
 
+def run_vnge_combinatorial(src, dst, n_nodes):
+    """The paper's VNGE (on L = D - A scaled by its trace) of the headline
+    graph in the three forms: ms per Lanczos run (CUDA events, second run of
+    each form), the VNGE and its relative error against FP64, and the heat
+    trace's over the t each reduced form serves (|t| * bound <= 2000 FP32,
+    <= 20 BF16)."""
+    import torch
+    from paper_2003_01282_gb300 import slaq
+    g = slaq.build_laplacian(src, dst, n_nodes, kind=slaq.COMBINATORIAL, flags=slaq.DROP_ISOLATED)
+    bound = 2.0 * float(slaq.graph_export(g)["diag"].max().item())
+    t_np = synth.t_grid(NT)
+    out = {"workload": "R-MAT 2^20 of the headline, L = D - A, nv=100, s=20", "bound": bound}
+    ref = None
+    for name, prec, limit in (("fp64", slaq.FP64, None), ("fp32", slaq.FP32, 2000.0),
+                              ("bf16", slaq.FP32_BF16BASIS, 20.0)):
+        K = None
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            K = slaq.lanczos(g, NV, S, PROBE_SEED, precision=prec, reuse=K)
+            e1.record()
+            torch.cuda.synchronize()
+        ts = t_np if limit is None else t_np[t_np * bound <= limit]
+        heat = (slaq.trace_heat(K, torch.as_tensor(ts, device="cuda"))[0].cpu().numpy()
+                if ts.size else None)
+        v = slaq.trace_vnge(K)[0].item()
+        row = {"ms_per_run": e0.elapsed_time(e1), "vnge": v,
+               "t_max_served_on_grid": float(ts[-1]) if ts.size else None}
+        if ref is None:
+            ref = (v, heat)
+        else:
+            row["vnge_rel_err_vs_fp64"] = abs(v - ref[0]) / abs(ref[0])
+            if heat is not None:
+                row["heat_rel_err_vs_fp64"] = float(np.max(np.abs(heat - ref[1][:heat.size]) /
+                                                           np.abs(ref[1][:heat.size])))
+            row["speedup_over_fp64"] = out["fp64"]["ms_per_run"] / row["ms_per_run"]
+        out[name] = row
+        K.close()
+    g.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_er_sweep(dev):
     """Fig. 4 / Sec. 4.1 on Erdos-Renyi graphs: relative l2 error of the heat
     descriptor (256 t) against the exact one for SLQ on the GPU (FP64, nv =
@@ -1109,6 +1152,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         if not dist:
             result["graph_replay"] = small_graph_replay()
+            result["vnge_combinatorial"] = run_vnge_combinatorial(src, dst, n_nodes)
 
     # end to end through the host-memory entry point (pinned buffers)
     if not args.quick and not dist:

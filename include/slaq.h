@@ -53,9 +53,10 @@ enum { SLAQ_DROP_ISOLATED = 1 };
  *   SLAQ_FP64           basis, SpMM and reorthogonalization in FP64;
  *   SLAQ_FP32           basis, SpMM and reorthogonalization in FP32;
  *   SLAQ_FP32_BF16BASIS basis stored in BF16, SpMM and updates in FP32.
- * The FP32 and BF16-basis forms run normalized Laplacians only (spectrum in
- * [0, 2]); on a combinatorial Laplacian slaq_lanczos returns
- * SLAQ_EUNSUPPORTED. */
+ * The FP32 and BF16-basis forms run both Laplacian kinds; their heat and
+ * wave traces are served for |t| * bound <= 2000 and <= 20 respectively
+ * (bound = 2 for the normalized Laplacian, 2 max d for L = D - A), see
+ * slaq_trace_heat. */
 enum { SLAQ_FP64 = 0, SLAQ_FP32 = 1, SLAQ_FP32_BF16BASIS = 2 };
 /* reorth_passes value for partial reorthogonalization (slaq_lanczos). */
 enum { SLAQ_REORTH_PARTIAL = 0 };
@@ -275,15 +276,17 @@ int slaq_krylov_info(slaq_krylov k, int *nv_host, int *s_host, int *precision_ho
  * device) by Eq. slq: out[i] = (n'/nv) sum_p sum_k tau2 exp(-t_i theta);
  * stderr_[i] = sample std over probes / sqrt(nv) (NaN when nv = 1);
  * per_probe float64[nv*nt] (row p = n' sum_k tau2 exp(-t theta)) or NULL.
- * The BF16-basis form serves |t| * bound <= 20 only (t <= 10 on a normalized
- * Laplacian, whose bound is 2): its basis rounding moves the Ritz values
- * that are not yet converged at first order, which exp(-t theta) turns into
- * errors growing with t (measured within 2.3e-5 of the FP64 form up to the
- * limit on every graph tried, above 1e-4 from t = 29 on cycles, paths,
- * grids, trees and small SBM graphs).  A larger t gives SLAQ_EUNSUPPORTED;
- * for that form the call copies t to the host and synchronizes `stream` to
- * check it.  The same holds for slaq_trace_heat_cv, slaq_trace_wave and
- * slaq_trace_wave_per_probe. */
+ * The reduced forms serve |t| * bound <= 20 (BF16 basis) and <= 2000 (FP32)
+ * only, with bound 2 for the normalized Laplacian (t <= 10 and t <= 1000)
+ * and 2 max d for L = D - A: the basis rounding moves the Ritz values that
+ * are not yet converged by about the rounding times bound, which
+ * exp(-t theta) turns into errors growing with t * bound (measured within
+ * 2.3e-5 (BF16) and 4.4e-7 (FP32, up to t * bound = 1000) of the FP64 form
+ * on every graph tried, both Laplacians; the 1e-4 bar first failed at
+ * t * bound = 58 (BF16) and 22,000 (FP32)).  A larger t gives
+ * SLAQ_EUNSUPPORTED; the reduced forms copy t to the host and synchronize
+ * `stream` to check it.  The same holds for slaq_trace_heat_cv,
+ * slaq_trace_wave and slaq_trace_wave_per_probe. */
 int slaq_trace_heat(slaq_krylov k, const double *t, int nt, double *out, double *stderr_,
                     double *per_probe, void *stream);
 
@@ -303,14 +306,15 @@ int slaq_trace_heat_cv(slaq_krylov k, const double *t, int nt, int degree, doubl
                        double *stderr_, double *per_probe, void *stream);
 
 /* Wave trace tr exp(-i t L): re[i] = sum cos(t lambda), im[i] = -sum sin(t lambda),
- * estimated as above; stderr arrays may be NULL.  The BF16-basis form's
- * limit on t is that of slaq_trace_heat (measured for the wave: below 1e-5
- * of max |Re| up to the limit, up to 0.28 at t = 100). */
+ * estimated as above; stderr arrays may be NULL.  The reduced forms'
+ * limits on t are those of slaq_trace_heat (measured for the wave with the
+ * BF16 basis: below 1e-5 of max |Re| up to its limit, up to 0.28 at t = 100
+ * on R-MAT). */
 int slaq_trace_wave(slaq_krylov k, const double *t, int nt, double *re, double *im,
                     double *stderr_re, double *stderr_im, void *stream);
 
 /* Per-probe values of the wave trace (as slaq_trace_wave, with its limit on
- * t for the BF16-basis form, before the mean
+ * t for the reduced forms, before the mean
  * over probes): re_pp[p][i] = n' sum_k tau2 cos(t_i theta) and im_pp[p][i] =
  * -n' sum_k tau2 sin(t_i theta), float64[nv*nt] each ([G][nv][nt] for a
  * batch).  With the per_probe outputs of the heat trace and the VNGE these

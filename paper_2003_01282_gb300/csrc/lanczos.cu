@@ -2398,12 +2398,6 @@ int run_lanczos(slaq_graph g, int nv, int s, uint64_t seed, int graph_id, int pr
     return set_error(SLAQ_EUNSUPPORTED,
                      "partial reorthogonalization needs an FP64 or FP32 basis (BF16 storage "
                      "rounds above the semi-orthogonality level)");
-  if (precision != SLAQ_FP64 && g->kind == SLAQ_COMBINATORIAL)
-    return set_error(SLAQ_EUNSUPPORTED,
-                     "the FP32 and BF16-basis forms need the normalized Laplacian: on L = D - A "
-                     "(spectrum up to 2 max d) their basis rounding moves the Ritz values by "
-                     "u * 2 max d, which exp(-t theta) turns into heat-trace errors above 1e-4; "
-                     "run combinatorial Laplacians in SLAQ_FP64");
   if (g->n < 1) return set_error(SLAQ_EINVAL, "graph has no nodes");
   if (g->n > (1LL << 31)) return set_error(SLAQ_EUNSUPPORTED, "too many nodes");
   const int ld = row_ld(nv, precision);

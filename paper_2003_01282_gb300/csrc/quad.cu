@@ -663,12 +663,12 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   return SLAQ_OK;
 }
 
-int check_bf16_t(slaq_krylov K, const double *t, int nt, const char *what, cudaStream_t st);
+int check_reduced_t(slaq_krylov K, const double *t, int nt, const char *what, cudaStream_t st);
 
 int trace_heat(slaq_krylov K, const double *t, int nt, double *out, double *se, double *per_probe,
                cudaStream_t st) {
   if (nt < 1 || !t || !out) return set_error(SLAQ_EINVAL, "heat trace needs t, nt >= 1 and out");
-  SLAQ_TRY(check_bf16_t(K, t, nt, "heat trace", st));
+  SLAQ_TRY(check_reduced_t(K, t, nt, "heat trace", st));
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
   const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
@@ -686,7 +686,7 @@ int trace_heat_cv(slaq_krylov K, const double *t, int nt, int degree, double *ou
                   double *per_probe, cudaStream_t st) {
   if (nt < 1 || !t || !out) return set_error(SLAQ_EINVAL, "heat trace needs t, nt >= 1 and out");
   if (degree != 1 && degree != 2) return set_error(SLAQ_EINVAL, "control-variate degree must be 1 or 2");
-  SLAQ_TRY(check_bf16_t(K, t, nt, "heat trace", st));
+  SLAQ_TRY(check_reduced_t(K, t, nt, "heat trace", st));
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
   const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);
@@ -702,32 +702,42 @@ int trace_heat_cv(slaq_krylov K, const double *t, int nt, int degree, double *ou
   return SLAQ_OK;
 }
 
-// The BF16-basis form serves heat and wave traces for |t| * bound <=
-// kBf16TB only.  Its basis is rounded at 2^-9, which moves the Ritz values
-// that are not yet converged at first order; exp(-t theta) and cos(t theta)
-// turn that into errors growing with t.  Measured against the FP64 form (nv
-// 24 and 64, s 16 and 20): up to t * bound = 20 (t = 10 on a normalized
-// Laplacian) the heat trace stayed within 2.3e-5 relative and the wave trace
-// within 1e-5 of max |Re| on every graph tried (R-MAT, BA, ER, SBM batches,
-// trees, cycles, paths, grids, weighted and not); beyond it graphs with many
-// small eigenvalues (cycles, paths, grids, trees, small SBM graphs) pass the
-// 1e-4 bar of the heat trace at t = 29 .. 66 and the wave's at t = 20 .. 45.
+// The reduced forms serve heat and wave traces for |t| * bound <= a limit
+// of their own (bound: 2 on a normalized Laplacian, 2 max d on L = D - A).
+// The stored basis is rounded (2^-9 for BF16, 2^-24 for FP32), which moves
+// the Ritz values that are not yet converged at first order, by about the
+// rounding times bound; exp(-t theta) and cos(t theta) turn that into errors
+// that grow with t * bound.  Measured against the FP64 form (nv 24 and 64,
+// s 16 and 20):
+// * BF16 basis, limit 20: within 2.3e-5 relative (heat) and 1e-5 of max
+//   |Re| (wave) up to t * bound = 20 on every graph tried (R-MAT, BA, ER, SBM
+//   batches, trees, cycles, paths, grids, weighted and not, both Laplacians);
+//   beyond it the first failures of the 1e-4 bars came at t * bound = 58
+//   (heat) and 40 (wave) on normalized small-eigenvalue graphs, 82 and 69 on
+//   weighted cycles and paths with L = D - A;
+// * FP32, limit 2000: within 4.4e-7 (heat) up to t * bound = 1000 on BA,
+//   ER, R-MAT, cycles and paths with L = D - A; the heat bar first failed at
+//   t * bound = 22,000 (a weighted BA graph), the wave's beyond 287,000.
+//   (On a normalized Laplacian the limit is t <= 1000.)
 constexpr double kBf16TB = 20.0;
+constexpr double kFp32TB = 2000.0;
 
-// SLAQ_OK, or SLAQ_EUNSUPPORTED if the form is the BF16 basis and some t is
-// beyond its limit (copies t to the host and synchronizes st for that form).
-int check_bf16_t(slaq_krylov K, const double *t, int nt, const char *what, cudaStream_t st) {
-  if (K->precision != SLAQ_FP32_BF16BASIS) return SLAQ_OK;
+// SLAQ_OK, or SLAQ_EUNSUPPORTED if some t is beyond the reduced form's
+// limit (copies t to the host and synchronizes st for the reduced forms).
+int check_reduced_t(slaq_krylov K, const double *t, int nt, const char *what, cudaStream_t st) {
+  if (K->precision == SLAQ_FP64) return SLAQ_OK;
+  const bool bf16 = K->precision == SLAQ_FP32_BF16BASIS;
+  const double limit = bf16 ? kBf16TB : kFp32TB;
   std::vector<double> th(nt);
   SLAQ_CHECK_CUDA(cudaMemcpyAsync(th.data(), t, nt * sizeof(double), cudaMemcpyDeviceToHost, st));
   SLAQ_CHECK_CUDA(cudaStreamSynchronize(st));
   for (int i = 0; i < nt; ++i)
-    if (!(std::fabs(th[i]) * K->bound <= kBf16TB))
+    if (!(std::fabs(th[i]) * K->bound <= limit))
       return set_error(SLAQ_EUNSUPPORTED,
-                       "the BF16-basis form serves the %s for |t| * bound <= %g only (t = %g, bound "
-                       "%g): beyond it the basis rounding moves the trace by more than 1e-4; use "
-                       "SLAQ_FP32",
-                       what, kBf16TB, th[i], K->bound);
+                       "the %s form serves the %s for |t| * bound <= %g only (t = %g, bound %g): "
+                       "beyond it the basis rounding moves the trace by more than 1e-4; use %s",
+                       bf16 ? "BF16-basis" : "FP32", what, limit, th[i], K->bound,
+                       bf16 ? "SLAQ_FP32 or SLAQ_FP64" : "SLAQ_FP64");
   return SLAQ_OK;
 }
 
@@ -737,7 +747,7 @@ int trace_wave(slaq_krylov K, const double *t, int nt, double *re, double *im, d
                double *se_im, cudaStream_t st, double *pp_re, double *pp_im) {
   if (nt < 1 || !t || ((!re || !im) && (!pp_re || !pp_im)))
     return set_error(SLAQ_EINVAL, "wave trace needs t, nt, and re, im or per-probe outputs");
-  SLAQ_TRY(check_bf16_t(K, t, nt, "wave trace", st));
+  SLAQ_TRY(check_reduced_t(K, t, nt, "wave trace", st));
   ProfScope prof(SLAQ_PROF_TRACE, st);
   ++tl_launches;
   const dim3 grid((unsigned)ceil_div(nt, kTT), K->n_graphs);

@@ -292,20 +292,38 @@ def test_reduced_forms_normalized_values_and_pattern_forms(weighted):
 
 
 @pytest.mark.parametrize("weighted", [True, False])
-def test_reduced_forms_refuse_combinatorial_laplacians(weighted):
-    """On L = D - A (spectrum up to 2 max d) the reduced forms' basis rounding
-    moves the Ritz values by about u * 2 max d, and exp(-t theta) turns that
-    into heat-trace errors above 1e-4 (measured: BF16 from t ~ 1 on a BA graph
-    with max d = 199 and from t ~ 27 on a cycle; FP32 from t ~ 50 on the BA
-    graph).  slaq_lanczos refuses the combination; FP64 runs it."""
-    s, d, n = synth.barabasi_albert(600, 3, seed=12)
-    w = np.random.default_rng(5).uniform(0.5, 2.0, s.size) if weighted else None
-    g = gpu_graph(s, d, n, COMBINATORIAL, weights=w)
-    for prec in (slaq.FP32, slaq.FP32_BF16BASIS):
-        with pytest.raises(slaq.SlaqError) as ei:
-            slaq.lanczos(g, 8, 10, 6, precision=prec)
-        assert ei.value.status == 6 and "normalized Laplacian" in str(ei.value)
-    slaq.lanczos(g, 8, 10, 6, precision=slaq.FP64)
+def test_reduced_forms_on_combinatorial_laplacians(weighted):
+    """On L = D - A (spectrum up to bound = 2 max d) the reduced forms serve
+    the heat and wave traces for |t| * bound <= 2000 (FP32) and <= 20 (BF16
+    basis): within relative 1e-4 (heat) and 1e-4 of max |Re| (wave) of the
+    FP64 form there, VNGE (the paper's, on L / tr L) within 1e-3; a t beyond
+    the limit is refused.  Graphs: a BA graph with hubs (bound ~400) and a
+    cycle (bound 4), where the limit leaves most of the grid and all of it."""
+    for s, d, n in (synth.barabasi_albert(3000, 5, seed=12), synth.cycle(1000)):
+        w = np.random.default_rng(5).uniform(0.5, 2.0, s.size) if weighted else None
+        g = gpu_graph(s, d, n, COMBINATORIAL, weights=w)
+        bound = 2.0 * float(slaq.graph_export(g)["diag"].max().item())
+        t_np = 10.0 ** np.linspace(-4, 2, 121)
+        K64 = slaq.lanczos(g, 24, 16, 6, precision=slaq.FP64)
+        v64 = slaq.trace_vnge(K64)[0].item()
+        for prec, limit in ((slaq.FP32, 2000.0), (slaq.FP32_BF16BASIS, 20.0)):
+            ts = t_np[t_np * bound <= limit]
+            t = dev(ts, torch.float64)
+            h64 = slaq.trace_heat(K64, t)[0].cpu().numpy()
+            (r64, _), (i64, _) = slaq.trace_wave(K64, t)
+            K = slaq.lanczos(g, 24, 16, 6, precision=prec)
+            h = slaq.trace_heat(K, t)[0].cpu().numpy()
+            (r, _), (i, _) = slaq.trace_wave(K, t)
+            assert _rel(h, h64) < 1e-4, (prec, bound)
+            scale = np.max(np.abs(r64.cpu().numpy()))
+            assert np.max(np.abs(r.cpu().numpy() - r64.cpu().numpy())) < 1e-4 * scale
+            assert np.max(np.abs(i.cpu().numpy() - i64.cpu().numpy())) < 1e-4 * scale
+            assert abs(slaq.trace_vnge(K)[0].item() - v64) / abs(v64) < 1e-3
+            bad = dev([1.01 * limit / bound], torch.float64)
+            for call in (lambda: slaq.trace_heat(K, bad), lambda: slaq.trace_wave(K, bad)):
+                with pytest.raises(slaq.SlaqError) as ei:
+                    call()
+                assert ei.value.status == 6
 
 
 def test_bf16_wave_served_up_to_its_limit():
@@ -330,9 +348,12 @@ def test_bf16_wave_served_up_to_its_limit():
             with pytest.raises(slaq.SlaqError) as ei:
                 call()
             assert ei.value.status == 6
-    # FP32 and FP64 serve every t
-    for prec in (slaq.FP32, slaq.FP64):
-        slaq.trace_heat(slaq.lanczos(g, 4, 6, 9, precision=prec), dev([100.0], torch.float64))
+    # FP32 serves t up to 1000 on a normalized Laplacian, FP64 every t
+    slaq.trace_heat(slaq.lanczos(g, 4, 6, 9, precision=slaq.FP32), dev([1000.0], torch.float64))
+    with pytest.raises(slaq.SlaqError) as ei:
+        slaq.trace_heat(slaq.lanczos(g, 4, 6, 9, precision=slaq.FP32), dev([1001.0], torch.float64))
+    assert ei.value.status == 6
+    slaq.trace_heat(slaq.lanczos(g, 4, 6, 9, precision=slaq.FP64), dev([1e6], torch.float64))
 
 
 @pytest.mark.parametrize("graph", ["star2600", "k9", "k35", "star30"])
