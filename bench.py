@@ -380,8 +380,8 @@ class ClockSampler:
 # R-MAT 2^20 workload from an ncu capture of step 16; it describes the
 # kernels only while csrc/lanczos.cu is byte-identical to the captured source.
 SPMM_TRAFFIC = {
-    "bytes_per_spmm": 1956395000 + 350863872 + 561344000 + 8396288,
-    "source_sha256": "8418a32ea6686eb7f759a6df2a314e77b04a66c6d95184af36e46fb04d248806",
+    "bytes_per_spmm": 1955549000 + 350689024 + 561410000 + 8378112,
+    "source_sha256": "c88440fec2e8e297210b9097e28debbf4ee01506b955e371400813a288fc1a60",
 }
 
 
