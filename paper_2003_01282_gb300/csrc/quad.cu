@@ -663,6 +663,97 @@ int run_ritz(slaq_krylov K, cudaStream_t st) {
   return SLAQ_OK;
 }
 
+namespace {
+// Heat trace of the reduced forms with no FP64 work per term (FP64 is the
+// narrow pipe of GB300).  The block stages its graph's rules once: theta as
+// two floats (hi = fl(theta), lo = fl(theta - hi)) and tau2 as a float.  The
+// product t theta is formed as p = fl(t_hi theta_hi) plus its residual
+// c = fma(t_hi, theta_hi, -p) + t_hi theta_lo + t_lo theta_hi, with
+// |c| <= 3 * 2^-24 |p|, so that e^{-t theta} = e^{-p} (1 - c) up to c^2 / 2
+// (below 2e-10 wherever e^{-p} is a normal float).  Rounding t theta itself
+// to a float, as a plain FP32 evaluation does, would cost |t theta| 2^-24
+// relative instead.  Welford updates multiply by staged reciprocals of the
+// probe counts.  Same layout, probe order and combination as k_trace_t.
+inline size_t heat_f32_smem(int nv, int s) {
+  const size_t per = (size_t)nv * s;
+  const size_t nrcp = (size_t)(nv + kPG - 1) / kPG + 1;
+  return nrcp * sizeof(double) + per * 3 * sizeof(float) + (size_t)nv * sizeof(int32_t);
+}
+constexpr size_t kHeatF32SmemMax = 48 * 1024;
+
+__global__ void __launch_bounds__(kTT * kPG)
+    k_heat_f32(const double *__restrict__ theta, const double *__restrict__ tau2,
+               const int32_t *__restrict__ mm, int nv, int s, const double *__restrict__ gn,
+               const double *__restrict__ t, int nt, double *out, double *se, double *per_probe) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int nrcp = (nv + kPG - 1) / kPG + 1;
+  double *rcp = reinterpret_cast<double *>(dyn);       // rcp[c] = 1 / c
+  float *th_hi = reinterpret_cast<float *>(rcp + nrcp);  // [nv][s] of this graph
+  float *th_lo = th_hi + nv * s;
+  float *wt = th_lo + nv * s;
+  int32_t *ms = reinterpret_cast<int32_t *>(wt + nv * s);
+  __shared__ double sh_mean[kPG][kTT], sh_m2[kPG][kTT];
+  __shared__ int sh_cnt[kPG][kTT];
+  const int gr = blockIdx.y;
+  const int64_t base = (int64_t)gr * nv * s;
+  for (int i = threadIdx.x; i < nv * s; i += blockDim.x) {
+    const double th = theta[base + i];
+    const float hi = (float)th;
+    th_hi[i] = hi;
+    th_lo[i] = (float)(th - (double)hi);
+    wt[i] = (float)tau2[base + i];
+  }
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) ms[i] = mm[(int64_t)gr * nv + i];
+  for (int i = threadIdx.x; i < nrcp; i += blockDim.x) rcp[i] = i > 0 ? 1.0 / i : 0.0;
+  __syncthreads();
+  const int tt = threadIdx.x % kTT, pg = threadIdx.x / kTT;
+  const int ti = blockIdx.x * kTT + tt;
+  double mean = 0.0, m2 = 0.0;
+  int cnt = 0;
+  if (ti < nt) {
+    const double tv = t[ti];
+    const float t_hi = (float)tv, t_lo = (float)(tv - (double)t_hi);
+    const double n = gn[gr];
+    for (int p = pg; p < nv; p += kPG) {
+      const int m = min(ms[p], s);
+      const float *h = th_hi + p * s, *l = th_lo + p * s, *w = wt + p * s;
+      float af = 0.0f;
+      for (int k = 0; k < m; ++k) {
+        const float pr = t_hi * h[k];
+        const float c = fmaf(t_hi, h[k], -pr) + fmaf(t_hi, l[k], t_lo * h[k]);
+        af = fmaf(w[k], expf(-pr) * (1.0f - c), af);
+      }
+      const double x = n * (double)af;
+      const int64_t q = (int64_t)gr * nv + p;
+      if (per_probe) per_probe[q * nt + ti] = x;
+      ++cnt;
+      const double d = x - mean;
+      mean += d * rcp[cnt];
+      m2 += d * (x - mean);
+    }
+  }
+  sh_mean[pg][tt] = mean;
+  sh_m2[pg][tt] = m2;
+  sh_cnt[pg][tt] = cnt;
+  __syncthreads();
+  if (pg == 0 && ti < nt) {
+    double M = sh_mean[0][tt], S2 = sh_m2[0][tt];
+    int N = sh_cnt[0][tt];
+    for (int h = 1; h < kPG; ++h) {
+      const int nb = sh_cnt[h][tt];
+      if (nb == 0) continue;
+      const double delta = sh_mean[h][tt] - M;
+      const int nn = N + nb;
+      M += delta * nb / nn;
+      S2 += sh_m2[h][tt] + delta * delta * ((double)N * nb / nn);
+      N = nn;
+    }
+    if (out) out[(int64_t)gr * nt + ti] = M;
+    if (se) se[(int64_t)gr * nt + ti] = nv > 1 ? sqrt(S2 / (nv - 1) / nv) : nan("");
+  }
+}
+}  // namespace
+
 int check_reduced_t(slaq_krylov K, const double *t, int nt, const char *what, cudaStream_t st);
 
 int trace_heat(slaq_krylov K, const double *t, int nt, double *out, double *se, double *per_probe,
@@ -675,6 +766,9 @@ int trace_heat(slaq_krylov K, const double *t, int nt, double *out, double *se, 
   if (K->precision == SLAQ_FP64)
     k_trace_t<0, false><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
                                                      t, nt, out, se, per_probe);
+  else if (heat_f32_smem(K->nv, K->s) <= kHeatF32SmemMax)
+    k_heat_f32<<<grid, kTT * kPG, heat_f32_smem(K->nv, K->s), st>>>(
+        K->theta, K->tau2, K->m, K->nv, K->s, K->gn, t, nt, out, se, per_probe);
   else
     k_trace_t<0, true><<<grid, kTT * kPG, 0, st>>>(K->theta, K->tau2, K->m, K->nv, K->s, K->gn, 0.0,
                                                     t, nt, out, se, per_probe);
