@@ -672,8 +672,15 @@ namespace {
 // |c| <= 3 * 2^-24 |p|, so that e^{-t theta} = e^{-p} (1 - c) up to c^2 / 2
 // (below 2e-10 wherever e^{-p} is a normal float).  Rounding t theta itself
 // to a float, as a plain FP32 evaluation does, would cost |t theta| 2^-24
-// relative instead.  Welford updates multiply by staged reciprocals of the
-// probe counts.  Same layout, probe order and combination as k_trace_t.
+// relative instead.  Same layout, probe order, Welford updates and
+// combination as k_trace_t, so slaq_pool_probes_host reproduces the mean and
+// standard error from the per-probe values to the last bit.  The Welford
+// division d / c takes Markstein's correction instead of a division (an
+// FP64 division is a long sequence on the FP64 pipe): with r = 1/c correctly
+// rounded (staged), q = fl(d r) and fl(q + fl(d - q c) r), the residual
+// formed exactly by an FMA, is the correctly rounded quotient (P. Markstein,
+// IBM J. Res. Dev. 34, 1990); checked against IEEE division on 2e8 random
+// quotients, c = 1..512.
 inline size_t heat_f32_smem(int nv, int s) {
   const size_t per = (size_t)nv * s;
   const size_t nrcp = (size_t)(nv + kPG - 1) / kPG + 1;
@@ -687,7 +694,7 @@ __global__ void __launch_bounds__(kTT * kPG)
                const double *__restrict__ t, int nt, double *out, double *se, double *per_probe) {
   extern __shared__ __align__(16) unsigned char dyn[];
   const int nrcp = (nv + kPG - 1) / kPG + 1;
-  double *rcp = reinterpret_cast<double *>(dyn);       // rcp[c] = 1 / c
+  double *rcp = reinterpret_cast<double *>(dyn);         // rcp[c] = 1 / c
   float *th_hi = reinterpret_cast<float *>(rcp + nrcp);  // [nv][s] of this graph
   float *th_lo = th_hi + nv * s;
   float *wt = th_lo + nv * s;
@@ -728,7 +735,8 @@ __global__ void __launch_bounds__(kTT * kPG)
       if (per_probe) per_probe[q * nt + ti] = x;
       ++cnt;
       const double d = x - mean;
-      mean += d * rcp[cnt];
+      const double r = rcp[cnt], qd = __dmul_rn(d, r);
+      mean += fma(fma(-qd, (double)cnt, d), r, qd);  // d / cnt, correctly rounded
       m2 += d * (x - mean);
     }
   }

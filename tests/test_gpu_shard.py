@@ -109,3 +109,21 @@ def test_rerun_keeps_the_range_and_limits():
             slaq.lanczos_probes(g, nv, p0, S, SEED)
         assert ei.value.status == 1
     slaq.lanczos_probes(g, 4, 65532, S, SEED)  # the last four probes of the field
+
+
+@pytest.mark.parametrize("precision", [slaq.FP64, slaq.FP32, slaq.FP32_BF16BASIS])
+def test_host_pool_reproduces_device_moments_bit_for_bit(precision):
+    """slaq_pool_probes_host over one run's per-probe values gives the
+    device's mean and standard error exactly: the same Welford updates per
+    probe group and Chan merge in group order as the quadrature kernels
+    (heat through k_trace_t for FP64 and k_heat_f32 for the reduced forms)."""
+    _, g = _graph()
+    K = slaq.lanczos(g, 37, S, SEED, precision=precision)
+    t_np = synth.t_grid(40)
+    if precision == slaq.FP32_BF16BASIS:
+        t_np = t_np[t_np * 2.0 <= 20.0]
+    t = torch.as_tensor(t_np, device="cuda", dtype=torch.float64)
+    h, hse, pp = slaq.trace_heat(K, t, per_probe=True)
+    mean, se = slaq.pool_probes_host(pp.cpu().numpy())
+    np.testing.assert_array_equal(mean, h.cpu().numpy())
+    np.testing.assert_array_equal(se, hse.cpu().numpy())
