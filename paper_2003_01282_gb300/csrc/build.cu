@@ -479,24 +479,63 @@ __global__ void k_emit_direct(const int32_t *src, const int32_t *dst, const int3
   }
 }
 
-__global__ void k_first_flags(const uint64_t *k, int64_t m, uint8_t *flag) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = (i == 0 || k[i] != k[i - 1]) ? 1 : 0;
+// Merging duplicates is a stream compaction of the sorted keys: key i starts a
+// run if i = 0 or it differs from key i-1.  k_unique_count counts run starts
+// per scan tile; after the tiles' exclusive scan, k_unique_compact stages its
+// tile's keys (and the key before the tile) in shared memory, finds the
+// starts again, scans them within the tile and writes each run's key, and its
+// largest weight, to the run's slot.  No per-key flag or position array.
+__global__ void __launch_bounds__(kScanThreads)
+    k_unique_count(const uint64_t *__restrict__ k, int64_t m, int64_t *__restrict__ bsum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t acc = 0;
+#pragma unroll
+  for (int it = 0; it < kScanItems; ++it) {
+    const int64_t i = base + (int64_t)it * kScanThreads + threadIdx.x;
+    if (i < m) acc += (i == 0 || k[i] != k[i - 1]) ? 1 : 0;
+  }
+  int64_t tot;
+  block_exclusive_scan(acc, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// Unique keys; the weight of a merged run is the largest of the run.
-__global__ void k_unique(const uint64_t *k, const double *pay, int64_t m, const uint8_t *flag,
-                         const int64_t *pos, uint64_t *ukey, double *uw) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (!flag[i]) continue;
-    ukey[pos[i]] = k[i];
+__global__ void __launch_bounds__(kScanThreads)
+    k_unique_compact(const uint64_t *__restrict__ k, const double *__restrict__ pay, int64_t m,
+                     const int64_t *__restrict__ bsum, uint64_t *__restrict__ ukey,
+                     double *__restrict__ uw) {
+  __shared__ uint64_t sk[kScanTile + 1];  // sk[q + 1] = key t0 + q, sk[0] = the key before
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+  for (int q = threadIdx.x; q < kScanTile; q += kScanThreads) {
+    const int64_t i = t0 + q;
+    sk[q + 1] = i < m ? k[i] : 0;
+  }
+  if (threadIdx.x == 0) sk[0] = t0 > 0 ? k[t0 - 1] : 0;
+  __syncthreads();
+  const int q0 = threadIdx.x * kScanItems;
+  uint32_t starts = 0;
+  int64_t cnt = 0;
+#pragma unroll
+  for (int it = 0; it < kScanItems; ++it) {
+    const int q = q0 + it;
+    const int64_t i = t0 + q;
+    if (i < m && (i == 0 || sk[q + 1] != sk[q])) {
+      starts |= 1u << it;
+      ++cnt;
+    }
+  }
+  int64_t pos = block_exclusive_scan(cnt, nullptr) + bsum[blockIdx.x];
+#pragma unroll
+  for (int it = 0; it < kScanItems; ++it) {
+    if (!((starts >> it) & 1u)) continue;
+    const int64_t i = t0 + q0 + it;
+    const uint64_t key = sk[q0 + it + 1];
+    ukey[pos] = key;
     if (pay) {
       double mx = pay[i];
-      for (int64_t j = i + 1; j < m && k[j] == k[i]; ++j) mx = fmax(mx, pay[j]);
-      uw[pos[i]] = mx;
+      for (int64_t j = i + 1; j < m && k[j] == key; ++j) mx = fmax(mx, pay[j]);
+      uw[pos] = mx;
     }
+    ++pos;
   }
 }
 
@@ -1009,25 +1048,27 @@ int build_laplacian(const int32_t *src, const int32_t *dst, int64_t m, int64_t n
   }
 
   // 3. merge duplicates, rows
-  uint8_t *first = nullptr;
-  int64_t *upos = nullptr, *d_total = nullptr;
-  SLAQ_TRY(tmp.get(&first, m2));
-  SLAQ_TRY(tmp.get(&upos, m2));
+  const int64_t nut = std::max<int64_t>(1, ceil_div(m2, kScanTile));
+  int64_t *ubsum = nullptr, *d_total = nullptr;
+  SLAQ_TRY(tmp.get(&ubsum, nut));
   SLAQ_TRY(tmp.get(&d_total, 1));
   if (m2 > 0) {
     ++tl_launches;
-    k_first_flags<<<grid_for(m2, 256), 256, 0, st>>>(k0, m2, first);
-    SLAQ_CHECK_LAUNCH("first_flags");
+    k_unique_count<<<(unsigned)nut, kScanThreads, 0, st>>>(k0, m2, ubsum);
+  } else {
+    SLAQ_CHECK_CUDA(cudaMemsetAsync(ubsum, 0, sizeof(int64_t), st));
   }
-  SLAQ_TRY(exclusive_scan(first, m2, upos, d_total, st));
+  ++tl_launches;
+  k_scan_tile_prefix<<<1, 1024, 0, st>>>(ubsum, nut, d_total);
+  SLAQ_CHECK_LAUNCH("unique_count");
   int64_t nnz = 0;
   SLAQ_TRY(to_host(&nnz, d_total, 1, st));
   uint64_t *ukey = k1;  // the sort's spare buffer
   double *uw = weighted ? p1 : nullptr;
   if (m2 > 0) {
     ++tl_launches;
-    k_unique<<<grid_for(m2, 256), 256, 0, st>>>(k0, weighted ? p0 : nullptr, m2, first, upos,
-                                                ukey, uw);
+    k_unique_compact<<<(unsigned)nut, kScanThreads, 0, st>>>(k0, weighted ? p0 : nullptr, m2,
+                                                              ubsum, ukey, uw);
     SLAQ_CHECK_LAUNCH("unique");
   }
   int64_t *rowptr_full = nullptr;
