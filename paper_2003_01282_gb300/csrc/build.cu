@@ -481,10 +481,10 @@ __global__ void k_emit_direct(const int32_t *src, const int32_t *dst, const int3
 
 // Merging duplicates is a stream compaction of the sorted keys: key i starts a
 // run if i = 0 or it differs from key i-1.  k_unique_count counts run starts
-// per scan tile; after the tiles' exclusive scan, k_unique_compact stages its
-// tile's keys (and the key before the tile) in shared memory, finds the
-// starts again, scans them within the tile and writes each run's key, and its
-// largest weight, to the run's slot.  No per-key flag or position array.
+// per scan tile; after the tiles' exclusive scan, k_unique_compact finds the
+// starts again (warp ballots over coalesced rounds), scans their counts
+// within the tile and writes each run's key, and its largest weight, to the
+// run's slot.  No per-key flag or position array.
 __global__ void __launch_bounds__(kScanThreads)
     k_unique_count(const uint64_t *__restrict__ k, int64_t m, int64_t *__restrict__ bsum) {
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -503,39 +503,56 @@ __global__ void __launch_bounds__(kScanThreads)
     k_unique_compact(const uint64_t *__restrict__ k, const double *__restrict__ pay, int64_t m,
                      const int64_t *__restrict__ bsum, uint64_t *__restrict__ ukey,
                      double *__restrict__ uw) {
-  __shared__ uint64_t sk[kScanTile + 1];  // sk[q + 1] = key t0 + q, sk[0] = the key before
+  // round r covers items t0 + r * kScanThreads + threadIdx.x (coalesced); in
+  // key order the items run round by round, warp by warp, lane by lane, so
+  // the run starts of (round, warp) pairs are counted by ballots, scanned in
+  // that order, and placed within a warp by the lanes below
+  constexpr int kW = kScanThreads / 32;
+  constexpr int kCnt = kScanItems * kW;  // (round, warp) counts, a multiple of 32
+  static_assert(kCnt % 32 == 0, "count table must split evenly over a warp");
+  __shared__ int64_t cnt[kCnt];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
-  for (int q = threadIdx.x; q < kScanTile; q += kScanThreads) {
-    const int64_t i = t0 + q;
-    sk[q + 1] = i < m ? k[i] : 0;
-  }
-  if (threadIdx.x == 0) sk[0] = t0 > 0 ? k[t0 - 1] : 0;
-  __syncthreads();
-  const int q0 = threadIdx.x * kScanItems;
-  uint32_t starts = 0;
-  int64_t cnt = 0;
+  uint32_t ball[kScanItems];
+  uint64_t key[kScanItems];
 #pragma unroll
-  for (int it = 0; it < kScanItems; ++it) {
-    const int q = q0 + it;
-    const int64_t i = t0 + q;
-    if (i < m && (i == 0 || sk[q + 1] != sk[q])) {
-      starts |= 1u << it;
-      ++cnt;
+  for (int r = 0; r < kScanItems; ++r) {
+    const int64_t i = t0 + (int64_t)r * kScanThreads + threadIdx.x;
+    const uint64_t kv = i < m ? k[i] : 0;
+    uint64_t prev = __shfl_up_sync(0xffffffffu, kv, 1);
+    if (lane == 0 && i > 0 && i < m) prev = k[i - 1];
+    ball[r] = __ballot_sync(0xffffffffu, i < m && (i == 0 || kv != prev));
+    key[r] = kv;
+    if (lane == 0) cnt[r * kW + warp] = __popc(ball[r]);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int per = kCnt / 32;
+    int64_t v[per], sum = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+      v[q] = cnt[lane * per + q];
+      sum += v[q];
+    }
+    int64_t ex = warp_inclusive_scan(sum) - sum + bsum[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+      cnt[lane * per + q] = ex;
+      ex += v[q];
     }
   }
-  int64_t pos = block_exclusive_scan(cnt, nullptr) + bsum[blockIdx.x];
+  __syncthreads();
 #pragma unroll
-  for (int it = 0; it < kScanItems; ++it) {
-    if (!((starts >> it) & 1u)) continue;
-    const int64_t i = t0 + q0 + it;
-    const uint64_t key = sk[q0 + it + 1];
-    ukey[pos] = key;
+  for (int r = 0; r < kScanItems; ++r) {
+    if (!((ball[r] >> lane) & 1u)) continue;
+    const int64_t pos = cnt[r * kW + warp] + __popc(ball[r] & ((1u << lane) - 1u));
+    ukey[pos] = key[r];
     if (pay) {
+      const int64_t i = t0 + (int64_t)r * kScanThreads + threadIdx.x;
       double mx = pay[i];
-      for (int64_t j = i + 1; j < m && k[j] == key; ++j) mx = fmax(mx, pay[j]);
+      for (int64_t j = i + 1; j < m && k[j] == key[r]; ++j) mx = fmax(mx, pay[j]);
       uw[pos] = mx;
     }
-    ++pos;
   }
 }
 
