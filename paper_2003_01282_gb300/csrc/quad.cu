@@ -679,8 +679,8 @@ namespace {
 // FP64 division is a long sequence on the FP64 pipe): with r = 1/c correctly
 // rounded (staged), q = fl(d r) and fl(q + fl(d - q c) r), the residual
 // formed exactly by an FMA, is the correctly rounded quotient (P. Markstein,
-// IBM J. Res. Dev. 34, 1990); checked against IEEE division on 2e8 random
-// quotients, c = 1..512.
+// IBM J. Res. Dev. 34, 1990; tests/test_markstein_cpu.py checks it against
+// IEEE division for c = 1..512).
 inline size_t heat_f32_smem(int nv, int s) {
   const size_t per = (size_t)nv * s;
   const size_t nrcp = (size_t)(nv + kPG - 1) / kPG + 1;
